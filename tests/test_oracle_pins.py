@@ -1,0 +1,334 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks one part of the oracle against a closed form, an invariant,
+an independent library routine (numpy / scipy) or a published fixture, chosen
+so that a dropped term, a wrong sign, a wrong index or a transposed operand in
+the oracle fails at least one of them.  Paper: Hupca et al., sec. 2.1.
+"""
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import legendre as npleg
+
+from paper_1010_1260_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+FOURPI = 4.0 * np.pi
+
+
+# ----------------------------------------------------------------- geometry --
+
+@pytest.mark.parametrize("n", [1, 2, 7, 8, 128, 257])
+def test_gl_nodes_match_numpy_leggauss(oracle_mod, n):
+    g = oracle_mod.gl_grid(n, 2 * n)
+    xr, wr = npleg.leggauss(n)
+    order = np.argsort(-xr)
+    np.testing.assert_allclose(g["x"], xr[order], rtol=0, atol=2e-15)
+    # numpy's own end weights drift to ~1e-10 relative above n = 100 (its
+    # documentation warns about high degrees); exact integration below is the
+    # tight check on the weights
+    np.testing.assert_allclose(g["w"], wr[order], rtol=5e-10, atol=0)
+    assert np.all(np.diff(g["x"]) < 0)
+
+
+@pytest.mark.parametrize("n", [16, 128])
+def test_gl_exact_integration(oracle_mod, n):
+    g = oracle_mod.gl_grid(n, 1)
+    for k in range(2 * n):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.sum(g["w"] * g["x"] ** k) - exact) < 1e-14
+
+
+def test_healpix_golden_centres(oracle_mod):
+    rows = np.loadtxt(os.path.join(GOLDEN, "healpix_nside1_nside2_centres.txt"))
+    for nside in (1, 2):
+        g = oracle_mod.healpix_grid(nside)
+        sub = rows[rows[:, 0] == nside]
+        assert len(sub) == g["nrings"]
+        np.testing.assert_allclose(g["x"], sub[:, 2], atol=1e-15)
+        np.testing.assert_array_equal(g["nphi"], sub[:, 3].astype(int))
+        np.testing.assert_allclose(g["phi0"] / np.pi, sub[:, 4], atol=1e-15)
+
+
+@pytest.mark.parametrize("nside", [1, 2, 3, 16, 512, 1024])
+def test_healpix_invariants(oracle_mod, nside):
+    g = oracle_mod.healpix_grid(nside)
+    assert g["nrings"] == 4 * nside - 1
+    assert g["npix"] == 12 * nside * nside
+    x, st, nphi = g["x"], g["st"], g["nphi"]
+    assert np.all(np.diff(x) < 0)                                   # north to south
+    np.testing.assert_allclose(x, -x[::-1], atol=1e-15)             # equatorial mirror
+    np.testing.assert_array_equal(nphi, nphi[::-1])
+    np.testing.assert_allclose(x * x + st * st, 1.0, atol=4e-16)
+    # equal area: the north polar cap (z > 2/3) holds 1/6 of the sphere, i.e.
+    # 2 nside^2 pixels = the cap rings plus half of the boundary ring i = nside
+    cap = np.sum(nphi[: nside - 1]) + nphi[nside - 1] // 2
+    assert cap == 2 * nside * nside
+    # the belt rings are equally spaced in z
+    belt = x[nside - 1: 3 * nside]
+    np.testing.assert_allclose(np.diff(belt), -2.0 / (3 * nside), atol=1e-14)
+
+
+# --------------------------------------------------------------- lambda_lm --
+
+def _closed_forms(theta):
+    c, s = np.cos(theta), np.sin(theta)
+    return {
+        (0, 0): 0.5 / np.sqrt(np.pi),
+        (1, 0): np.sqrt(3 / FOURPI) * c,
+        (1, 1): -np.sqrt(3 / (8 * np.pi)) * s,
+        (2, 0): np.sqrt(5 / (16 * np.pi)) * (3 * c * c - 1),
+        (2, 1): -np.sqrt(15 / (8 * np.pi)) * s * c,
+        (2, 2): np.sqrt(15 / (32 * np.pi)) * s * s,
+        (3, 0): np.sqrt(7 / (16 * np.pi)) * (5 * c ** 3 - 3 * c),
+        (3, 1): -np.sqrt(21 / (64 * np.pi)) * s * (5 * c * c - 1),
+        (3, 2): np.sqrt(105 / (32 * np.pi)) * s * s * c,
+        (3, 3): -np.sqrt(35 / (64 * np.pi)) * s ** 3,
+    }
+
+
+@pytest.mark.parametrize("theta", [1e-3, 0.3, 1.0, np.pi / 2, 2.0, np.pi - 0.01])
+def test_lambda_closed_forms_l_le_3(oracle_mod, theta):
+    lam = oracle_mod.lam(3, 3, np.cos(theta), np.sin(theta))
+    for (l, m), v in _closed_forms(theta).items():
+        assert abs(lam[inputs.alm_index(l, m, 3)] - v) < 2e-15, (l, m)
+
+
+def _addition(lam, lmax):
+    ls, ms = inputs.lm_arrays(lmax, lmax)
+    w = np.where(ms == 0, 1.0, 2.0)
+    return np.bincount(ls, weights=w * lam * lam, minlength=lmax + 1)
+
+
+@pytest.mark.parametrize("theta", [5.6e-4, 0.01, 0.2, 1.1, np.pi / 2, 2.9])
+def test_addition_theorem_lmax_2048(oracle_mod, theta):
+    # sum_m |Y_lm|^2 = (2l+1)/(4 pi) at every l, including polar rings where
+    # lambda_mm underflows by thousands of binary orders (exponent tracking)
+    # (sin theta is formed from the rounded x so that x^2 + s^2 = 1 holds to
+    # rounding: near the poles the identity is that sensitive to the pair)
+    lmax = 2048
+    lam = oracle_mod.lam(lmax, lmax, np.cos(theta))
+    assert np.all(np.isfinite(lam))
+    got = _addition(lam, lmax)
+    want = (2 * np.arange(lmax + 1) + 1) / FOURPI
+    # 2048 recurrence steps near x = 1 accumulate a few 1e-12 of rounding
+    np.testing.assert_allclose(got, want, rtol=5e-12)
+
+
+def test_addition_theorem_healpix_polar_rings(oracle_mod):
+    g = oracle_mod.healpix_grid(1024)
+    for r in (0, 1, 2, 1023, 2047):
+        lam = oracle_mod.lam(2048, 2048, g["x"][r])
+        got = _addition(lam, 2048)
+        want = (2 * np.arange(2049) + 1) / FOURPI
+        np.testing.assert_allclose(got, want, rtol=5e-12)
+
+
+@pytest.mark.parametrize("x", [-0.97, -0.3, 0.0, 0.41, 0.999])
+def test_m0_matches_numpy_legendre(oracle_mod, x):
+    lmax = 200
+    lam = oracle_mod.lam(lmax, 0, x)
+    for l in range(lmax + 1):
+        c = np.zeros(l + 1)
+        c[l] = 1.0
+        want = np.sqrt((2 * l + 1) / FOURPI) * npleg.legval(x, c)
+        # both sides round differently (numpy sums a Clenshaw series); the
+        # envelope of lambda_l0 is sqrt((2l+1)/(4 pi))
+        assert abs(lam[l] - want) < 5e-13 * np.sqrt((2 * l + 1) / FOURPI), l
+
+
+def test_rescaling_is_exact_where_unscaled_is_representable(oracle_mod):
+    # powers of two are exact: where the unscaled recurrence stays in the FP64
+    # normal range the tracked one must agree bit for bit, although it rescales
+    lmax = 300
+    for theta in (0.05, 0.2, 0.7):
+        x, s = np.cos(theta), np.sin(theta)
+        a = oracle_mod.lam(lmax, lmax, x, s, track=True)
+        b = oracle_mod.lam(lmax, lmax, x, s, track=False)
+        # an entry counts if it and every earlier entry of its m-column are
+        # normal numbers in the unscaled run
+        good = np.isfinite(b) & (np.abs(b) >= np.finfo(float).tiny)
+        ok = np.zeros_like(good)
+        for m in range(lmax + 1):
+            i0 = inputs.alm_index(m, m, lmax)
+            col = good[i0: i0 + lmax + 1 - m]
+            ok[i0: i0 + lmax + 1 - m] = np.cumprod(col).astype(bool)
+        assert ok.sum() > 1000
+        np.testing.assert_array_equal(a[ok], b[ok])
+    # and at theta = 0.05 the tracked path did rescale (lambda_mm < 2^-400 there)
+    lam = oracle_mod.lam(lmax, lmax, np.cos(0.05), np.sin(0.05), track=False)
+    assert np.min(np.abs(lam[lam != 0])) < 2.0 ** -400
+
+
+def test_tracking_needed_and_sound_at_poles(oracle_mod):
+    theta = 5.6e-4
+    raw = oracle_mod.lam(2048, 2048, np.cos(theta), np.sin(theta), track=False)
+    trk = oracle_mod.lam(2048, 2048, np.cos(theta), np.sin(theta), track=True)
+    # the untracked recurrence loses the large-m columns entirely (all zero)
+    ls, ms = inputs.lm_arrays(2048, 2048)
+    sel = (ms == 300) & (ls == 2048)
+    assert raw[sel][0] == 0.0
+    assert np.all(np.isfinite(trk))
+
+
+# ----------------------------------------------------------- ring synthesis --
+
+def _scipy_map(grid, lmax, mmax, alm):
+    from scipy.special import sph_harm_y
+    theta = np.arccos(np.clip(grid["x"], -1, 1))
+    out = np.zeros(grid["npix"])
+    ls, ms = inputs.lm_arrays(lmax, mmax)
+    for r in range(grid["nrings"]):
+        n = grid["nphi"][r]
+        phi = grid["phi0"][r] + 2 * np.pi * np.arange(n) / n
+        acc = np.zeros(n)
+        for i, (l, m) in enumerate(zip(ls, ms)):
+            y = sph_harm_y(int(l), int(m), theta[r], phi)
+            if m == 0:
+                acc += alm[i].real * y.real
+            else:
+                acc += 2.0 * (alm[i] * y).real
+        out[grid["ofs"][r]: grid["ofs"][r] + n] = acc
+    return out
+
+
+@pytest.mark.parametrize("case", [("hp", 1, 8, 8), ("hp", 2, 8, 8), ("hp", 4, 8, 5),
+                                  ("hp", 2, 3, 3), ("gl", (8, 16), 7, 7), ("gl", (9, 15), 7, 3)])
+def test_alm2map_brute_force_scipy(oracle_mod, case):
+    kind, size, lmax, mmax = case
+    grid = oracle_mod.healpix_grid(size) if kind == "hp" else oracle_mod.gl_grid(*size)
+    alm = inputs.gaussian_alm(lmax, mmax, 11, spectrum="white")[0]
+    got = oracle_mod.alm2map(grid, lmax, mmax, alm)[0]
+    want = _scipy_map(grid, lmax, mmax, alm)
+    assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def test_alm2map_generic_rings_brute_force(oracle_mod):
+    theta = np.array([0.1, 0.8, 1.3, 2.2, 3.0])
+    nphi = np.array([5, 9, 12, 7, 3])
+    phi0 = np.array([0.3, -0.2, 0.0, 1.7, 0.05])
+    grid = oracle_mod.rings_grid(theta, nphi, phi0)
+    alm = inputs.gaussian_alm(6, 6, 12, spectrum="white")[0]
+    got = oracle_mod.alm2map(grid, 6, 6, alm)[0]
+    want = _scipy_map(grid, 6, 6, alm)
+    assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def test_ring_sum_matches_numpy_fft(oracle_mod):
+    # Delta_m from the oracle's lambda, folded onto the n_phi bins with the
+    # e^{i m phi0} shift and transformed with numpy's inverse FFT
+    nside, lmax = 4, 20                 # n_phi <= 16 < 2 lmax + 1: aliasing active
+    grid = oracle_mod.healpix_grid(nside)
+    alm = inputs.gaussian_alm(lmax, lmax, 13, spectrum="white")[0]
+    got = oracle_mod.alm2map(grid, lmax, lmax, alm)[0]
+    ls, ms = inputs.lm_arrays(lmax, lmax)
+    for r in range(grid["nrings"]):
+        lam = oracle_mod.lam(lmax, lmax, grid["x"][r], grid["st"][r])
+        delta = np.bincount(ms, weights=(alm * lam).real, minlength=lmax + 1) + \
+            1j * np.bincount(ms, weights=(alm * lam).imag, minlength=lmax + 1)
+        delta[0] = delta[0].real
+        n = grid["nphi"][r]
+        spec = np.zeros(n, dtype=complex)
+        for m in range(lmax + 1):
+            c = delta[m] * np.exp(1j * m * grid["phi0"][r])
+            spec[m % n] += c
+            if m > 0:
+                spec[(-m) % n] += np.conj(c)
+        want = (np.fft.ifft(spec) * n).real
+        seg = got[grid["ofs"][r]: grid["ofs"][r] + n]
+        assert np.max(np.abs(seg - want)) < 1e-13 * max(1.0, np.max(np.abs(want)))
+
+
+def test_ring_subset_equals_full(oracle_mod):
+    grid = oracle_mod.healpix_grid(8)
+    alm = inputs.batch_alm(16, 16, 14, 2, spectrum="white")
+    full = oracle_mod.alm2map(grid, 16, 16, alm)
+    rings = np.array([0, 5, 15, 30], dtype=np.int32)
+    sub = oracle_mod.alm2map(grid, 16, 16, alm, rings=rings)
+    for r in rings:
+        sl = slice(grid["ofs"][r], grid["ofs"][r] + grid["nphi"][r])
+        np.testing.assert_array_equal(sub[:, sl], full[:, sl])
+    assert np.isnan(sub[0, grid["ofs"][1]])
+
+
+def test_gl_round_trip_identity(oracle_mod):
+    # Gauss-Legendre quadrature with n_rings = lmax + 1 and n_phi > 2 lmax is
+    # exact for band-limited fields: a' = sum w_r (2 pi / n_phi) s Y* = a
+    lmax = 127
+    grid = oracle_mod.gl_grid(128, 256)
+    alm = inputs.gaussian_alm(lmax, lmax, 1, spectrum="white")[0]
+    s = oracle_mod.alm2map(grid, lmax, lmax, alm)[0]
+    y = s.copy()
+    for r in range(grid["nrings"]):
+        sl = slice(grid["ofs"][r], grid["ofs"][r] + grid["nphi"][r])
+        y[sl] *= grid["w"][r] * 2 * np.pi / grid["nphi"][r]
+    g = oracle_mod.map2alm_adjoint(grid, lmax, lmax, y)[0]
+    ls, ms = inputs.lm_arrays(lmax, lmax)
+    back = g / np.where(ms == 0, 1.0, 2.0)
+    want = alm.copy()
+    want[ms == 0] = want[ms == 0].real
+    assert np.max(np.abs(back - want)) < 1e-12 * np.max(np.abs(want))
+
+
+# ------------------------------------------------------------------ adjoint --
+
+@pytest.mark.parametrize("grid_args", [("hp", 4), ("gl", (10, 21)), ("hp", 2)])
+def test_adjoint_dot_product(oracle_mod, grid_args):
+    kind, size = grid_args
+    grid = oracle_mod.healpix_grid(size) if kind == "hp" else oracle_mod.gl_grid(*size)
+    lmax, mmax = 12, 9
+    a = inputs.gaussian_alm(lmax, mmax, 21, spectrum="white")[0]
+    y = inputs.gaussian_map(grid["npix"], 22)[0]
+    ya = oracle_mod.alm2map(grid, lmax, mmax, a)[0]
+    g = oracle_mod.map2alm_adjoint(grid, lmax, mmax, y)[0]
+    lhs = np.dot(ya, y)
+    _, ms = inputs.lm_arrays(lmax, mmax)
+    a_eff = np.where(ms == 0, a.real + 0j, a)
+    rhs = np.sum(a_eff.real * g.real + a_eff.imag * g.imag)
+    assert abs(lhs - rhs) < 1e-12 * (np.linalg.norm(ya) * np.linalg.norm(y))
+    assert np.all(g[ms == 0].imag == 0)
+
+
+def test_adjoint_brute_force_matrix(oracle_mod):
+    # the explicit real matrix of alm2map, built column by column from scipy's
+    # Y_lm; its transpose applied to y is the oracle's adjoint
+    grid = oracle_mod.healpix_grid(2)
+    lmax = mmax = 4
+    n = inputs.nalm(lmax, mmax)
+    ls, ms = inputs.lm_arrays(lmax, mmax)
+    cols = []
+    for i in range(n):
+        e = np.zeros(n, complex)
+        e[i] = 1.0
+        cols.append(_scipy_map(grid, lmax, mmax, e))
+        e[i] = 1j
+        cols.append(_scipy_map(grid, lmax, mmax, e))
+    A = np.stack(cols, axis=1)                   # (npix, 2 n): [Re a_0, Im a_0, ...]
+    y = inputs.gaussian_map(grid["npix"], 23)[0]
+    gt = A.T @ y
+    g = oracle_mod.map2alm_adjoint(grid, lmax, mmax, y)[0]
+    np.testing.assert_allclose(g.real, gt[0::2], atol=1e-13)
+    np.testing.assert_allclose(g.imag, gt[1::2], atol=1e-13)
+
+
+def test_adjoint_m_subset_equals_full(oracle_mod):
+    grid = oracle_mod.gl_grid(12, 25)
+    y = inputs.gaussian_map(grid["npix"], 24, nmaps=2)
+    full = oracle_mod.map2alm_adjoint(grid, 11, 11, y)
+    sub = oracle_mod.map2alm_adjoint(grid, 11, 11, y, ms=[0, 3, 11])
+    _, ms = inputs.lm_arrays(11, 11)
+    sel = np.isin(ms, [0, 3, 11])
+    np.testing.assert_allclose(sub[:, sel], full[:, sel], rtol=1e-13, atol=1e-14)
+    assert np.all(np.isnan(sub[:, ~sel].real))
+
+
+def test_map_variance_matches_spectrum(oracle_mod):
+    # weak statistical check: <s^2> = sum_l (2l+1) C_l / (4 pi)
+    lmax = 64
+    grid = oracle_mod.healpix_grid(32)
+    alm = inputs.batch_alm(lmax, lmax, 25, 4)
+    s = oracle_mod.alm2map(grid, lmax, lmax, alm)
+    l = np.arange(2, lmax + 1)
+    want = np.sum((2 * l + 1) / (l * (l + 1.0))) / FOURPI
+    assert abs(np.mean(s * s) / want - 1) < 0.15
