@@ -1,0 +1,122 @@
+/*
+ * sht.h -- C ABI of libsht: the inverse spherical harmonic transform
+ * (alm2map) and its real-linear transpose on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Hupca, Falcou, Grigori, Stompor, "Spherical harmonic transform with
+ * GPUs" (INRIA RR-7409).  alm2map evaluates Eq. alm2mapDef,
+ *     s(theta, phi) = sum_{l <= lmax} sum_{|m| <= l} a_lm Y_lm(theta, phi),
+ * on an iso-latitude ring grid in the two steps of Algorithm 1: the Legendre
+ * step forms Delta_m(theta_r) of Eq. DeltaDef with the recurrence of
+ * Eq. assLegRec (starting values Eq. pmm / Eq. pm1m, rescaled against
+ * underflow as in Algorithm 2), and the ring step sums Eq. Delta2map with one
+ * FFT per ring (sec. 2.2.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Coefficients (alm): complex128, interleaved (re, im), m-major packed:
+ *     idx(l, m) = m (2 lmax + 3 - m) / 2 + (l - m),  0 <= m <= mmax, m <= l <= lmax,
+ *   nalm = (mmax + 1)(2 lmax + 2 - mmax) / 2 entries per map; map b of a batch
+ *   starts at entry b * nalm.  Y_lm = lambda_lm(cos theta) e^{i m phi} with
+ *   orthonormal lambda_lm including the Condon-Shortley sign (-1)^m.  The map
+ *   is real (sec. 2.1), so Im(a_l0) is ignored and a_{l,-m} = (-1)^m conj(a_lm)
+ *   is implied.
+ * Maps: real, RING order (rings north to south, pixels by increasing phi
+ *   within a ring); npix pixels per map, map b starts at pixel b * npix.
+ *   float64 for SHT_FP64, float32 for the tensor-core forms.
+ * Pointers named *_dev are device pointers on the plan's device; the caller
+ *   owns them and the library never frees them.  The library owns the plan,
+ *   its tables and its workspace (allocated at plan time or grown on first use
+ *   of a larger batch).
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Launches are asynchronous; calls on one plan must be ordered on
+ *   one stream (they share the plan's workspace).
+ * Errors: every int-returning call returns SHT_OK (0) or a negative code; the
+ *   calling thread's message is available from sht_last_error().  Bad
+ *   arguments are rejected before anything is launched.
+ */
+#ifndef SHT_H
+#define SHT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHT_OK 0
+#define SHT_EINVAL (-1)       /* bad argument (null pointer, size, kind) */
+#define SHT_ENOMEM (-2)       /* host or device allocation failed */
+#define SHT_ECUDA (-3)        /* a CUDA call failed */
+#define SHT_EUNSUPPORTED (-4) /* valid but not supported (e.g. ring too long) */
+#define SHT_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
+
+typedef struct sht_plan_s *sht_plan_t;
+
+typedef enum {
+    SHT_GRID_GL = 0,      /* Gauss-Legendre rings, nphi_gl equispaced pixels, phi0 = 0 */
+    SHT_GRID_HEALPIX = 1, /* HEALPix RING scheme (Gorski et al. 2005), 4 nside - 1 rings */
+    SHT_GRID_RINGS = 2    /* caller-given rings: theta, nphi, phi0 (copied at plan time) */
+} sht_grid_kind;
+
+typedef struct {
+    int kind;            /* sht_grid_kind */
+    int nside;           /* HEALPIX: nside >= 1 */
+    int nrings;          /* GL, RINGS: number of rings >= 1 */
+    int nphi_gl;         /* GL: pixels per ring >= 1 */
+    const double *theta; /* RINGS: host array [nrings], colatitudes in [0, pi] */
+    const int *nphi;     /* RINGS: host array [nrings], pixels per ring >= 1 */
+    const double *phi0;  /* RINGS: host array [nrings], azimuth of pixel 0 */
+} sht_grid;
+
+typedef enum {
+    SHT_FP64 = 0,      /* FP64 recurrence, FP64 contraction, FP64 ring FFT; float64 map */
+    SHT_FP32_TC = 1,   /* FP64 recurrence, 3xTF32 tensor-core contraction, FP32 ring FFT; float32 map */
+    SHT_BF16X3_TC = 2  /* FP64 recurrence, split-BF16 (hi/lo, 3 products) tensor-core contraction,
+                          FP32 ring FFT; float32 map */
+} sht_prec;
+
+/* Build a plan for grid g and band limits 0 <= mmax <= lmax on the current
+ * CUDA device: ring geometry, the recurrence coefficients of Eq. betaDef in
+ * the scaled form used by the kernels, the starting values lambda_mm of
+ * Eq. pmm with their binary exponents, and the ring-FFT twiddle tables.
+ * Limits: lmax <= 8192; every ring's nphi <= 8192.  On success *out holds the
+ * plan (free with sht_plan_destroy).  Errors: SHT_EINVAL, SHT_EUNSUPPORTED,
+ * SHT_ENOMEM, SHT_ECUDA. */
+int sht_plan(const sht_grid *g, int lmax, int mmax, sht_plan_t *out);
+
+/* Free a plan and its device memory (synchronises the plan's device).  NULL is a no-op. */
+int sht_plan_destroy(sht_plan_t plan);
+
+/* Sizes: coefficients per map, pixels per map, rings; 0 for a NULL plan. */
+size_t sht_nalm(sht_plan_t plan);
+size_t sht_npix(sht_plan_t plan);
+int sht_nrings(sht_plan_t plan);
+int sht_lmax(sht_plan_t plan);
+int sht_mmax(sht_plan_t plan);
+
+/* alm2map of one map (Eq. alm2mapDef via Eq. DeltaDef and Eq. Delta2map).
+ * alm_dev: nalm complex128 (device); map_dev: npix reals (device), fully
+ * overwritten.  prec: sht_prec (selects the map's float type). */
+int sht_alm2map(sht_plan_t plan, const void *alm_dev, void *map_dev, int prec, void *stream);
+
+/* Real-linear transpose of alm2map (Eq. map2almDef without quadrature weights):
+ *   g_lm = c_m sum_p y_p lambda_lm(theta_p) e^{-i m phi_p},  c_0 = 1, c_m = 2 (m > 0),
+ *   Im g_l0 = 0, so that <alm2map(a), y> = sum Re(a) Re(g) + Im(a) Im(g).
+ * map_dev: npix reals (float64; float32 for the tensor-core forms); alm_dev:
+ * nalm complex128, fully overwritten. */
+int sht_map2alm_adjoint(sht_plan_t plan, const void *map_dev, void *alm_dev, int prec, void *stream);
+
+/* Batched forms: nbatch >= 0 maps, strides nalm and npix.  nbatch == 0 is a no-op. */
+int sht_alm2map_batch(sht_plan_t plan, int nbatch, const void *alm_dev, void *map_dev,
+                      int prec, void *stream);
+int sht_map2alm_adjoint_batch(sht_plan_t plan, int nbatch, const void *map_dev, void *alm_dev,
+                              int prec, void *stream);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *sht_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H */

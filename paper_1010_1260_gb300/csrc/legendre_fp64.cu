@@ -1,0 +1,180 @@
+// Legendre step in FP64: Delta_m(theta_r) = sum_{l >= m} a_lm lambda_lm(cos theta_r)
+// (Eq. DeltaDef) for every order m and ring r.
+//
+// Mapping (GB300): one CTA per (ring-pair block of 128, m, map group).  Each
+// thread owns one pair of mirrored rings and walks l = m..lmax sequentially
+// (the recurrence of Eq. assLegRec is serial in l).  The per-l data shared by
+// the CTA -- the recurrence coefficient A_{l+1} and the prescaled
+// coefficients C_l a_lm of the CTA's maps -- is staged through shared memory
+// in chunks of 64 l with coalesced loads and read back as broadcasts.
+//
+// Recurrence form.  With lambda_l = C_l p_l, C_m = C_{m+1} = 1 and
+// C_l = (beta_l / beta_{l-1}) C_{l-2}, the normalised recurrence
+//     lambda_l = beta_l (x lambda_{l-1} - lambda_{l-2} / beta_{l-1})
+// becomes p_l = A_l x p_{l-1} - p_{l-2} with A_l = beta_{l-1} C_{l-1} / C_{l-2}
+// (A_{m+1} = sqrt(2m+3), Eq. pm1m): one multiply and one FMA per step.
+//
+// North/south symmetry (sec. 2.2.1): lambda_lm(-x) = (-1)^(l-m) lambda_lm(x),
+// so the even-(l-m) and odd-(l-m) partial sums E, O of the northern ring give
+// Delta_m(north) = E + O and Delta_m(south) = E - O.
+//
+// Exponent tracking (Algorithm 2): the start value lambda_mm comes with an
+// exponent k <= 0 (value = p * 2^(512 k)); while k < 0 the thread rescales
+// when |p| > 2^256 and contributes nothing (the true value is < 2^-256).
+#include "sht_internal.cuh"
+
+namespace sht {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kChunk = 64;  // even, so every chunk starts on an even (l - m)
+
+__device__ __forceinline__ bool above_hi(double v)
+{
+    // |v| > 2^kScaleHi, tested on the exponent bits (integer pipe)
+    const int e = (__double2hiint(v) >> 20) & 0x7ff;
+    return e > 1023 + kScaleHi;
+}
+
+template <int BC>
+__global__ void __launch_bounds__(kThreads)
+legendre_fwd_fp64_kernel(const DevPlan P, const double2 *__restrict__ alm,
+                         double2 *__restrict__ delta, int nmaps)
+{
+    const int m = blockIdx.y;
+    const int L = P.lmax;
+    const int pair = blockIdx.x * kThreads + threadIdx.x;
+    const int b0 = blockIdx.z * BC;
+    const bool live = pair < P.npairs;
+
+    __shared__ double sA[kChunk];        // A_{l+1} for l in the chunk
+    __shared__ double2 sa[kChunk][BC];   // C_l a_lm for the CTA's maps
+
+    double x = 0.0, p0 = 0.0, p1 = 0.0;
+    int k = 0;
+    if (live) {
+        x = P.pair_x[pair];
+        p1 = P.start_v[(size_t)m * P.npairs + pair];
+        k = P.start_k[(size_t)m * P.npairs + pair];
+    }
+    double er[BC], ei[BC], orr[BC], oi[BC];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) er[b] = ei[b] = orr[b] = oi[b] = 0.0;
+
+    const long long mofs = (long long)m * (2 * L + 3 - m) / 2;  // packed index of (m, m)
+
+    for (int l0 = m; l0 <= L; l0 += kChunk) {
+        const int cnt = min(kChunk, L + 1 - l0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += kThreads) {
+            const int l = l0 + i;
+            sA[i] = (l + 1 <= L) ? P.coefA[mofs + (l + 1 - m)] : 0.0;
+        }
+        for (int i = threadIdx.x; i < cnt * BC; i += kThreads) {
+            const int b = i / cnt;
+            const int j = i - b * cnt;
+            const long long q = mofs + (l0 - m) + j;
+            const double c = P.coefC[q];
+            double2 a = make_double2(0.0, 0.0);
+            if (b0 + b < nmaps) a = alm[(size_t)(b0 + b) * P.nalm + q];
+            if (m == 0) a.y = 0.0;  // real field: Im(a_l0) is ignored
+            sa[j][b] = make_double2(c * a.x, c * a.y);
+        }
+        __syncthreads();
+
+        const bool slow = __any_sync(0xffffffffu, k < 0);
+        if (!slow) {
+            int j = 0;
+            for (; j + 1 < cnt; j += 2) {
+                // even (l - m): E
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    er[b] = fma(p1, sa[j][b].x, er[b]);
+                    ei[b] = fma(p1, sa[j][b].y, ei[b]);
+                }
+                double t = fma(sA[j] * x, p1, -p0);
+                p0 = p1;
+                p1 = t;
+                // odd (l - m): O
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    orr[b] = fma(p1, sa[j + 1][b].x, orr[b]);
+                    oi[b] = fma(p1, sa[j + 1][b].y, oi[b]);
+                }
+                t = fma(sA[j + 1] * x, p1, -p0);
+                p0 = p1;
+                p1 = t;
+            }
+            if (j < cnt) {  // last l of the band, even (l - m)
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    er[b] = fma(p1, sa[j][b].x, er[b]);
+                    ei[b] = fma(p1, sa[j][b].y, ei[b]);
+                }
+                const double t = fma(sA[j] * x, p1, -p0);
+                p0 = p1;
+                p1 = t;
+            }
+        } else {
+            for (int j = 0; j < cnt; ++j) {
+                if (k == 0) {
+                    if ((j & 1) == 0) {
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) {
+                            er[b] = fma(p1, sa[j][b].x, er[b]);
+                            ei[b] = fma(p1, sa[j][b].y, ei[b]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) {
+                            orr[b] = fma(p1, sa[j][b].x, orr[b]);
+                            oi[b] = fma(p1, sa[j][b].y, oi[b]);
+                        }
+                    }
+                }
+                const double t = fma(sA[j] * x, p1, -p0);
+                p0 = p1;
+                p1 = t;
+                if (k < 0 && above_hi(p1)) {
+                    p1 *= 0x1p-512;
+                    p0 *= 0x1p-512;
+                    k += 1;
+                }
+            }
+        }
+    }
+
+    if (!live) return;
+    const int2 rr = P.pair_ring[pair];
+    const int M1 = P.mmax + 1;
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+        if (b0 + b >= nmaps) break;
+        double2 *d = delta + (size_t)(b0 + b) * P.nrings * M1;
+        d[(size_t)rr.x * M1 + m] = make_double2(er[b] + orr[b], ei[b] + oi[b]);
+        if (rr.y >= 0) d[(size_t)rr.y * M1 + m] = make_double2(er[b] - orr[b], ei[b] - oi[b]);
+    }
+}
+
+template <int BC>
+cudaError_t launch_bc(const DevPlan &P, const double2 *alm, double2 *delta, int nmaps,
+                      cudaStream_t st)
+{
+    dim3 grid((P.npairs + kThreads - 1) / kThreads, P.mmax + 1, (nmaps + BC - 1) / BC);
+    legendre_fwd_fp64_kernel<BC><<<grid, kThreads, 0, st>>>(P, alm, delta, nmaps);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, double2 *delta,
+                                     int nmaps, cudaStream_t st)
+{
+    if (nmaps <= 0) return cudaSuccess;
+    if (nmaps >= 8) return launch_bc<8>(P, alm, delta, nmaps, st);
+    if (nmaps >= 4) return launch_bc<4>(P, alm, delta, nmaps, st);
+    if (nmaps >= 2) return launch_bc<2>(P, alm, delta, nmaps, st);
+    return launch_bc<1>(P, alm, delta, nmaps, st);
+}
+
+}  // namespace sht

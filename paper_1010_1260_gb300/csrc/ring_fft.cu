@@ -1,0 +1,322 @@
+// Ring step of alm2map (Eq. Delta2map, sec. 2.2.2): for every ring r,
+//   s_r(j) = sum_{m=-M..M} Delta_m(r) e^{i m (phi0_r + 2 pi j / n)},  n = n_phi(r),
+// with Delta_{-m} = conj(Delta_m).  Steps, all inside one CTA per (ring, map):
+//   1. phase shift and fold: F_k = sum_{m = k mod n} Delta_m e^{i m phi0}
+//      + sum_{m >= 1, -m = k mod n} conj(Delta_m e^{i m phi0}) for k = 0..n/2
+//      (modes beyond the ring's Nyquist frequency alias onto its bins; the
+//      paper defers this "wrapping" to Gorski et al. 2005);
+//   2. real inverse DFT of length n.  For even n it runs as one complex DFT of
+//      length h = n/2: Z_k = (F_k + conj F_{h-k}) + i w^k (F_k - conj F_{h-k}),
+//      w = e^{2 pi i / n}, z = IDFT_h(Z), s_{2j} = Re z_j, s_{2j+1} = Im z_j.
+//      Odd n runs the full-length complex DFT of the Hermitian spectrum.
+//   3. the complex DFT is a self-sorting (Stockham) mixed-radix transform in
+//      shared memory, ping-ponging between two buffers: radix 4, 2, 3, 5
+//      butterflies, and a direct pass for any other prime factor.
+// Twiddles come from per-plan tables T_n[q] = e^{i pi q / n}, q < 2n, one per
+// distinct ring length; HEALPix and Gauss-Legendre rings have
+// phi0 = pi * ps / n with an integer ps, so e^{i m phi0} = T_n[(m ps) mod 2n].
+#include "sht_internal.cuh"
+
+namespace sht {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename R> struct C2T;
+template <> struct C2T<double> { using type = double2; };
+template <> struct C2T<float> { using type = float2; };
+
+template <typename R>
+__device__ __forceinline__ typename C2T<R>::type mk(R x, R y)
+{
+    typename C2T<R>::type c;
+    c.x = x;
+    c.y = y;
+    return c;
+}
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    C c;
+    c.x = a.x * b.x - a.y * b.y;
+    c.y = a.x * b.y + a.y * b.x;
+    return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b)
+{
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+template <typename C> __device__ __forceinline__ C csub(C a, C b)
+{
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a)
+{
+    a.y = -a.y;
+    return a;
+}
+// multiply by +i
+template <typename C> __device__ __forceinline__ C cmuli(C a)
+{
+    C c;
+    c.x = -a.y;
+    c.y = a.x;
+    return c;
+}
+
+template <typename R> __device__ __forceinline__ const typename C2T<R>::type *tw_table(const DevPlan &P);
+template <> __device__ __forceinline__ const double2 *tw_table<double>(const DevPlan &P) { return P.tw64; }
+template <> __device__ __forceinline__ const float2 *tw_table<float>(const DevPlan &P) { return P.tw32; }
+
+// Factor N into radices: 4s first, then 2, 3, 5, then remaining primes.
+__device__ int factorize(int N, int *rad)
+{
+    int np = 0;
+    while (N % 4 == 0) { rad[np++] = 4; N /= 4; }
+    while (N % 2 == 0) { rad[np++] = 2; N /= 2; }
+    while (N % 3 == 0) { rad[np++] = 3; N /= 3; }
+    while (N % 5 == 0) { rad[np++] = 5; N /= 5; }
+    for (int p = 7; N > 1; p += 2) {
+        while (N % p == 0) { rad[np++] = p; N /= p; }
+        if (p * p > N && N > 1) { rad[np++] = N; N = 1; }
+    }
+    return np;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ delta,
+                  R *__restrict__ map)
+{
+    using C = typename C2T<R>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + P.fft_cap;
+    __shared__ int s_rad[32];
+    __shared__ int s_np;
+
+    const int r = blockIdx.x;
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int n = P.nphi[r];
+    const int M = P.mmax;
+    const C *D = delta + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
+    const C *T = tw_table<R>(P) + P.twofs[r];  // T[q] = e^{i pi q / n}, q < 2n
+    const int ps = P.ps[r];
+    const double phi0 = P.phi0[r];
+    const bool even = (n % 2) == 0;
+    const int N = even ? n / 2 : n;                 // complex DFT length
+    const int nb = even ? n / 2 + 1 : (n - 1) / 2 + 1;  // half-spectrum bins
+    const int tstep = even ? 4 : 2;                 // T index of w_N^1
+
+    if (tid == 0) s_np = factorize(N, s_rad);
+
+    // 1. phase shift + fold onto the half spectrum, into buf1[0..nb)
+    for (int k = tid; k < nb; k += kThreads) {
+        C acc = mk<R>(0, 0);
+        for (int m = k; m <= M; m += n) {
+            C ph;
+            if (ps >= 0) {
+                ph = T[(int)(((long long)m * ps) % (2 * n))];
+            } else {
+                double s, c;
+                sincos((double)m * phi0, &s, &c);
+                ph = mk<R>((R)c, (R)s);
+            }
+            acc = cadd(acc, cmul(D[m], ph));
+        }
+        for (int m = n - k; m <= M; m += n) {
+            if (m < 1) continue;
+            C ph;
+            if (ps >= 0) {
+                ph = T[(int)(((long long)m * ps) % (2 * n))];
+            } else {
+                double s, c;
+                sincos((double)m * phi0, &s, &c);
+                ph = mk<R>((R)c, (R)s);
+            }
+            acc = cadd(acc, cconj(cmul(D[m], ph)));
+        }
+        buf1[k] = acc;
+    }
+    __syncthreads();
+
+    // 2. spectrum of the complex DFT, into buf0[0..N)
+    if (even) {
+        for (int k = tid; k < N; k += kThreads) {
+            const C f = buf1[k];
+            const C g = cconj(buf1[N - k]);
+            const C w = T[2 * k];  // e^{2 pi i k / n}
+            buf0[k] = cadd(cadd(f, g), cmuli(cmul(w, csub(f, g))));
+        }
+    } else {
+        for (int k = tid; k < N; k += kThreads) buf0[k] = (k < nb) ? buf1[k] : cconj(buf1[N - k]);
+    }
+    __syncthreads();
+
+    // 3. Stockham passes, inverse sign: Y[(j/Ns) Ns R + j%Ns + q Ns] =
+    //    sum_r X[j + r N/R] w_{Ns R}^{r (j%Ns)} w_R^{r q}
+    C *src = buf0;
+    C *dst = buf1;
+    int Ns = 1;
+    const int npass = s_np;
+    for (int pi = 0; pi < npass; ++pi) {
+        const int Rr = s_rad[pi];
+        const int NR = N / Rr;
+        const int tscale = N / (Ns * Rr);  // w_{Ns R}^e = w_N^{e tscale}
+        if (Rr == 2) {
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR];
+                if (kk) v1 = cmul(v1, T[(kk * tscale) % N * tstep]);
+                const int o = (j / Ns) * Ns * 2 + kk;
+                dst[o] = cadd(v0, v1);
+                dst[o + Ns] = csub(v0, v1);
+            }
+        } else if (Rr == 4) {
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+                    v1 = cmul(v1, T[(e % N) * tstep]);
+                    v2 = cmul(v2, T[((2 * e) % N) * tstep]);
+                    v3 = cmul(v3, T[((3 * e) % N) * tstep]);
+                }
+                // inverse radix-4: w_4 = +i
+                const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
+                const C a2 = cadd(v1, v3), a3 = cmuli(csub(v1, v3));
+                const int o = (j / Ns) * Ns * 4 + kk;
+                dst[o] = cadd(a0, a2);
+                dst[o + Ns] = cadd(a1, a3);
+                dst[o + 2 * Ns] = csub(a0, a2);
+                dst[o + 3 * Ns] = csub(a1, a3);
+            }
+        } else if (Rr == 3) {
+            const R c3 = (R)-0.5;
+            const R s3 = (R)0.86602540378443864676372317075294;  // sin(2 pi / 3)
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+                    v1 = cmul(v1, T[(e % N) * tstep]);
+                    v2 = cmul(v2, T[((2 * e) % N) * tstep]);
+                }
+                const C t1 = cadd(v1, v2);
+                const C t2 = csub(v1, v2);
+                const C m1 = mk<R>(v0.x + c3 * t1.x, v0.y + c3 * t1.y);
+                const C m2 = mk<R>(-s3 * t2.y, s3 * t2.x);  // i s3 (v1 - v2)
+                const int o = (j / Ns) * Ns * 3 + kk;
+                dst[o] = cadd(v0, t1);
+                dst[o + Ns] = cadd(m1, m2);
+                dst[o + 2 * Ns] = csub(m1, m2);
+            }
+        } else if (Rr == 5) {
+            const R c1 = (R)0.30901699437494742410229341718282;   // cos(2 pi / 5)
+            const R c2 = (R)-0.80901699437494742410229341718282;  // cos(4 pi / 5)
+            const R s1 = (R)0.95105651629515357211643933337938;   // sin(2 pi / 5)
+            const R s2 = (R)0.58778525229247312916870595463907;   // sin(4 pi / 5)
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR],
+                  v4 = src[j + 4 * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+                    v1 = cmul(v1, T[(e % N) * tstep]);
+                    v2 = cmul(v2, T[((2 * e) % N) * tstep]);
+                    v3 = cmul(v3, T[((3 * e) % N) * tstep]);
+                    v4 = cmul(v4, T[((4 * e) % N) * tstep]);
+                }
+                const C a1 = cadd(v1, v4), b1 = csub(v1, v4);
+                const C a2 = cadd(v2, v3), b2 = csub(v2, v3);
+                const C m1 = mk<R>(v0.x + c1 * a1.x + c2 * a2.x, v0.y + c1 * a1.y + c2 * a2.y);
+                const C m2 = mk<R>(v0.x + c2 * a1.x + c1 * a2.x, v0.y + c2 * a1.y + c1 * a2.y);
+                // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
+                const C n1 = mk<R>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
+                const C n2 = mk<R>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
+                const int o = (j / Ns) * Ns * 5 + kk;
+                dst[o] = cadd(v0, cadd(a1, a2));
+                dst[o + Ns] = cadd(m1, n1);
+                dst[o + 2 * Ns] = cadd(m2, n2);
+                dst[o + 3 * Ns] = csub(m2, n2);
+                dst[o + 4 * Ns] = csub(m1, n1);
+            }
+        } else {
+            // direct pass for a general prime radix: one thread per output,
+            // Y[o + q Ns] = sum_r X[j + r NR] w_N^{r (kk tscale + q NR)}
+            for (int t = tid; t < N; t += kThreads) {
+                const int j = t % NR;
+                const int q = t / NR;
+                const int kk = j % Ns;
+                const int e = (kk * tscale + q * NR) % N;
+                C acc = src[j];
+                int idx = e;
+                for (int rr = 1; rr < Rr; ++rr) {
+                    acc = cadd(acc, cmul(src[j + rr * NR], T[idx * tstep]));
+                    idx += e;
+                    if (idx >= N) idx -= N;
+                }
+                dst[(j / Ns) * Ns * Rr + kk + q * Ns] = acc;
+            }
+        }
+        __syncthreads();
+        C *tmp = src;
+        src = dst;
+        dst = tmp;
+        Ns *= Rr;
+    }
+
+    // 4. store the ring
+    R *out = map + (size_t)b * P.npix + P.ofs[r];
+    if (even) {
+        for (int j = tid; j < N; j += kThreads) {
+            const C z = src[j];
+            out[2 * j] = z.x;
+            out[2 * j + 1] = z.y;
+        }
+    } else {
+        for (int j = tid; j < N; j += kThreads) out[j] = src[j].x;
+    }
+}
+
+template <typename R>
+cudaError_t launch_synth(const DevPlan &P, const typename C2T<R>::type *delta, R *map, int nmaps,
+                         cudaStream_t st)
+{
+    if (nmaps <= 0) return cudaSuccess;
+    const size_t smem = ring_smem_bytes(P, sizeof(R) == 8);
+    auto kern = ring_synth_kernel<R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(P.nrings, nmaps);
+    kern<<<grid, kThreads, smem, st>>>(P, delta, map);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t ring_smem_bytes(const DevPlan &P, bool fp64)
+{
+    return ring_smem_bytes_for_cap(P.fft_cap, fp64);
+}
+
+cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps,
+                                   cudaStream_t st)
+{
+    return launch_synth<double>(P, delta, map, nmaps, st);
+}
+
+cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float *map, int nmaps,
+                                   cudaStream_t st)
+{
+    return launch_synth<float>(P, delta, map, nmaps, st);
+}
+
+}  // namespace sht

@@ -1,0 +1,524 @@
+// libsht C ABI: plans (ring geometry, recurrence tables, twiddle tables) and
+// the alm2map / map2alm_adjoint entry points declared in include/sht.h.
+#include "sht.h"
+#include "sht_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using sht::DevPlan;
+
+struct sht_plan_s {
+    int device = 0;
+    int kind = 0, lmax = 0, mmax = 0, nrings = 0, npairs = 0;
+    long long nalm = 0, npix = 0;
+    DevPlan dp{};
+    std::vector<void *> allocs;
+    void *ws = nullptr;  // Delta workspace
+    size_t ws_bytes = 0;
+    std::mutex mu;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SHT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+constexpr int kMaxL = 8192;
+constexpr int kMaxNphi = 8192;
+constexpr size_t kMaxDynSmem = 227 * 1024 - 1024;  // per-CTA opt-in limit minus static use
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------------- geometry --
+
+struct Rings {
+    std::vector<double> x, s, phi0;
+    std::vector<int> nphi, ps;
+};
+
+// Gauss-Legendre nodes by Newton iteration on P_n, northern half only and
+// mirrored, so that the southern ring of each pair is exactly -x.
+void gl_geometry(int n, int nphi, Rings &R)
+{
+    R.x.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double pa = 1.0, pb = z;  // P_{j-1}, P_j
+            for (int j = 2; j <= n; ++j) {
+                const double pc = ((2.0 * j - 1.0) * z * pb - (j - 1.0) * pa) / j;
+                pa = pb;
+                pb = pc;
+            }
+            const double pn = (n == 1) ? z : pb;
+            const double pn1 = (n == 1) ? 1.0 : pa;
+            const double dp = n * (z * pn - pn1) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        R.x[i] = z;
+        R.x[n - 1 - i] = -z;
+    }
+    if (n % 2) R.x[n / 2] = 0.0;
+    R.s.resize(n);
+    for (int i = 0; i < n; ++i) R.s[i] = std::sqrt((1.0 - R.x[i]) * (1.0 + R.x[i]));
+    R.nphi.assign(n, nphi);
+    R.phi0.assign(n, 0.0);
+    R.ps.assign(n, 0);
+}
+
+// HEALPix RING geometry (Gorski et al. 2005): polar-cap ring i < nside at
+// z = 1 - i^2 / (3 nside^2) with 4 i pixels starting at phi = pi / (4 i);
+// equatorial ring nside <= i <= 3 nside at z = 4/3 - 2 i / (3 nside) with
+// 4 nside pixels starting at phi = (pi / (4 nside)) ((i - nside + 1) mod 2).
+// The southern hemisphere is the exact mirror of the northern one.
+void healpix_geometry(int nside, Rings &R)
+{
+    const int nr = 4 * nside - 1;
+    const double dn = (double)nside;
+    R.x.assign(nr, 0.0);
+    R.s.assign(nr, 0.0);
+    R.nphi.assign(nr, 0);
+    R.phi0.assign(nr, 0.0);
+    R.ps.assign(nr, 0);
+    for (int i = 1; i <= 2 * nside; ++i) {
+        double z, s, p0;
+        int np, ps;
+        if (i < nside) {
+            const double omz = (double)i * (double)i / (3.0 * dn * dn);
+            z = 1.0 - omz;
+            s = std::sqrt(omz * (2.0 - omz));
+            np = 4 * i;
+            ps = 1;
+            p0 = kPi / (4.0 * i);
+        } else {
+            z = 4.0 / 3.0 - 2.0 * i / (3.0 * dn);
+            s = std::sqrt((1.0 - z) * (1.0 + z));
+            np = 4 * nside;
+            ps = (i - nside + 1) % 2;
+            p0 = (kPi / (2.0 * dn)) * (0.5 * ps);
+        }
+        const int rn = i - 1, rs = nr - i;
+        R.x[rn] = z;
+        R.s[rn] = s;
+        R.nphi[rn] = np;
+        R.ps[rn] = ps;
+        R.phi0[rn] = p0;
+        if (rs != rn) {
+            R.x[rs] = -z;
+            R.s[rs] = s;
+            R.nphi[rs] = np;
+            R.ps[rs] = ps;
+            R.phi0[rs] = p0;
+        }
+    }
+    R.x[2 * nside - 1] = 0.0;  // equator
+    R.s[2 * nside - 1] = 1.0;
+}
+
+// ----------------------------------------------------------------- tables --
+
+template <typename T>
+int upload(sht_plan_s *p, const std::vector<T> &h, const T **out)
+{
+    *out = nullptr;
+    if (h.empty()) return SHT_OK;
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, h.size() * sizeof(T));
+    if (e != cudaSuccess) return fail(SHT_ENOMEM, "cudaMalloc(%zu): %s", h.size() * sizeof(T),
+                                      cudaGetErrorString(e));
+    p->allocs.push_back(d);
+    e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    *out = static_cast<const T *>(d);
+    return SHT_OK;
+}
+
+void free_plan(sht_plan_s *p)
+{
+    if (!p) return;
+    {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        for (void *d : p->allocs) cudaFree(d);
+        if (p->ws) cudaFree(p->ws);
+    }
+    delete p;
+}
+
+inline long long mofs(int lmax, int m) { return (long long)m * (2LL * lmax + 3 - m) / 2; }
+
+int build_tables(sht_plan_s *p, const Rings &R)
+{
+    const int L = p->lmax, M = p->mmax, nr = p->nrings;
+    // ring pairs
+    std::vector<double> px;
+    std::vector<double> pss;
+    std::vector<int2> pr;
+    if (p->kind == SHT_GRID_RINGS) {
+        for (int r = 0; r < nr; ++r) {
+            px.push_back(R.x[r]);
+            pss.push_back(R.s[r]);
+            pr.push_back(make_int2(r, -1));
+        }
+    } else {
+        for (int r = 0; r < nr / 2; ++r) {
+            px.push_back(R.x[r]);
+            pss.push_back(R.s[r]);
+            pr.push_back(make_int2(r, nr - 1 - r));
+        }
+        if (nr % 2) {
+            px.push_back(R.x[nr / 2]);
+            pss.push_back(R.s[nr / 2]);
+            pr.push_back(make_int2(nr / 2, -1));
+        }
+    }
+    const int np = (int)px.size();
+    p->npairs = np;
+
+    // lambda_mm = mu_m sin^m(theta) (Eq. pmm with the Condon-Shortley sign),
+    // carried as mantissa * 2^e and stored as (v, k): value = v * 2^(512 k)
+    std::vector<double> fm(M + 1, 0.0);
+    for (int m = 1; m <= M; ++m) fm[m] = -std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+    std::vector<double> sv((size_t)(M + 1) * np);
+    std::vector<int> sk((size_t)(M + 1) * np);
+    for (int q = 0; q < np; ++q) {
+        const double s = pss[q];
+        int e = 0;
+        double v = std::frexp(1.0 / std::sqrt(4.0 * kPi), &e);
+        for (int m = 0; m <= M; ++m) {
+            if (m > 0) {
+                v = v * s * fm[m];
+                int de = 0;
+                v = std::frexp(v, &de);
+                e += de;
+            }
+            double vv;
+            int kk;
+            if (v == 0.0) {
+                vv = 0.0;
+                kk = 0;
+            } else if (e > -sht::kScaleHi) {
+                vv = std::ldexp(v, e);
+                kk = 0;
+            } else {
+                // k = ceil((e - 256) / 512) < 0: the stored mantissa lies in [2^-257, 2^256)
+                kk = (int)std::ceil((double)(e - sht::kScaleHi) / sht::kScaleUnit);
+                vv = std::ldexp(v, e - sht::kScaleUnit * kk);
+            }
+            sv[(size_t)m * np + q] = vv;
+            sk[(size_t)m * np + q] = kk;
+        }
+    }
+
+    // scaled recurrence coefficients (see legendre_fp64.cu):
+    // C_m = C_{m+1} = 1, C_l = (beta_l / beta_{l-1}) C_{l-2},
+    // A_{m+1} = sqrt(2m+3), A_l = beta_{l-1} C_{l-1} / C_{l-2}
+    std::vector<double> cA(p->nalm), cC(p->nalm);
+    for (int m = 0; m <= M; ++m) {
+        const long long o = mofs(L, m);
+        auto beta = [m](int l) {
+            const double dl = l, dm = m;
+            return std::sqrt((4.0 * dl * dl - 1.0) / (dl * dl - dm * dm));
+        };
+        cA[o] = 0.0;
+        cC[o] = 1.0;
+        if (m + 1 <= L) {
+            cA[o + 1] = std::sqrt(2.0 * m + 3.0);
+            cC[o + 1] = 1.0;
+        }
+        for (int l = m + 2; l <= L; ++l) {
+            const double bl = beta(l), bl1 = beta(l - 1);
+            cC[o + l - m] = (bl / bl1) * cC[o + l - m - 2];
+            cA[o + l - m] = bl1 * cC[o + l - m - 1] / cC[o + l - m - 2];
+        }
+    }
+
+    // rings and twiddle tables T_n[q] = e^{i pi q / n}, q < 2n
+    std::vector<long long> ofs(nr);
+    long long acc = 0;
+    int maxn = 0, cap = 0;
+    for (int r = 0; r < nr; ++r) {
+        ofs[r] = acc;
+        acc += R.nphi[r];
+        maxn = std::max(maxn, R.nphi[r]);
+        const int n = R.nphi[r];
+        const int N = (n % 2 == 0) ? n / 2 : n;
+        cap = std::max(cap, N + 1);
+    }
+    std::map<int, long long> where;
+    std::vector<double2> tw64;
+    std::vector<float2> tw32;
+    std::vector<long long> twofs(nr);
+    for (int r = 0; r < nr; ++r) {
+        const int n = R.nphi[r];
+        auto it = where.find(n);
+        if (it == where.end()) {
+            const long long o = (long long)tw64.size();
+            where[n] = o;
+            for (int q = 0; q < 2 * n; ++q) {
+                const double a = kPi * (double)q / (double)n;
+                const double c = std::cos(a), s = std::sin(a);
+                tw64.push_back(make_double2(c, s));
+                tw32.push_back(make_float2((float)c, (float)s));
+            }
+            twofs[r] = o;
+        } else {
+            twofs[r] = it->second;
+        }
+    }
+
+    // both shared-memory FFT buffers of the FP64 ring kernel must fit in one CTA
+    if (sht::ring_smem_bytes_for_cap(cap, true) > kMaxDynSmem)
+        return fail(SHT_EUNSUPPORTED, "ring of %d pixels too long for the shared-memory FFT", maxn);
+
+    DevPlan &d = p->dp;
+    d.lmax = L;
+    d.mmax = M;
+    d.nrings = nr;
+    d.npairs = np;
+    d.nalm = p->nalm;
+    d.npix = p->npix;
+    d.max_nphi = maxn;
+    d.fft_cap = cap;
+    int rc;
+    if ((rc = upload(p, px, &d.pair_x))) return rc;
+    if ((rc = upload(p, pr, &d.pair_ring))) return rc;
+    if ((rc = upload(p, sv, &d.start_v))) return rc;
+    if ((rc = upload(p, sk, &d.start_k))) return rc;
+    if ((rc = upload(p, cA, &d.coefA))) return rc;
+    if ((rc = upload(p, cC, &d.coefC))) return rc;
+    if ((rc = upload(p, R.nphi, &d.nphi))) return rc;
+    if ((rc = upload(p, ofs, &d.ofs))) return rc;
+    if ((rc = upload(p, R.phi0, &d.phi0))) return rc;
+    if ((rc = upload(p, R.ps, &d.ps))) return rc;
+    if ((rc = upload(p, twofs, &d.twofs))) return rc;
+    if ((rc = upload(p, tw64, &d.tw64))) return rc;
+    if ((rc = upload(p, tw32, &d.tw32))) return rc;
+    return SHT_OK;
+}
+
+// Grow the Delta workspace to at least `bytes` (stream-ordered callers only).
+int ensure_ws(sht_plan_s *p, size_t bytes)
+{
+    if (p->ws_bytes >= bytes) return SHT_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if (p->ws) cudaFree(p->ws);
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+    e = cudaMalloc(&p->ws, bytes);
+    if (e != cudaSuccess) {
+        p->ws = nullptr;
+        cudaGetLastError();
+        return fail(SHT_ENOMEM, "workspace cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    p->ws_bytes = bytes;
+    return SHT_OK;
+}
+
+size_t max_ws_bytes()
+{
+    const char *env = std::getenv("SHT_MAX_WORKSPACE_MB");
+    if (env) {
+        const long long v = std::atoll(env);
+        if (v > 0) return (size_t)v << 20;
+    }
+    return (size_t)16 << 30;
+}
+
+int check_plan(sht_plan_t p)
+{
+    if (!p) return fail(SHT_EINVAL, "null plan");
+    return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sht_last_error(void) { return g_err.c_str(); }
+
+int sht_plan(const sht_grid *g, int lmax, int mmax, sht_plan_t *out)
+{
+    g_err.clear();
+    if (!out) return fail(SHT_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (!g) return fail(SHT_EINVAL, "null grid");
+    if (lmax < 0 || mmax < 0 || mmax > lmax) return fail(SHT_EINVAL, "need 0 <= mmax <= lmax");
+    if (lmax > kMaxL) return fail(SHT_EUNSUPPORTED, "lmax > %d", kMaxL);
+    Rings R;
+    switch (g->kind) {
+    case SHT_GRID_GL:
+        if (g->nrings < 1 || g->nphi_gl < 1) return fail(SHT_EINVAL, "GL grid needs nrings, nphi_gl >= 1");
+        if (g->nphi_gl > kMaxNphi) return fail(SHT_EUNSUPPORTED, "nphi > %d", kMaxNphi);
+        if (g->nrings > 65536) return fail(SHT_EUNSUPPORTED, "too many rings");
+        gl_geometry(g->nrings, g->nphi_gl, R);
+        break;
+    case SHT_GRID_HEALPIX:
+        if (g->nside < 1) return fail(SHT_EINVAL, "HEALPix grid needs nside >= 1");
+        if (4 * (long long)g->nside > kMaxNphi) return fail(SHT_EUNSUPPORTED, "nside > %d", kMaxNphi / 4);
+        healpix_geometry(g->nside, R);
+        break;
+    case SHT_GRID_RINGS: {
+        if (g->nrings < 1 || !g->theta || !g->nphi || !g->phi0)
+            return fail(SHT_EINVAL, "RINGS grid needs nrings >= 1 and theta, nphi, phi0");
+        if (g->nrings > 65536) return fail(SHT_EUNSUPPORTED, "too many rings");
+        const int n = g->nrings;
+        R.x.resize(n);
+        R.s.resize(n);
+        R.nphi.resize(n);
+        R.phi0.resize(n);
+        R.ps.resize(n);
+        for (int r = 0; r < n; ++r) {
+            const double th = g->theta[r];
+            if (!(th >= 0.0 && th <= kPi)) return fail(SHT_EINVAL, "theta[%d] outside [0, pi]", r);
+            if (g->nphi[r] < 1) return fail(SHT_EINVAL, "nphi[%d] < 1", r);
+            if (g->nphi[r] > kMaxNphi) return fail(SHT_EUNSUPPORTED, "nphi[%d] > %d", r, kMaxNphi);
+            if (!std::isfinite(g->phi0[r])) return fail(SHT_EINVAL, "phi0[%d] not finite", r);
+            R.x[r] = std::cos(th);
+            R.s[r] = std::sin(th);
+            R.nphi[r] = g->nphi[r];
+            R.phi0[r] = g->phi0[r];
+            R.ps[r] = (g->phi0[r] == 0.0) ? 0 : -1;
+        }
+        break;
+    }
+    default:
+        return fail(SHT_EINVAL, "unknown grid kind %d", g->kind);
+    }
+
+    auto *p = new (std::nothrow) sht_plan_s();
+    if (!p) return fail(SHT_ENOMEM, "plan allocation");
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    p->kind = g->kind;
+    p->lmax = lmax;
+    p->mmax = mmax;
+    p->nrings = (int)R.x.size();
+    p->nalm = (long long)(mmax + 1) * (2LL * lmax + 2 - mmax) / 2;
+    long long npix = 0;
+    for (int v : R.nphi) npix += v;
+    p->npix = npix;
+    int rc = build_tables(p, R);
+    if (rc != SHT_OK) {
+        std::string keep = g_err;
+        free_plan(p);
+        g_err = keep;
+        return rc;
+    }
+    *out = p;
+    return SHT_OK;
+}
+
+int sht_plan_destroy(sht_plan_t plan)
+{
+    free_plan(plan);
+    return SHT_OK;
+}
+
+size_t sht_nalm(sht_plan_t p) { return p ? (size_t)p->nalm : 0; }
+size_t sht_npix(sht_plan_t p) { return p ? (size_t)p->npix : 0; }
+int sht_nrings(sht_plan_t p) { return p ? p->nrings : 0; }
+int sht_lmax(sht_plan_t p) { return p ? p->lmax : 0; }
+int sht_mmax(sht_plan_t p) { return p ? p->mmax : 0; }
+
+int sht_alm2map_batch(sht_plan_t p, int nbatch, const void *alm_dev, void *map_dev, int prec,
+                      void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (nbatch < 0) return fail(SHT_EINVAL, "nbatch < 0");
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC)
+        return fail(SHT_EINVAL, "unknown precision %d", prec);
+    if (nbatch == 0) return SHT_OK;
+    if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
+    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "precision %d not built", prec);
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
+    size_t chunk_sz = std::max<size_t>(1, max_ws_bytes() / per_map);
+    int chunk = (int)std::min<size_t>(chunk_sz, 32768);  // grid.y limit of the ring kernel
+    chunk = std::min(chunk, nbatch);
+    if ((rc = ensure_ws(p, per_map * chunk))) return rc;
+    const double2 *alm = static_cast<const double2 *>(alm_dev);
+    double *map = static_cast<double *>(map_dev);
+    double2 *delta = static_cast<double2 *>(p->ws);
+    for (int b0 = 0; b0 < nbatch; b0 += chunk) {
+        const int nb = std::min(chunk, nbatch - b0);
+        cudaError_t e = sht::launch_legendre_fwd_fp64(p->dp, alm + (size_t)b0 * p->nalm, delta, nb, st);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_fwd_fp64 launch");
+        e = sht::launch_ring_synth_fp64(p->dp, delta, map + (size_t)b0 * p->npix, nb, st);
+        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp64 launch");
+    }
+    return SHT_OK;
+}
+
+int sht_alm2map(sht_plan_t p, const void *alm_dev, void *map_dev, int prec, void *stream)
+{
+    return sht_alm2map_batch(p, 1, alm_dev, map_dev, prec, stream);
+}
+
+int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, void *alm_dev,
+                              int prec, void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    (void)nbatch;
+    (void)map_dev;
+    (void)alm_dev;
+    (void)prec;
+    (void)stream;
+    return fail(SHT_EUNSUPPORTED, "map2alm_adjoint not built yet");
+}
+
+int sht_map2alm_adjoint(sht_plan_t p, const void *map_dev, void *alm_dev, int prec, void *stream)
+{
+    return sht_map2alm_adjoint_batch(p, 1, map_dev, alm_dev, prec, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Internal declarations shared by the CUDA translation units of libsht.
+// Nothing here is part of the C ABI (see include/sht.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace sht {
+
+// Exponent tracking of the Legendre recurrence (Algorithm 2 of the paper,
+// real-time rescaling).  A value v carried with exponent k stands for
+// v * 2^(kScaleUnit * k).  While k < 0 the value is below 2^-256 and its
+// contribution to Delta_m is dropped; when |v| exceeds 2^kScaleHi the pair
+// (p_l, p_{l-1}) is multiplied by 2^-kScaleUnit and k is incremented.  Powers
+// of two are exact, so the rescaling changes no rounding.
+constexpr int kScaleUnit = 512;
+constexpr int kScaleHi = 256;
+
+// Device-side view of a plan, passed by value to every kernel.
+struct DevPlan {
+    int lmax, mmax, nrings, npairs;
+    long long nalm, npix;
+    int max_nphi;   // longest ring
+    int fft_cap;    // complex elements per shared-memory FFT buffer
+    // ring pairs: the Legendre step runs once per pair of mirrored rings
+    const double *pair_x;   // [npairs] cos(theta) of the pair's northern ring
+    const int2 *pair_ring;  // [npairs] (northern ring, southern ring or -1)
+    // lambda_mm (Eq. pmm) for every (m, pair), as (mantissa, exponent k)
+    const double *start_v;  // [mmax+1][npairs]
+    const int *start_k;     // [mmax+1][npairs]
+    // scaled recurrence p_l = A_l x p_{l-1} - p_{l-2}, lambda_l = C_l p_l,
+    // packed m-major like the coefficients (entry (l, m) holds A_l, C_l)
+    const double *coefA;
+    const double *coefC;
+    // rings
+    const int *nphi;         // [nrings]
+    const long long *ofs;    // [nrings] first pixel
+    const double *phi0;      // [nrings]
+    const int *ps;           // [nrings] phi0 = pi * ps / nphi, or -1 (arbitrary phi0)
+    const long long *twofs;  // [nrings] offset of the ring's table in tw64 / tw32
+    const double2 *tw64;     // per distinct nphi = n: e^{i pi q / n}, q in [0, 2n)
+    const float2 *tw32;
+};
+
+// Legendre step, FP64 (recurrence and contraction in FP64).
+//   delta[b][ring][m] (complex) = Delta_m(theta_ring) for maps b in [0, nmaps).
+cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, double2 *delta,
+                                     int nmaps, cudaStream_t st);
+
+// Ring step: phase shift, fold of m onto the ring's bins, real inverse DFT of
+// each ring.  T = double (FP64 path) or float (tensor-core paths).
+cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps,
+                                   cudaStream_t st);
+cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float *map, int nmaps,
+                                   cudaStream_t st);
+
+// Shared-memory bytes the ring kernels need for this plan.
+size_t ring_smem_bytes(const DevPlan &P, bool fp64);
+inline size_t ring_smem_bytes_for_cap(int cap, bool fp64)
+{
+    return (size_t)2 * cap * (fp64 ? 16 : 8);
+}
+
+}  // namespace sht

@@ -1,0 +1,189 @@
+"""Python binding of libsht (ctypes; argument marshalling only).
+
+Every step of the transform runs in the library's CUDA kernels; PyTorch only
+provides device memory and the current stream.  There is no CPU fallback: if
+the library has not been built, loading it raises.
+
+    from paper_1010_1260_gb300 import sht
+    plan = sht.Plan(sht.healpix(512), lmax=1024)
+    m = plan.alm2map(alm)            # alm: cuda complex128 [B, nalm] or [nalm]
+    g = plan.map2alm_adjoint(m)      # transpose: cuda complex128
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsht.so")
+
+SHT_OK = 0
+SHT_EINVAL = -1
+SHT_ENOMEM = -2
+SHT_ECUDA = -3
+SHT_EUNSUPPORTED = -4
+SHT_ETIMEOUT = -5
+
+GRID_GL, GRID_HEALPIX, GRID_RINGS = 0, 1, 2
+PREC = {"fp64": 0, "fp32_tc": 1, "bf16x3_tc": 2}
+MAP_DTYPE = {"fp64": torch.float64, "fp32_tc": torch.float32, "bf16x3_tc": torch.float32}
+
+
+class ShtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("libsht error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nside", ctypes.c_int), ("nrings", ctypes.c_int),
+                ("nphi_gl", ctypes.c_int), ("theta", ctypes.c_void_p), ("nphi", ctypes.c_void_p),
+                ("phi0", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libsht.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libsht.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+            L.sht_plan.argtypes = [ctypes.POINTER(_Grid), I, I, ctypes.POINTER(P)]
+            L.sht_plan_destroy.argtypes = [P]
+            for f in ("sht_nalm", "sht_npix"):
+                getattr(L, f).argtypes = [P]
+                getattr(L, f).restype = ctypes.c_size_t
+            for f in ("sht_nrings", "sht_lmax", "sht_mmax"):
+                getattr(L, f).argtypes = [P]
+                getattr(L, f).restype = I
+            L.sht_alm2map.argtypes = [P, V, V, I, V]
+            L.sht_map2alm_adjoint.argtypes = [P, V, V, I, V]
+            L.sht_alm2map_batch.argtypes = [P, I, V, V, I, V]
+            L.sht_map2alm_adjoint_batch.argtypes = [P, I, V, V, I, V]
+            L.sht_last_error.restype = ctypes.c_char_p
+            for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
+                      "sht_alm2map_batch", "sht_map2alm_adjoint_batch"):
+                getattr(L, f).restype = I
+            _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != SHT_OK:
+        raise ShtError(rc, lib().sht_last_error().decode())
+
+
+# ------------------------------------------------------------------ grids --
+
+class GridSpec:
+    """A ring grid: Gauss-Legendre, HEALPix or caller-given rings."""
+
+    def __init__(self, kind: int, nside: int = 0, nrings: int = 0, nphi_gl: int = 0,
+                 theta=None, nphi=None, phi0=None):
+        self.kind = kind
+        self.nside = nside
+        self.nrings = nrings
+        self.nphi_gl = nphi_gl
+        self.theta = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+        self.nphi = None if nphi is None else np.ascontiguousarray(nphi, dtype=np.int32)
+        self.phi0 = None if phi0 is None else np.ascontiguousarray(phi0, dtype=np.float64)
+
+    def _c(self) -> _Grid:
+        g = _Grid()
+        g.kind, g.nside, g.nrings, g.nphi_gl = self.kind, self.nside, self.nrings, self.nphi_gl
+        g.theta = None if self.theta is None else self.theta.ctypes.data
+        g.nphi = None if self.nphi is None else self.nphi.ctypes.data
+        g.phi0 = None if self.phi0 is None else self.phi0.ctypes.data
+        return g
+
+
+def gl(nrings: int, nphi: int) -> GridSpec:
+    return GridSpec(GRID_GL, nrings=nrings, nphi_gl=nphi)
+
+
+def healpix(nside: int) -> GridSpec:
+    return GridSpec(GRID_HEALPIX, nside=nside)
+
+
+def rings(theta, nphi, phi0) -> GridSpec:
+    theta = np.asarray(theta, dtype=np.float64)
+    return GridSpec(GRID_RINGS, nrings=len(theta), theta=theta, nphi=nphi, phi0=phi0)
+
+
+# ------------------------------------------------------------------- plan --
+
+def _stream_ptr(stream) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """A libsht plan on the current CUDA device."""
+
+    def __init__(self, grid: GridSpec, lmax: int, mmax: int | None = None):
+        L = lib()
+        self.grid = grid
+        self.lmax = int(lmax)
+        self.mmax = int(lmax if mmax is None else mmax)
+        h = ctypes.c_void_p()
+        g = grid._c()
+        check(L.sht_plan(ctypes.byref(g), self.lmax, self.mmax, ctypes.byref(h)))
+        self._h = h
+        self.nalm = int(L.sht_nalm(h))
+        self.npix = int(L.sht_npix(h))
+        self.nrings = int(L.sht_nrings(h))
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sht_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alm2map(self, alm: torch.Tensor, prec: str = "fp64", out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        """Maps of ``alm`` (cuda complex128, [B, nalm] or [nalm])."""
+        if not (alm.is_cuda and alm.dtype == torch.complex128):
+            raise TypeError("alm must be a CUDA complex128 tensor")
+        single = alm.dim() == 1
+        a = alm.reshape(-1, self.nalm).contiguous()
+        B = a.shape[0]
+        if out is None:
+            out = torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], device=alm.device)
+        elif not (out.is_contiguous() and out.dtype == MAP_DTYPE[prec] and out.numel() == B * self.npix):
+            raise TypeError("bad output tensor")
+        check(lib().sht_alm2map_batch(self._h, B, a.data_ptr(), out.data_ptr(), PREC[prec],
+                                      _stream_ptr(stream)))
+        return out.reshape(self.npix) if single else out.reshape(B, self.npix)
+
+    def map2alm_adjoint(self, maps: torch.Tensor, prec: str = "fp64", out: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+        """Real-linear transpose of alm2map (cuda complex128 result)."""
+        if not (maps.is_cuda and maps.dtype == MAP_DTYPE[prec]):
+            raise TypeError("maps must be a CUDA tensor of dtype %s" % MAP_DTYPE[prec])
+        single = maps.dim() == 1
+        y = maps.reshape(-1, self.npix).contiguous()
+        B = y.shape[0]
+        if out is None:
+            out = torch.empty((B, self.nalm), dtype=torch.complex128, device=maps.device)
+        check(lib().sht_map2alm_adjoint_batch(self._h, B, y.data_ptr(), out.data_ptr(), PREC[prec],
+                                              _stream_ptr(stream)))
+        return out.reshape(self.nalm) if single else out.reshape(B, self.nalm)
