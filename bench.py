@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""alm2map throughput on GB300: maps/s at lmax = 2048.
+
+Workload (one step): a batch of 64 maps on a HEALPix grid with nside = 1024
+(4095 rings, 12,582,912 pixels per map), lmax = mmax = 2048, coefficients
+drawn from a Gaussian with C_l = 1 / (l (l + 1)) (seeded, synthetic), one
+alm2map of the whole batch through the library's C ABI.  Inputs (2.15 GB of
+coefficients) and outputs are larger than the 129 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32_tc|bf16x3_tc]
+    python bench.py --impl reference     # the CPU oracle on the same workload
+
+Under torchrun every rank transforms its own batch (weak scaling, no
+collective on the data path); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "alm2map maps/s at lmax=2048 (HEALPix nside 1024, batch of 64 maps)"
+UNIT = "maps/s"
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
+DTYPE = {"fp64": "f64", "fp32_tc": "f64 recurrence + tf32x3 MMA / f32", "bf16x3_tc": "f64 recurrence + bf16 split MMA / f32"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp64", "fp32_tc", "bf16x3_tc"], default="fp64")
+    ap.add_argument("--nside", type=int, default=1024)
+    ap.add_argument("--lmax", type=int, default=2048)
+    ap.add_argument("--maps", type=int, default=64)
+    ap.add_argument("--cpu-rings", type=int, default=384,
+                    help="rings of one map in the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(args):
+    return {"workload": "alm2map HEALPix nside=%d lmax=mmax=%d batch=%d" % (args.nside, args.lmax, args.maps),
+            "grid": "healpix", "nside": args.nside, "lmax": args.lmax, "mmax": args.lmax,
+            "maps_per_gpu": args.maps, "spectrum": "C_l = 1/(l(l+1)) Gaussian, seeds (3, b)",
+            "l2": "inputs larger than L2 (alm %.2f GB per step), no flush" % (
+                16.0 * (args.lmax + 1) * (args.lmax + 2) / 2 * args.maps / 1e9)}
+
+
+# --------------------------------------------------------------- CPU oracle --
+
+def cpu_oracle_sample(args, rings_count: int, seed: int = 41):
+    """Time the oracle on one map's seeded ring sample; returns (maps/s, seconds, threads, desc)."""
+    import oracle
+    from paper_1010_1260_gb300 import inputs
+    g = oracle.healpix_grid(args.nside)
+    alm = inputs.batch_alm(args.lmax, args.lmax, 3, 1)
+    rng = np.random.default_rng(seed)
+    rings = np.sort(rng.choice(g["nrings"], size=min(rings_count, g["nrings"]), replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    _, nt = oracle.alm2map(g, args.lmax, args.lmax, alm, rings=rings, return_threads=True)
+    dt = time.perf_counter() - t0
+    frac = len(rings) / g["nrings"]
+    maps_per_s = frac / dt
+    desc = "%d of %d rings (seeded uniform sample) of 1 map; maps/s = sampled fraction / time" % (
+        len(rings), g["nrings"])
+    return maps_per_s, dt, nt, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args, max(16, args.cpu_rings // 8))
+    nt = 0
+    desc = ""
+    t_tot = 0.0
+    for k in range(args.steps):
+        v, dt, nt, desc = cpu_oracle_sample(args, args.cpu_rings, seed=41 + k)
+        vals.append(v)
+        t_tot += dt
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * args.maps / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload(args), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our impl --
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        tab = json.load(open(path))
+    except ValueError:
+        return None
+    ent = tab.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+def legendre_flops(R: int, L: int, M: int, B: int, prec: str):
+    """Algorithmic flops of one Legendre launch: 3 R N_lm (recurrence) + 4 R N_lm B (contraction)."""
+    nlm = (M + 1) * (2 * L + 2 - M) // 2
+    return 3.0 * R * nlm + 4.0 * R * nlm * B
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1010_1260_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1010_1260_gb300 import inputs, sht
+    dev = torch.device("cuda", torch.cuda.current_device())
+    L, B = args.lmax, args.maps
+    plan = sht.Plan(sht.healpix(args.nside), L)
+    alm_h = np.empty((B, plan.nalm), dtype=np.complex128)
+    for b in range(B):
+        alm_h[b] = inputs.gaussian_alm(L, L, (3, rank * B + b))[0]
+    alm = torch.from_numpy(alm_h).to(dev)
+    out = torch.empty((B, plan.npix), dtype=sht.MAP_DTYPE[args.prec], device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.alm2map(alm, args.prec, out=out)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    plan.profile(True)
+    plan.profile_read()
+    n0 = sht.kernel_launches()
+    clk = ClockSampler(local)
+    if not args.no_clocks:
+        clk.start()
+        time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.alm2map(alm, args.prec, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = sht.kernel_launches() - n0
+    stages = plan.profile_read()
+    plan.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    # per-map accuracy on a sample of rings against the CPU oracle (rank 0)
+    accuracy = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        g = oracle.healpix_grid(args.nside)
+        rings = inputs.sample_rings(g["nrings"], 4, 77)
+        nchk = min(B, 8)
+        want = oracle.alm2map(g, L, L, alm_h[:nchk], rings=rings)
+        got = out[:nchk].double().cpu().numpy()
+        errs = []
+        for b in range(nchk):
+            ok = np.isfinite(want[b])
+            errs.append(float(np.max(np.abs(got[b, ok] - want[b, ok])) / np.max(np.abs(want[b, ok]))))
+        accuracy = {"metric": "max|s - s_oracle| / max|s_oracle| per map", "maps_checked": nchk,
+                    "rings_checked": [int(r) for r in rings], "max": max(errs), "per_map": errs}
+
+    # end to end: pinned host coefficients in, host map out, through the binding
+    e2e = None
+    if args.e2e_steps > 0:
+        a_pin = torch.from_numpy(alm_h).pin_memory()
+        m_pin = torch.empty((B, plan.npix), dtype=sht.MAP_DTYPE[args.prec], pin_memory=True)
+        plan.alm2map_host(a_pin, args.prec, out=m_pin)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.alm2map_host(a_pin, args.prec, out=m_pin)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * B / dt, "unit": UNIT, "h2d_bytes_per_step": int(a_pin.numel() * 16),
+               "d2h_bytes_per_step": int(m_pin.numel() * m_pin.element_size()), "ms_per_step": dt * 1000}
+        del a_pin, m_pin
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    dom = max(stages, key=lambda s: stages[s][0])
+    dom_ms = stages[dom][0] / max(1, stages[dom][1])
+    R = (4 * args.nside - 1 + 1) // 2
+    roof = None
+    if dom == "legendre" and args.prec == "fp64":
+        fl = legendre_flops(R, L, L, B, args.prec)
+        ach = fl / (dom_ms * 1e-3) / 1e12
+        roof = {"kernel": "legendre_fwd_fp64", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_fwd_fp64"),
+                "peak_source": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "flops_per_launch": fl, "ms_per_launch": dom_ms}
+    elif dom == "ring":
+        npix = 12 * args.nside ** 2
+        esz = 8 if args.prec == "fp64" else 4
+        by = B * ((4 * args.nside - 1) * (L + 1) * 2 * esz + npix * esz)
+        ach = by / (dom_ms * 1e-3) / 1e9
+        peak = _peaks().get("hbm_gbs", 6800.0)
+        roof = {"kernel": "ring_synth", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic_for("ring_synth"), "bytes_per_launch": by,
+                "ms_per_launch": dom_ms}
+
+    maps_per_s = world * B / (ms * 1e-3)
+    line = {"metric": METRIC, "value": maps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+            "config": dict(workload(args), parallelism="replicas x%d" % world, precision=args.prec),
+            "roofline": roof,
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
+            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy}
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt, nt, desc = cpu_oracle_sample(args, args.cpu_rings)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc,
+                                "seconds": dt}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

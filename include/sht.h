@@ -115,6 +115,25 @@ int sht_map2alm_adjoint_batch(sht_plan_t plan, int nbatch, const void *map_dev, 
 /* Message describing the last error on the calling thread ("" if none). */
 const char *sht_last_error(void);
 
+/* Per-stage GPU timing (the paper times its kernels with gettimeofday,
+ * sec. 6; here CUDA events are recorded on the launch stream around every
+ * kernel the plan launches while profiling is enabled).
+ * Stages: SHT_STAGE_LEGENDRE (Legendre step), SHT_STAGE_RING (ring step),
+ * SHT_STAGE_ADJ_RING, SHT_STAGE_ADJ_LEGENDRE (the transpose's two steps).
+ * sht_profile_read synchronises the plan's device, writes the summed
+ * milliseconds and the launch count of each of the first nstage stages into
+ * ms[] and launches[] (either may be NULL) and resets the counters. */
+#define SHT_STAGE_LEGENDRE 0
+#define SHT_STAGE_RING 1
+#define SHT_STAGE_ADJ_RING 2
+#define SHT_STAGE_ADJ_LEGENDRE 3
+#define SHT_NSTAGES 4
+int sht_profile(sht_plan_t plan, int enable);
+int sht_profile_read(sht_plan_t plan, int nstage, double *ms, long long *launches);
+
+/* Number of kernels libsht has launched in this process (all plans). */
+unsigned long long sht_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -15,8 +16,18 @@
 
 using sht::DevPlan;
 
+struct ProfEvent {
+    int stage;
+    cudaEvent_t a, b;
+};
+
 struct sht_plan_s {
     int device = 0;
+    bool profiling = false;
+    std::vector<ProfEvent> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[SHT_NSTAGES] = {0};
+    long long prof_n[SHT_NSTAGES] = {0};
     int kind = 0, lmax = 0, mmax = 0, nrings = 0, npairs = 0;
     long long nalm = 0, npix = 0;
     DevPlan dp{};
@@ -29,6 +40,7 @@ struct sht_plan_s {
 namespace {
 
 thread_local std::string g_err;
+std::atomic<unsigned long long> g_launches{0};
 
 int fail(int code, const char *fmt, ...)
 {
@@ -180,9 +192,54 @@ void free_plan(sht_plan_s *p)
         cudaDeviceSynchronize();
         for (void *d : p->allocs) cudaFree(d);
         if (p->ws) cudaFree(p->ws);
+        for (auto &e : p->prof_pending) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+        for (auto e : p->prof_pool) cudaEventDestroy(e);
     }
     delete p;
 }
+
+// ------------------------------------------------------------ profiling --
+
+cudaEvent_t prof_event(sht_plan_s *p)
+{
+    if (!p->prof_pool.empty()) {
+        cudaEvent_t e = p->prof_pool.back();
+        p->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch: records events on the launch stream when the
+// plan is profiling, and counts the launch.
+struct StageScope {
+    sht_plan_s *p;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageScope(sht_plan_s *p_, int stage_, cudaStream_t st_) : p(p_), stage(stage_), st(st_)
+    {
+        if (p->profiling) {
+            a = prof_event(p);
+            cudaEventRecord(a, st);
+        }
+    }
+    void done(cudaError_t launch_rc)
+    {
+        if (launch_rc == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (a) {
+            cudaEvent_t b = prof_event(p);
+            cudaEventRecord(b, st);
+            p->prof_pending.push_back({stage, a, b});
+            a = nullptr;
+        }
+    }
+};
 
 inline long long mofs(int lmax, int m) { return (long long)m * (2LL * lmax + 3 - m) / 2; }
 
@@ -489,9 +546,13 @@ int sht_alm2map_batch(sht_plan_t p, int nbatch, const void *alm_dev, void *map_d
     double2 *delta = static_cast<double2 *>(p->ws);
     for (int b0 = 0; b0 < nbatch; b0 += chunk) {
         const int nb = std::min(chunk, nbatch - b0);
+        StageScope s1(p, SHT_STAGE_LEGENDRE, st);
         cudaError_t e = sht::launch_legendre_fwd_fp64(p->dp, alm + (size_t)b0 * p->nalm, delta, nb, st);
+        s1.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_fwd_fp64 launch");
+        StageScope s2(p, SHT_STAGE_RING, st);
         e = sht::launch_ring_synth_fp64(p->dp, delta, map + (size_t)b0 * p->npix, nb, st);
+        s2.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp64 launch");
     }
     return SHT_OK;
@@ -514,6 +575,48 @@ int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, voi
     (void)prec;
     (void)stream;
     return fail(SHT_EUNSUPPORTED, "map2alm_adjoint not built yet");
+}
+
+unsigned long long sht_kernel_launches(void) { return g_launches.load(); }
+
+int sht_profile(sht_plan_t p, int enable)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->profiling = enable != 0;
+    return SHT_OK;
+}
+
+int sht_profile_read(sht_plan_t p, int nstage, double *ms, long long *launches)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (nstage < 0) return fail(SHT_EINVAL, "nstage < 0");
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    for (auto &e : p->prof_pending) {
+        cudaError_t err = cudaEventSynchronize(e.b);
+        float t = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e.a, e.b);
+        if (err != cudaSuccess) return cuda_fail(err, "profiling event");
+        p->prof_ms[e.stage] += t;
+        p->prof_n[e.stage] += 1;
+        p->prof_pool.push_back(e.a);
+        p->prof_pool.push_back(e.b);
+    }
+    p->prof_pending.clear();
+    for (int i = 0; i < nstage; ++i) {
+        if (ms) ms[i] = i < SHT_NSTAGES ? p->prof_ms[i] : 0.0;
+        if (launches) launches[i] = i < SHT_NSTAGES ? p->prof_n[i] : 0;
+    }
+    for (int i = 0; i < SHT_NSTAGES; ++i) {
+        p->prof_ms[i] = 0.0;
+        p->prof_n[i] = 0;
+    }
+    return SHT_OK;
 }
 
 int sht_map2alm_adjoint(sht_plan_t p, const void *map_dev, void *alm_dev, int prec, void *stream)

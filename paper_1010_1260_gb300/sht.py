@@ -71,8 +71,13 @@ def lib():
             L.sht_alm2map_batch.argtypes = [P, I, V, V, I, V]
             L.sht_map2alm_adjoint_batch.argtypes = [P, I, V, V, I, V]
             L.sht_last_error.restype = ctypes.c_char_p
+            L.sht_profile.argtypes = [P, I]
+            L.sht_profile_read.argtypes = [P, I, V, V]
+            L.sht_kernel_launches.argtypes = []
+            L.sht_kernel_launches.restype = ctypes.c_ulonglong
             for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
-                      "sht_alm2map_batch", "sht_map2alm_adjoint_batch"):
+                      "sht_alm2map_batch", "sht_map2alm_adjoint_batch", "sht_profile",
+                      "sht_profile_read"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -81,6 +86,14 @@ def lib():
 def check(rc: int):
     if rc != SHT_OK:
         raise ShtError(rc, lib().sht_last_error().decode())
+
+
+STAGES = ("legendre", "ring", "adj_ring", "adj_legendre")
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libsht in this process so far."""
+    return int(lib().sht_kernel_launches())
 
 
 # ------------------------------------------------------------------ grids --
@@ -187,3 +200,39 @@ class Plan:
         check(lib().sht_map2alm_adjoint_batch(self._h, B, y.data_ptr(), out.data_ptr(), PREC[prec],
                                               _stream_ptr(stream)))
         return out.reshape(self.nalm) if single else out.reshape(B, self.nalm)
+
+    # ---------------------------------------------------------- profiling --
+    def profile(self, enable: bool = True):
+        """Record CUDA events around every kernel this plan launches."""
+        check(lib().sht_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{stage: (total ms, launches)} since the last read (synchronises)."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        check(lib().sht_profile_read(self._h, n, ms, cnt))
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
+
+    # ------------------------------------------------------- host buffers --
+    def alm2map_host(self, alm: torch.Tensor, prec: str = "fp64", out: torch.Tensor | None = None) -> torch.Tensor:
+        """alm2map of host coefficients into a host map: copies in on the
+        current stream, transforms, copies out, and waits.  Pinned host tensors
+        make the copies asynchronous."""
+        if alm.is_cuda or alm.dtype != torch.complex128:
+            raise TypeError("alm must be a host complex128 tensor")
+        a = alm.reshape(-1, self.nalm)
+        B = a.shape[0]
+        key = (B, prec)
+        if getattr(self, "_host_bufs", None) is None or self._host_bufs[0] != key:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            self._host_bufs = (key, torch.empty((B, self.nalm), dtype=torch.complex128, device=dev),
+                               torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], device=dev))
+        _, d_alm, d_map = self._host_bufs
+        if out is None:
+            out = torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], pin_memory=True)
+        d_alm.copy_(a, non_blocking=True)
+        self.alm2map(d_alm, prec, out=d_map)
+        out.copy_(d_map, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return out
