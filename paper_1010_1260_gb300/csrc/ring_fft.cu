@@ -86,6 +86,140 @@ __device__ int factorize(int N, int *rad)
     return np;
 }
 
+// Self-sorting (Stockham) mixed-radix complex DFT of length N in shared
+// memory, ping-ponging between src and dst; returns the buffer holding the
+// result.  INV: sign + (inverse, unnormalised) or - (forward).  w_N^q is
+// T[q * tstep] (conjugated for the forward sign).  Pass with radix R and
+// sub-transform size Ns:
+//   Y[(j/Ns) Ns R + j%Ns + q Ns] = sum_r X[j + r N/R] w_{Ns R}^{r (j%Ns)} w_R^{r q}.
+template <bool INV, typename R, typename C>
+__device__ C *stockham(C *src, C *dst, const int N, const C *__restrict__ T, const int tstep,
+                       const int *rad, const int npass)
+{
+    const int tid = threadIdx.x;
+    const R sg = INV ? (R)1 : (R)-1;
+    auto tw = [&](int q) {
+        C w = T[q * tstep];
+        if (!INV) w.y = -w.y;
+        return w;
+    };
+    // multiply by sg * i
+    auto muli = [&](C a) {
+        C c;
+        c.x = -sg * a.y;
+        c.y = sg * a.x;
+        return c;
+    };
+    int Ns = 1;
+    for (int pi = 0; pi < npass; ++pi) {
+        const int Rr = rad[pi];
+        const int NR = N / Rr;
+        const int tscale = N / (Ns * Rr);  // w_{Ns R}^e = w_N^{e tscale}
+        if (Rr == 2) {
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR];
+                if (kk) v1 = cmul(v1, tw((kk * tscale) % N));
+                const int o = (j / Ns) * Ns * 2 + kk;
+                dst[o] = cadd(v0, v1);
+                dst[o + Ns] = csub(v0, v1);
+            }
+        } else if (Rr == 4) {
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+                    v1 = cmul(v1, tw(e % N));
+                    v2 = cmul(v2, tw((2 * e) % N));
+                    v3 = cmul(v3, tw((3 * e) % N));
+                }
+                // radix 4 with w_4 = sg * i
+                const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
+                const C a2 = cadd(v1, v3), a3 = muli(csub(v1, v3));
+                const int o = (j / Ns) * Ns * 4 + kk;
+                dst[o] = cadd(a0, a2);
+                dst[o + Ns] = cadd(a1, a3);
+                dst[o + 2 * Ns] = csub(a0, a2);
+                dst[o + 3 * Ns] = csub(a1, a3);
+            }
+        } else if (Rr == 3) {
+            const R c3 = (R)-0.5;
+            const R s3 = sg * (R)0.86602540378443864676372317075294;  // sg sin(2 pi / 3)
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+                    v1 = cmul(v1, tw(e % N));
+                    v2 = cmul(v2, tw((2 * e) % N));
+                }
+                const C t1 = cadd(v1, v2);
+                const C t2 = csub(v1, v2);
+                const C m1 = mk<R>(v0.x + c3 * t1.x, v0.y + c3 * t1.y);
+                const C m2 = mk<R>(-s3 * t2.y, s3 * t2.x);  // i s3 (v1 - v2)
+                const int o = (j / Ns) * Ns * 3 + kk;
+                dst[o] = cadd(v0, t1);
+                dst[o + Ns] = cadd(m1, m2);
+                dst[o + 2 * Ns] = csub(m1, m2);
+            }
+        } else if (Rr == 5) {
+            const R c1 = (R)0.30901699437494742410229341718282;        // cos(2 pi / 5)
+            const R c2 = (R)-0.80901699437494742410229341718282;       // cos(4 pi / 5)
+            const R s1 = sg * (R)0.95105651629515357211643933337938;   // sg sin(2 pi / 5)
+            const R s2 = sg * (R)0.58778525229247312916870595463907;   // sg sin(4 pi / 5)
+            for (int j = tid; j < NR; j += kThreads) {
+                const int kk = j % Ns;
+                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR],
+                  v4 = src[j + 4 * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+                    v1 = cmul(v1, tw(e % N));
+                    v2 = cmul(v2, tw((2 * e) % N));
+                    v3 = cmul(v3, tw((3 * e) % N));
+                    v4 = cmul(v4, tw((4 * e) % N));
+                }
+                const C a1 = cadd(v1, v4), b1 = csub(v1, v4);
+                const C a2 = cadd(v2, v3), b2 = csub(v2, v3);
+                const C m1 = mk<R>(v0.x + c1 * a1.x + c2 * a2.x, v0.y + c1 * a1.y + c2 * a2.y);
+                const C m2 = mk<R>(v0.x + c2 * a1.x + c1 * a2.x, v0.y + c2 * a1.y + c1 * a2.y);
+                // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
+                const C n1 = mk<R>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
+                const C n2 = mk<R>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
+                const int o = (j / Ns) * Ns * 5 + kk;
+                dst[o] = cadd(v0, cadd(a1, a2));
+                dst[o + Ns] = cadd(m1, n1);
+                dst[o + 2 * Ns] = cadd(m2, n2);
+                dst[o + 3 * Ns] = csub(m2, n2);
+                dst[o + 4 * Ns] = csub(m1, n1);
+            }
+        } else {
+            // direct pass for a general prime radix: one thread per output,
+            // Y[o + q Ns] = sum_r X[j + r NR] w_N^{r (kk tscale + q NR)}
+            for (int t = tid; t < N; t += kThreads) {
+                const int j = t % NR;
+                const int q = t / NR;
+                const int kk = j % Ns;
+                const int e = (kk * tscale + q * NR) % N;
+                C acc = src[j];
+                int idx = e;
+                for (int rr = 1; rr < Rr; ++rr) {
+                    acc = cadd(acc, cmul(src[j + rr * NR], tw(idx)));
+                    idx += e;
+                    if (idx >= N) idx -= N;
+                }
+                dst[(j / Ns) * Ns * Rr + kk + q * Ns] = acc;
+            }
+        }
+        __syncthreads();
+        C *tmp = src;
+        src = dst;
+        dst = tmp;
+        Ns *= Rr;
+    }
+    return src;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ delta,
@@ -157,118 +291,8 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
     }
     __syncthreads();
 
-    // 3. Stockham passes, inverse sign: Y[(j/Ns) Ns R + j%Ns + q Ns] =
-    //    sum_r X[j + r N/R] w_{Ns R}^{r (j%Ns)} w_R^{r q}
-    C *src = buf0;
-    C *dst = buf1;
-    int Ns = 1;
-    const int npass = s_np;
-    for (int pi = 0; pi < npass; ++pi) {
-        const int Rr = s_rad[pi];
-        const int NR = N / Rr;
-        const int tscale = N / (Ns * Rr);  // w_{Ns R}^e = w_N^{e tscale}
-        if (Rr == 2) {
-            for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
-                C v0 = src[j], v1 = src[j + NR];
-                if (kk) v1 = cmul(v1, T[(kk * tscale) % N * tstep]);
-                const int o = (j / Ns) * Ns * 2 + kk;
-                dst[o] = cadd(v0, v1);
-                dst[o + Ns] = csub(v0, v1);
-            }
-        } else if (Rr == 4) {
-            for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
-                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR];
-                if (kk) {
-                    const int e = kk * tscale;
-                    v1 = cmul(v1, T[(e % N) * tstep]);
-                    v2 = cmul(v2, T[((2 * e) % N) * tstep]);
-                    v3 = cmul(v3, T[((3 * e) % N) * tstep]);
-                }
-                // inverse radix-4: w_4 = +i
-                const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
-                const C a2 = cadd(v1, v3), a3 = cmuli(csub(v1, v3));
-                const int o = (j / Ns) * Ns * 4 + kk;
-                dst[o] = cadd(a0, a2);
-                dst[o + Ns] = cadd(a1, a3);
-                dst[o + 2 * Ns] = csub(a0, a2);
-                dst[o + 3 * Ns] = csub(a1, a3);
-            }
-        } else if (Rr == 3) {
-            const R c3 = (R)-0.5;
-            const R s3 = (R)0.86602540378443864676372317075294;  // sin(2 pi / 3)
-            for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
-                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR];
-                if (kk) {
-                    const int e = kk * tscale;
-                    v1 = cmul(v1, T[(e % N) * tstep]);
-                    v2 = cmul(v2, T[((2 * e) % N) * tstep]);
-                }
-                const C t1 = cadd(v1, v2);
-                const C t2 = csub(v1, v2);
-                const C m1 = mk<R>(v0.x + c3 * t1.x, v0.y + c3 * t1.y);
-                const C m2 = mk<R>(-s3 * t2.y, s3 * t2.x);  // i s3 (v1 - v2)
-                const int o = (j / Ns) * Ns * 3 + kk;
-                dst[o] = cadd(v0, t1);
-                dst[o + Ns] = cadd(m1, m2);
-                dst[o + 2 * Ns] = csub(m1, m2);
-            }
-        } else if (Rr == 5) {
-            const R c1 = (R)0.30901699437494742410229341718282;   // cos(2 pi / 5)
-            const R c2 = (R)-0.80901699437494742410229341718282;  // cos(4 pi / 5)
-            const R s1 = (R)0.95105651629515357211643933337938;   // sin(2 pi / 5)
-            const R s2 = (R)0.58778525229247312916870595463907;   // sin(4 pi / 5)
-            for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
-                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR],
-                  v4 = src[j + 4 * NR];
-                if (kk) {
-                    const int e = kk * tscale;
-                    v1 = cmul(v1, T[(e % N) * tstep]);
-                    v2 = cmul(v2, T[((2 * e) % N) * tstep]);
-                    v3 = cmul(v3, T[((3 * e) % N) * tstep]);
-                    v4 = cmul(v4, T[((4 * e) % N) * tstep]);
-                }
-                const C a1 = cadd(v1, v4), b1 = csub(v1, v4);
-                const C a2 = cadd(v2, v3), b2 = csub(v2, v3);
-                const C m1 = mk<R>(v0.x + c1 * a1.x + c2 * a2.x, v0.y + c1 * a1.y + c2 * a2.y);
-                const C m2 = mk<R>(v0.x + c2 * a1.x + c1 * a2.x, v0.y + c2 * a1.y + c1 * a2.y);
-                // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
-                const C n1 = mk<R>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
-                const C n2 = mk<R>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
-                const int o = (j / Ns) * Ns * 5 + kk;
-                dst[o] = cadd(v0, cadd(a1, a2));
-                dst[o + Ns] = cadd(m1, n1);
-                dst[o + 2 * Ns] = cadd(m2, n2);
-                dst[o + 3 * Ns] = csub(m2, n2);
-                dst[o + 4 * Ns] = csub(m1, n1);
-            }
-        } else {
-            // direct pass for a general prime radix: one thread per output,
-            // Y[o + q Ns] = sum_r X[j + r NR] w_N^{r (kk tscale + q NR)}
-            for (int t = tid; t < N; t += kThreads) {
-                const int j = t % NR;
-                const int q = t / NR;
-                const int kk = j % Ns;
-                const int e = (kk * tscale + q * NR) % N;
-                C acc = src[j];
-                int idx = e;
-                for (int rr = 1; rr < Rr; ++rr) {
-                    acc = cadd(acc, cmul(src[j + rr * NR], T[idx * tstep]));
-                    idx += e;
-                    if (idx >= N) idx -= N;
-                }
-                dst[(j / Ns) * Ns * Rr + kk + q * Ns] = acc;
-            }
-        }
-        __syncthreads();
-        C *tmp = src;
-        src = dst;
-        dst = tmp;
-        Ns *= Rr;
-    }
+    // 3. inverse complex DFT of length N
+    C *src = stockham<true, R>(buf0, buf1, N, T, tstep, s_rad, s_np);
 
     // 4. store the ring
     R *out = map + (size_t)b * P.npix + P.ofs[r];
@@ -281,6 +305,96 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
     } else {
         for (int j = tid; j < N; j += kThreads) out[j] = src[j].x;
     }
+}
+
+// Ring step of the transpose (map2alm_adjoint): for every ring r and m <= M,
+//   q_m(r) = sum_j y_rj e^{-i m (phi0_r + 2 pi j / n)} = e^{-i m phi0} Y_{m mod n},
+// where Y is the forward real DFT of the ring (Y_{n-k} = conj Y_k).  For even
+// n the real DFT runs as one complex DFT of z_j = y_{2j} + i y_{2j+1}, length
+// h = n/2: Y_k = (Z_k + conj Z_{h-k})/2 - (i/2) w^{-k} (Z_k - conj Z_{h-k}).
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
+                     typename C2T<R>::type *__restrict__ qout)
+{
+    using C = typename C2T<R>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + P.fft_cap;
+    __shared__ int s_rad[32];
+    __shared__ int s_np;
+
+    const int r = blockIdx.x;
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int n = P.nphi[r];
+    const int M = P.mmax;
+    const C *T = tw_table<R>(P) + P.twofs[r];
+    const int ps = P.ps[r];
+    const double phi0 = P.phi0[r];
+    const bool even = (n % 2) == 0;
+    const int N = even ? n / 2 : n;
+    const int nb = even ? n / 2 + 1 : (n - 1) / 2 + 1;
+    const int tstep = even ? 4 : 2;
+    const R *in = map + (size_t)b * P.npix + P.ofs[r];
+
+    if (tid == 0) s_np = factorize(N, s_rad);
+    if (even) {
+        for (int j = tid; j < N; j += kThreads) buf0[j] = mk<R>(in[2 * j], in[2 * j + 1]);
+    } else {
+        for (int j = tid; j < N; j += kThreads) buf0[j] = mk<R>(in[j], (R)0);
+    }
+    __syncthreads();
+
+    C *res = stockham<false, R>(buf0, buf1, N, T, tstep, s_rad, s_np);
+    C *Y = (res == buf0) ? buf1 : buf0;
+    if (even) {
+        for (int k = tid; k < nb; k += kThreads) {
+            const C z = res[k % N];
+            const C zc = cconj(res[(N - k) % N]);
+            C w = T[2 * k];  // e^{2 pi i k / n}; conjugated below
+            w.y = -w.y;
+            const C e = cadd(z, zc);
+            const C o = cmul(w, csub(z, zc));
+            // Y_k = e/2 - (i/2) o
+            Y[k] = mk<R>((R)0.5 * (e.x + o.y), (R)0.5 * (e.y - o.x));
+        }
+    } else {
+        for (int k = tid; k < nb; k += kThreads) Y[k] = res[k];
+    }
+    __syncthreads();
+
+    C *q = qout + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
+    for (int m = tid; m <= M; m += kThreads) {
+        const int k = m % n;
+        const C yk = (k < nb) ? Y[k] : cconj(Y[n - k]);
+        C ph;
+        if (ps >= 0) {
+            ph = T[(int)(((long long)m * ps) % (2 * n))];
+        } else {
+            double sn, cs;
+            sincos((double)m * phi0, &sn, &cs);
+            ph = mk<R>((R)cs, (R)sn);
+        }
+        q[m] = cmul(yk, cconj(ph));
+    }
+}
+
+template <typename R>
+cudaError_t launch_analysis(const DevPlan &P, const R *map, typename C2T<R>::type *q, int nmaps,
+                            cudaStream_t st)
+{
+    if (nmaps <= 0) return cudaSuccess;
+    const size_t smem = ring_smem_bytes(P, sizeof(R) == 8);
+    auto kern = ring_analysis_kernel<R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(P.nrings, nmaps);
+    kern<<<grid, kThreads, smem, st>>>(P, map, q);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -319,4 +433,18 @@ cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float 
     return launch_synth<float>(P, delta, map, nmaps, st);
 }
 
+}  // namespace sht
+
+namespace sht {
+cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
+                                      cudaStream_t st)
+{
+    return launch_analysis<double>(P, map, q, nmaps, st);
+}
+
+cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
+                                      cudaStream_t st)
+{
+    return launch_analysis<float>(P, map, q, nmaps, st);
+}
 }  // namespace sht

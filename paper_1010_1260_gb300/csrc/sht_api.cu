@@ -569,12 +569,37 @@ int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, voi
     g_err.clear();
     int rc = check_plan(p);
     if (rc) return rc;
-    (void)nbatch;
-    (void)map_dev;
-    (void)alm_dev;
-    (void)prec;
-    (void)stream;
-    return fail(SHT_EUNSUPPORTED, "map2alm_adjoint not built yet");
+    if (nbatch < 0) return fail(SHT_EINVAL, "nbatch < 0");
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC)
+        return fail(SHT_EINVAL, "unknown precision %d", prec);
+    if (nbatch == 0) return SHT_OK;
+    if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
+    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "precision %d not built for the adjoint", prec);
+    if (sht::legendre_adj_smem_bytes(p->dp, 4) == 0)
+        return fail(SHT_EUNSUPPORTED, "adjoint: %d ring pairs exceed the shared-memory state", p->npairs);
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
+    size_t chunk_sz = std::max<size_t>(1, max_ws_bytes() / per_map);
+    int chunk = (int)std::min<size_t>(chunk_sz, 32768);
+    chunk = std::min(chunk, nbatch);
+    if ((rc = ensure_ws(p, per_map * chunk))) return rc;
+    const double *map = static_cast<const double *>(map_dev);
+    double2 *alm = static_cast<double2 *>(alm_dev);
+    double2 *q = static_cast<double2 *>(p->ws);
+    for (int b0 = 0; b0 < nbatch; b0 += chunk) {
+        const int nb = std::min(chunk, nbatch - b0);
+        StageScope s1(p, SHT_STAGE_ADJ_RING, st);
+        cudaError_t e = sht::launch_ring_analysis_fp64(p->dp, map + (size_t)b0 * p->npix, q, nb, st);
+        s1.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "ring_analysis_fp64 launch");
+        StageScope s2(p, SHT_STAGE_ADJ_LEGENDRE, st);
+        e = sht::launch_legendre_adj_fp64(p->dp, q, alm + (size_t)b0 * p->nalm, nb, st);
+        s2.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_adj_fp64 launch");
+    }
+    return SHT_OK;
 }
 
 unsigned long long sht_kernel_launches(void) { return g_launches.load(); }

@@ -56,6 +56,19 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
 cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float *map, int nmaps,
                                    cudaStream_t st);
 
+// Ring step of the transpose: q[b][ring][m] = sum_j y_j e^{-i m phi_j}.
+cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
+                                      cudaStream_t st);
+cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
+                                      cudaStream_t st);
+
+// Legendre step of the transpose, FP64:
+//   g[b][idx(l, m)] = c_m sum_r lambda_lm(x_r) q[b][r][m],  c_0 = 1, c_m = 2.
+cudaError_t launch_legendre_adj_fp64(const DevPlan &P, const double2 *q, double2 *g, int nmaps,
+                                     cudaStream_t st);
+// Shared memory the FP64 adjoint Legendre kernel needs (0 if the plan has too many ring pairs).
+size_t legendre_adj_smem_bytes(const DevPlan &P, int bc);
+
 // Shared-memory bytes the ring kernels need for this plan.
 size_t ring_smem_bytes(const DevPlan &P, bool fp64);
 inline size_t ring_smem_bytes_for_cap(int cap, bool fp64)
