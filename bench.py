@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "alm2map maps/s at lmax=2048 (HEALPix nside 1024, batch of 64 maps)"
 UNIT = "maps/s"
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe): ~2 DFMA/clk/SM x 152 SMs x 2.07 GHz
 DTYPE = {"fp64": "f64", "fp32_tc": "f64 recurrence + tf32x3 MMA / f32", "bf16x3_tc": "f64 recurrence + bf16 split MMA / f32"}
 
 
@@ -305,7 +305,7 @@ def run_ours(args):
         ach = fl / (dom_ms * 1e-3) / 1e12
         roof = {"kernel": "legendre_fwd_fp64", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_fwd_fp64"),
-                "peak_source": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "peak_source": "nominal FP64 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2070 MHz); ncu fp64 pipe active is the cross-check",
                 "flops_per_launch": fl, "ms_per_launch": dom_ms}
     elif dom == "ring":
         npix = 12 * args.nside ** 2
