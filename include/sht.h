@@ -112,6 +112,27 @@ int sht_alm2map_batch(sht_plan_t plan, int nbatch, const void *alm_dev, void *ma
 int sht_map2alm_adjoint_batch(sht_plan_t plan, int nbatch, const void *map_dev, void *alm_dev,
                               int prec, void *stream);
 
+/* FP64 alm2map that allocates nothing (the paper has no counterpart: this is
+ * an interface for callers that must not allocate device memory once their
+ * processing loop runs, e.g. a host framework that has reserved nearly all
+ * device memory for its own pool, or a latency-critical pipeline in which an
+ * allocation after start-up is not acceptable).  Same arguments and result as
+ * sht_alm2map_batch(plan, nbatch, alm_dev, map_dev, SHT_FP64, stream), but the
+ * Delta_m scratch lives in a 16 MiB array that the library reserves statically
+ * on every GPU that loads it, for the life of the process; the call allocates
+ * no device memory and calls no cudaMalloc, cudaFree or other allocating CUDA
+ * or PyTorch routine (a rejected call only records its error message, like
+ * every libsht call).  The plan itself is created (and allocates its tables)
+ * beforehand with sht_plan.
+ * Limit: nbatch * nrings * (mmax + 1) <= 1,048,576 (16 MiB of complex128), else
+ * SHT_EUNSUPPORTED.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the one scratch array: calls
+ * that overlap on the GPU (different streams, no ordering) race and corrupt
+ * each other's results.  The scratch keeps the last call's contents; every
+ * entry a call reads is first written by that call. */
+int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *map_dev, void *stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *sht_last_error(void);
 

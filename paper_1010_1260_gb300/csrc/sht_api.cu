@@ -650,3 +650,14 @@ int sht_map2alm_adjoint(sht_plan_t p, const void *map_dev, void *alm_dev, int pr
 }
 
 }  // extern "C"
+
+// Internal hooks for other translation units of the library (not C ABI).
+namespace sht {
+const DevPlan *plan_dev(sht_plan_t p) { return p ? &p->dp : nullptr; }
+int plan_device(sht_plan_t p) { return p ? p->device : -1; }
+std::mutex *plan_mutex(sht_plan_t p) { return p ? &p->mu : nullptr; }
+int record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+int record_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+void clear_error() { g_err.clear(); }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace sht
