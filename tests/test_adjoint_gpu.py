@@ -158,5 +158,5 @@ def test_finite_differences_weighted_loss(sht, nside, lmax, nmaps):
             lm = float(_loss(plan, a0 - e, w, d))
         fd = (lp - lm) / (2 * h)
         an = float(grad[b, i].real if comp == 0 else grad[b, i].imag)
-        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * float(L) / plan.npix))
+        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * float(L.detach()) / plan.npix))
     assert worst < 1e-6, worst
