@@ -71,8 +71,10 @@ typedef struct {
 typedef enum {
     SHT_FP64 = 0,      /* FP64 recurrence, FP64 contraction, FP64 ring FFT; float64 map */
     SHT_FP32_TC = 1,   /* FP64 recurrence, 3xTF32 tensor-core contraction, FP32 ring FFT; float32 map */
-    SHT_BF16X3_TC = 2  /* FP64 recurrence, split-BF16 (hi/lo, 3 products) tensor-core contraction,
+    SHT_BF16X3_TC = 2, /* FP64 recurrence, split-BF16 (hi/lo, 3 products) tensor-core contraction,
                           FP32 ring FFT; float32 map */
+    SHT_BF16X6_TC = 3  /* as SHT_BF16X3_TC with three BF16 pieces and 6 products (hi*hi, hi*mid,
+                          mid*hi, hi*lo, mid*mid, lo*hi) */
 } sht_prec;
 
 /* Build a plan for grid g and band limits 0 <= mmax <= lmax on the current
@@ -96,7 +98,8 @@ int sht_mmax(sht_plan_t plan);
 
 /* alm2map of one map (Eq. alm2mapDef via Eq. DeltaDef and Eq. Delta2map).
  * alm_dev: nalm complex128 (device); map_dev: npix reals (device), fully
- * overwritten.  prec: sht_prec (selects the map's float type). */
+ * overwritten.  prec: sht_prec (selects the map's float type).  The
+ * tensor-core forms process batches in groups of up to 64 maps. */
 int sht_alm2map(sht_plan_t plan, const void *alm_dev, void *map_dev, int prec, void *stream);
 
 /* Real-linear transpose of alm2map (Eq. map2almDef without quadrature weights):
@@ -151,6 +154,12 @@ const char *sht_last_error(void);
 #define SHT_NSTAGES 4
 int sht_profile(sht_plan_t plan, int enable);
 int sht_profile_read(sht_plan_t plan, int nstage, double *ms, long long *launches);
+
+/* Wait for all work on the plan's device and report device-side failures:
+ * SHT_ETIMEOUT if a kernel of this plan gave up a bounded wait (the kernel
+ * then returned early and its output is invalid; the flag is cleared),
+ * SHT_ECUDA for a CUDA error, else SHT_OK. */
+int sht_sync(sht_plan_t plan);
 
 /* Number of kernels libsht has launched in this process (all plans). */
 unsigned long long sht_kernel_launches(void);

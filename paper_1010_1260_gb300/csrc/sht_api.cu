@@ -34,6 +34,8 @@ struct sht_plan_s {
     std::vector<void *> allocs;
     void *ws = nullptr;  // Delta workspace
     size_t ws_bytes = 0;
+    sht::TcWork tc;      // tensor-core forms: segment tables, status word, B-operand buffer
+    size_t tc_bytes = 0;
     std::mutex mu;
 };
 
@@ -192,6 +194,7 @@ void free_plan(sht_plan_s *p)
         cudaDeviceSynchronize();
         for (void *d : p->allocs) cudaFree(d);
         if (p->ws) cudaFree(p->ws);
+        if (p->tc.bbuf) cudaFree(p->tc.bbuf);
         for (auto &e : p->prof_pending) {
             cudaEventDestroy(e.a);
             cudaEventDestroy(e.b);
@@ -390,6 +393,38 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, twofs, &d.twofs))) return rc;
     if ((rc = upload(p, tw64, &d.tw64))) return rc;
     if ((rc = upload(p, tw32, &d.tw32))) return rc;
+
+    // tensor-core forms: (m, parity) segments of the B operand, padded to
+    // whole stages of KC degrees per parity (KC = 8 for TF32, 16 for BF16)
+    for (int pass = 0; pass < 2; ++pass) {
+        const int kc = pass == 0 ? 8 : 16;
+        std::vector<int> seg(2 * (size_t)(M + 1));
+        long long off = 0;
+        for (int m = 0; m <= M; ++m) {
+            const long long kpad = (long long)((L - m + 1 + 2 * kc - 1) / (2 * kc)) * kc;
+            seg[2 * m] = (int)off;
+            off += kpad;
+            seg[2 * m + 1] = (int)off;
+            off += kpad;
+        }
+        if (off > 0x7fffffffLL) return fail(SHT_EUNSUPPORTED, "tensor-core operand too large");
+        if (pass == 0) {
+            if ((rc = upload(p, seg, &p->tc.seg_tf32))) return rc;
+            p->tc.kall_tf32 = off;
+        } else {
+            if ((rc = upload(p, seg, &p->tc.seg_bf16))) return rc;
+            p->tc.kall_bf16 = off;
+        }
+    }
+    {
+        void *st = nullptr;
+        cudaError_t e = cudaMalloc(&st, sizeof(int));
+        if (e != cudaSuccess) return fail(SHT_ENOMEM, "cudaMalloc(status): %s", cudaGetErrorString(e));
+        p->allocs.push_back(st);
+        e = cudaMemset(st, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+        p->tc.status = static_cast<int *>(st);
+    }
     return SHT_OK;
 }
 
@@ -412,6 +447,25 @@ int ensure_ws(sht_plan_s *p, size_t bytes)
     return SHT_OK;
 }
 
+int ensure_tc(sht_plan_s *p, int prec)
+{
+    const size_t need = sht::tc_bbuf_bytes(p->tc, prec);
+    if (p->tc_bytes >= need) return SHT_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if (p->tc.bbuf) cudaFree(p->tc.bbuf);
+    p->tc.bbuf = nullptr;
+    p->tc_bytes = 0;
+    e = cudaMalloc(&p->tc.bbuf, need);
+    if (e != cudaSuccess) {
+        p->tc.bbuf = nullptr;
+        cudaGetLastError();
+        return fail(SHT_ENOMEM, "tensor-core operand cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+    }
+    p->tc_bytes = need;
+    return SHT_OK;
+}
+
 size_t max_ws_bytes()
 {
     const char *env = std::getenv("SHT_MAX_WORKSPACE_MB");
@@ -425,6 +479,39 @@ size_t max_ws_bytes()
 int check_plan(sht_plan_t p)
 {
     if (!p) return fail(SHT_EINVAL, "null plan");
+    return SHT_OK;
+}
+
+// Precision forms: FP64 recurrence + tensor-core contraction (groups of at
+// most 64 maps), FP32 Delta, FP32 ring step, float32 maps.
+int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, int prec, void *stream)
+{
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc;
+    const int group = std::min(nbatch, sht::kTcMaxMaps);
+    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(float2);
+    if ((rc = ensure_ws(p, per_map * group))) return rc;
+    if ((rc = ensure_tc(p, prec))) return rc;
+    const double2 *alm = static_cast<const double2 *>(alm_dev);
+    float *map = static_cast<float *>(map_dev);
+    float2 *delta = static_cast<float2 *>(p->ws);
+    for (int b0 = 0; b0 < nbatch; b0 += group) {
+        const int nb = std::min(group, nbatch - b0);
+        StageScope s0(p, SHT_STAGE_LEGENDRE, st);
+        cudaError_t e = sht::launch_tc_prep(p->dp, p->tc, prec, alm + (size_t)b0 * p->nalm, nb, st);
+        s0.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
+        StageScope s1(p, SHT_STAGE_LEGENDRE, st);
+        e = sht::launch_tc_main(p->dp, p->tc, prec, delta, nb, st);
+        s1.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_tc launch");
+        StageScope s2(p, SHT_STAGE_RING, st);
+        e = sht::launch_ring_synth_fp32(p->dp, delta, map + (size_t)b0 * p->npix, nb, st);
+        s2.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp32 launch");
+    }
     return SHT_OK;
 }
 
@@ -528,11 +615,11 @@ int sht_alm2map_batch(sht_plan_t p, int nbatch, const void *alm_dev, void *map_d
     int rc = check_plan(p);
     if (rc) return rc;
     if (nbatch < 0) return fail(SHT_EINVAL, "nbatch < 0");
-    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC)
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
         return fail(SHT_EINVAL, "unknown precision %d", prec);
     if (nbatch == 0) return SHT_OK;
     if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
-    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "precision %d not built", prec);
+    if (prec != SHT_FP64) return alm2map_tc(p, nbatch, alm_dev, map_dev, prec, stream);
     std::lock_guard<std::mutex> lk(p->mu);
     DeviceGuard dg(p->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -570,7 +657,7 @@ int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, voi
     int rc = check_plan(p);
     if (rc) return rc;
     if (nbatch < 0) return fail(SHT_EINVAL, "nbatch < 0");
-    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC)
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
         return fail(SHT_EINVAL, "unknown precision %d", prec);
     if (nbatch == 0) return SHT_OK;
     if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
@@ -603,6 +690,25 @@ int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, voi
 }
 
 unsigned long long sht_kernel_launches(void) { return g_launches.load(); }
+
+int sht_sync(sht_plan_t p)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, p->tc.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st != 0) {
+        const int zero = 0;
+        cudaMemcpy(p->tc.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(SHT_ETIMEOUT, "a bounded device-side wait gave up (kernel status %d)", st);
+    }
+    return SHT_OK;
+}
 
 int sht_profile(sht_plan_t p, int enable)
 {

@@ -69,6 +69,27 @@ cudaError_t launch_legendre_adj_fp64(const DevPlan &P, const double2 *q, double2
 // Shared memory the FP64 adjoint Legendre kernel needs (0 if the plan has too many ring pairs).
 size_t legendre_adj_smem_bytes(const DevPlan &P, int bc);
 
+// Tensor-core Legendre step (precision forms).  Per launch group of at most
+// kTcMaxMaps maps, the B operand (C_l a_lm split into TF32 / BF16 pieces) is
+// laid out per (m, parity) segment of padded length K in bbuf; seg_* hold the
+// segment offsets ([mmax+1][2]) for the TF32 (K chunk 8) and BF16 (K chunk 16)
+// layouts, kall_* the total padded K.  status: device word set to SHT_ETIMEOUT
+// when a bounded device-side wait gives up.
+constexpr int kTcMaxMaps = 64;
+struct TcWork {
+    const int *seg_tf32 = nullptr;
+    const int *seg_bf16 = nullptr;
+    long long kall_tf32 = 0, kall_bf16 = 0;
+    void *bbuf = nullptr;
+    int *status = nullptr;
+};
+inline int tc_ncols(int nmaps) { return ((2 * nmaps + 31) / 32) * 32; }
+size_t tc_bbuf_bytes(const TcWork &W, int prec);
+cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const double2 *alm, int nmaps,
+                           cudaStream_t st);
+cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, float2 *delta, int nmaps,
+                           cudaStream_t st);
+
 // Shared-memory bytes the ring kernels need for this plan.
 size_t ring_smem_bytes(const DevPlan &P, bool fp64);
 inline size_t ring_smem_bytes_for_cap(int cap, bool fp64)

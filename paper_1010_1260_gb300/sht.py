@@ -29,8 +29,9 @@ SHT_EUNSUPPORTED = -4
 SHT_ETIMEOUT = -5
 
 GRID_GL, GRID_HEALPIX, GRID_RINGS = 0, 1, 2
-PREC = {"fp64": 0, "fp32_tc": 1, "bf16x3_tc": 2}
-MAP_DTYPE = {"fp64": torch.float64, "fp32_tc": torch.float32, "bf16x3_tc": torch.float32}
+PREC = {"fp64": 0, "fp32_tc": 1, "bf16x3_tc": 2, "bf16x6_tc": 3}
+MAP_DTYPE = {"fp64": torch.float64, "fp32_tc": torch.float32, "bf16x3_tc": torch.float32,
+             "bf16x6_tc": torch.float32}
 
 
 class ShtError(RuntimeError):
@@ -73,11 +74,12 @@ def lib():
             L.sht_last_error.restype = ctypes.c_char_p
             L.sht_profile.argtypes = [P, I]
             L.sht_profile_read.argtypes = [P, I, V, V]
+            L.sht_sync.argtypes = [P]
             L.sht_kernel_launches.argtypes = []
             L.sht_kernel_launches.restype = ctypes.c_ulonglong
             for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
                       "sht_alm2map_batch", "sht_map2alm_adjoint_batch", "sht_profile",
-                      "sht_profile_read"):
+                      "sht_profile_read", "sht_sync"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -200,6 +202,11 @@ class Plan:
         check(lib().sht_map2alm_adjoint_batch(self._h, B, y.data_ptr(), out.data_ptr(), PREC[prec],
                                               _stream_ptr(stream)))
         return out.reshape(self.nalm) if single else out.reshape(B, self.nalm)
+
+    def sync(self):
+        """Wait for the plan's device; raise ShtError(SHT_ETIMEOUT) if a kernel
+        of this plan gave up a bounded device-side wait."""
+        check(lib().sht_sync(self._h))
 
     # ---------------------------------------------------------- profiling --
     def profile(self, enable: bool = True):

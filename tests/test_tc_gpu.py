@@ -1,0 +1,83 @@
+"""Precision forms of alm2map on the GPU: FP64 recurrence, tensor-core
+contraction (3xTF32, split-BF16 with 3 products, BF16 with 3 pieces and 6
+products), FP32 ring step.  Error per map is the relative L2 norm against the
+FP64 oracle, ||s - s_ref||_2 / ||s_ref||_2; targets: 1e-5 for the TF32 form,
+1e-6 for the BF16 forms (the 3-product BF16 form is reported, and checked
+against the bound its two 8-bit pieces allow, 3e-5)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1010_1260_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32_tc": 1e-5, "bf16x3_tc": 3e-5, "bf16x6_tc": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def sht():
+    from paper_1010_1260_gb300 import sht as s
+    s.lib()
+    return s
+
+
+def _rl2(got, want):
+    ok = np.isfinite(want)
+    return float(np.linalg.norm(got[ok] - want[ok]) / np.linalg.norm(want[ok]))
+
+
+def _grids(oracle_mod, sht, kind, size):
+    if kind == "hp":
+        return oracle_mod.healpix_grid(size), sht.healpix(size)
+    return oracle_mod.gl_grid(*size), sht.gl(*size)
+
+
+CASES = [
+    ("hp", 16, 40, 40, 3),
+    ("hp", 37, 70, 61, 1),      # 74 ring pairs (< 128), lmax - m not a multiple of the stage
+    ("hp", 8, 100, 100, 33),    # aliasing; 66 columns -> N = 96
+    ("gl", (128, 256), 127, 127, 2),
+    ("hp", 64, 130, 130, 65),   # two launch groups (64 + 1 maps), 255 rings -> 2 ring blocks
+]
+
+
+@pytest.mark.parametrize("prec", ["fp32_tc", "bf16x3_tc", "bf16x6_tc"])
+@pytest.mark.parametrize("case", CASES)
+def test_tc_forms_vs_oracle(oracle_mod, sht, case, prec):
+    kind, size, lmax, mmax, nmaps = case
+    og, sg = _grids(oracle_mod, sht, kind, size)
+    alm = inputs.batch_alm(lmax, mmax, 300 + lmax, nmaps)
+    plan = sht.Plan(sg, lmax, mmax)
+    got = plan.alm2map(torch.from_numpy(alm).cuda(), prec)
+    plan.sync()
+    got = got.double().cpu().numpy()
+    want = oracle_mod.alm2map(og, lmax, mmax, alm)
+    errs = [_rl2(got[b], want[b]) for b in range(nmaps)]
+    assert max(errs) < TOL[prec], (prec, max(errs))
+
+
+@pytest.mark.parametrize("prec", ["fp32_tc", "bf16x6_tc"])
+def test_tc_full_size_sampled_rings(oracle_mod, sht, prec):
+    """HEALPix nside 1024, lmax 2048, a batch of 64 maps (the benchmark's
+    workload); maps 0 and 63 checked on sampled rings, per map."""
+    og, sg = _grids(oracle_mod, sht, "hp", 1024)
+    alm = inputs.batch_alm(2048, 2048, 3, 64)
+    plan = sht.Plan(sg, 2048)
+    out = plan.alm2map(torch.from_numpy(alm).cuda(), prec)
+    plan.sync()
+    rings = inputs.sample_rings(og["nrings"], 10, 33)
+    for b in (0, 63):
+        want = oracle_mod.alm2map(og, 2048, 2048, alm[b: b + 1], rings=rings)[0]
+        got = out[b].double().cpu().numpy()
+        assert _rl2(got, want) < TOL[prec]
+
+
+def test_tc_batch_equals_singles(sht):
+    plan = sht.Plan(sht.healpix(16), 47)
+    alm = torch.from_numpy(inputs.batch_alm(47, 47, 9, 5)).cuda()
+    batch = plan.alm2map(alm, "fp32_tc")
+    for b in range(5):
+        single = plan.alm2map(alm[b], "fp32_tc")
+        assert torch.allclose(single, batch[b], rtol=0, atol=1e-6 * float(batch[b].abs().max()))
+    plan.sync()
