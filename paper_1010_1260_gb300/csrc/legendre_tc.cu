@@ -12,14 +12,25 @@
 // products hi*hi + hi*lo + lo*hi (+ the second-order terms for 3 pieces)
 // accumulate in FP32 in tensor memory.
 //
-// CTA (192 threads) = (block of 128 ring pairs, m, group of <= 64 maps):
-//   warps 0-3  one ring pair per thread: FP64 recurrence -> split pieces ->
-//              swizzled K-major A tiles in shared memory; at the end, the
-//              epilogue reads E and O from tensor memory (tcgen05.ld) and
-//              writes Delta in FP32;
-//   warp 4     allocates tensor memory and loads the B tiles with TMA;
-//   warp 5     one thread issues tcgen05.mma (M = 128, N = 2 x maps, K = one
-//              chunk) and releases stages with tcgen05.commit.
+// Persistent kernel, one CTA (10 warps) per SM; work item = (m, block of 128
+// ring pairs) for a group of <= 64 maps, heavy (small m) items first:
+//   warps 0-3  one ring pair per thread: FP64 recurrence (recurrence
+//              coefficients prefetched a stage ahead and broadcast by warp
+//              shuffle, so the only dependent chain is one DFMA per degree)
+//              -> pieces -> swizzled K-major A tiles in shared memory;
+//   warp 8     allocates tensor memory and loads each stage's B tiles with
+//              one bulk copy (the operand prep writes them pre-swizzled and
+//              contiguous), prefetching the next stages into L2;
+//   warp 9     one thread issues tcgen05.mma (M = 128, N = 2 x maps, K = one
+//              chunk) and releases stages with tcgen05.commit;
+//   warps 4-7  drain: the MMAs of every 64 degrees accumulate into one of two
+//              tensor-memory accumulator sets; the drain warps read a finished
+//              set (tcgen05.ld), add it in FP32 (round to nearest) into
+//              per-row totals in shared memory, release the set, and at the
+//              end of an item write Delta.  The tensor core's FP32
+//              accumulation rounds toward zero, which over ~400 accumulating
+//              MMAs biases the result by ~1e-5; summing short groups on the
+//              CUDA cores removes the bias.
 // Stages hold KC degrees of each parity (one MMA K step); NS stages rotate
 // through mbarriers.  Every wait is bounded by a global-timer limit; on
 // timeout the CTA records an error in the plan's status word, drains its
@@ -27,9 +38,8 @@
 #include "sht.h"
 #include "sht_internal.cuh"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -38,7 +48,6 @@ namespace {
 
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s per wait
 constexpr int kRows = 128;                      // ring pairs per CTA = MMA M
-constexpr int kThreads = 192;
 constexpr int kRowBytes = 32;                   // one K chunk per tile row (SW32 swizzle)
 constexpr int kTileBytes = kRows * kRowBytes;   // 4 KB per operand tile (N <= 128 rows for B)
 
@@ -106,13 +115,18 @@ __device__ __forceinline__ void fence_proxy_async()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+// Contiguous bulk copy global -> shared completing on an mbarrier, and an L2
+// prefetch of a contiguous range (no shared memory used).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
+                 : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -211,24 +225,20 @@ __device__ __forceinline__ bool above_hi(double v)
     return e > 1023 + kScaleHi;
 }
 
-// tensor-memory columns for the E and O accumulators (power of two >= 32)
-__device__ __forceinline__ uint32_t tmem_cols(int ncols)
-{
-    const int need = 2 * ncols;
-    return need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : 256u));
-}
-
 template <bool BF16, int NPA, int NPB>
 struct Cfg {
     static constexpr int KC = BF16 ? 16 : 8;   // degrees of one parity per stage = MMA K
     static constexpr int VEC = BF16 ? 8 : 4;   // values per 16-byte chunk
     static constexpr int NCHUNK = KC / VEC;    // 16-byte chunks per tile row (= 2)
+    static constexpr int STEPS = 2 * KC;       // consecutive degrees per stage
     static constexpr int A_TILES = 2 * NPA;    // [parity][piece]
     static constexpr int B_TILES = 2 * NPB;
     static constexpr int STAGE_BYTES = (A_TILES + B_TILES) * kTileBytes;
-    static constexpr int NS = (STAGE_BYTES * 3 <= 100 * 1024) ? 3 : 2;
+    static constexpr int NS = (STAGE_BYTES * 3 <= 96 * 1024) ? 3 : 2;
     static constexpr int NPROD = (NPA == 2 && NPB == 2) ? 3 : 6;
-    static constexpr int SMEM = NS * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
+    static constexpr int GROUP = 64 / STEPS;   // stages per accumulation group (64 degrees)
+    static constexpr int TOT_BYTES = kRows * 256 * 4;  // FP32 totals, [column][row]
+    static constexpr int SMEM = NS * STAGE_BYTES + TOT_BYTES + 1024 /* align */ + 256 /* barriers */;
 };
 
 template <int NPA, int NPB>
@@ -241,39 +251,128 @@ __device__ __forceinline__ void product_pieces(int i, int &ia, int &ib)
     ib = b[i];
 }
 
+// One producer stage: 2 KC consecutive degrees of one ring pair (row t),
+// written as NPA pieces into the stage's A tiles ([parity][piece], 4 KB
+// each, K-major rows of 32 bytes with the 32-byte swizzle).  a_cur holds
+// A_{l+1} for the stage's degrees, one per lane.  With SLOW = false (no ring
+// of the warp still rescaled) the stage is one branch-free block: the FP64
+// chain of DFMAs, then the conversions, which the compiler interleaves with
+// the chain's latency.  With SLOW = true rescaled rings contribute zeros and
+// the rescale test runs once per chunk of 2 VEC degrees (the values grow by
+// far less than 2^512 over a chunk).
+template <bool BF16, int NPA, bool SLOW>
+__device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, double x, double a_cur, int l, int L,
+                                              double &p0, double &p1, int &k)
+{
+    constexpr int KC = BF16 ? 16 : 8;
+    constexpr int VEC = BF16 ? 8 : 4;
+    constexpr int NCH = KC / VEC;
+    constexpr int STEPS = 2 * KC;
+    double ax[STEPS], vv[STEPS];
+#pragma unroll
+    for (int q = 0; q < STEPS; ++q) ax[q] = __shfl_sync(0xffffffffu, a_cur, q) * x;
+    if (!SLOW) {
+#pragma unroll
+        for (int q = 0; q < STEPS; ++q) {
+            vv[q] = p1;
+            const double tt = fma(ax[q], p1, -p0);
+            p0 = p1;
+            p1 = tt;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const bool live_k = (k == 0);
+#pragma unroll
+            for (int q = c * 2 * VEC; q < (c + 1) * 2 * VEC; ++q) {
+                vv[q] = live_k ? p1 : 0.0;
+                const double tt = fma(ax[q], p1, -p0);
+                p0 = p1;
+                p1 = tt;
+            }
+            if (k < 0 && above_hi(p1)) {
+                p1 *= 0x1p-512;
+                p0 *= 0x1p-512;
+                k += 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        uint32_t pe[NPA][VEC], po[NPA][VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int q = c * 2 * VEC + 2 * v;
+            uint32_t ce[NPA], co[NPA];
+            split_pieces<BF16, NPA>(rn_f32(l + q <= L ? vv[q] : 0.0), ce);
+            split_pieces<BF16, NPA>(rn_f32(l + q + 1 <= L ? vv[q + 1] : 0.0), co);
+#pragma unroll
+            for (int i = 0; i < NPA; ++i) {
+                pe[i][v] = ce[i];
+                po[i][v] = co[i];
+            }
+        }
+        const int off = t * kRowBytes + ((c ^ ((t >> 2) & 1)) << 4);
+#pragma unroll
+        for (int i = 0; i < NPA; ++i) {
+            uint4 we, wo;
+            if (BF16) {
+                we = make_uint4((pe[i][0] >> 16) | (pe[i][1] & 0xFFFF0000u), (pe[i][2] >> 16) | (pe[i][3] & 0xFFFF0000u),
+                                (pe[i][4 % VEC] >> 16) | (pe[i][5 % VEC] & 0xFFFF0000u),
+                                (pe[i][6 % VEC] >> 16) | (pe[i][7 % VEC] & 0xFFFF0000u));
+                wo = make_uint4((po[i][0] >> 16) | (po[i][1] & 0xFFFF0000u), (po[i][2] >> 16) | (po[i][3] & 0xFFFF0000u),
+                                (po[i][4 % VEC] >> 16) | (po[i][5 % VEC] & 0xFFFF0000u),
+                                (po[i][6 % VEC] >> 16) | (po[i][7 % VEC] & 0xFFFF0000u));
+            } else {
+                we = make_uint4(pe[i][0], pe[i][1], pe[i][2 % VEC], pe[i][3 % VEC]);
+                wo = make_uint4(po[i][0], po[i][1], po[i][2 % VEC], po[i][3 % VEC]);
+            }
+            *reinterpret_cast<uint4 *>(sbase + (0 * NPA + i) * kTileBytes + off) = we;
+            *reinterpret_cast<uint4 *>(sbase + (1 * NPA + i) * kTileBytes + off) = wo;
+        }
+    }
+}
+
+constexpr int kWarps = 10;    // 0-3 producers, 4-7 drain, 8 TMA + tensor memory, 9 MMA
+constexpr int kPrefetch = 8;  // stages of B tiles prefetched into L2 ahead of their load
+
+// Persistent kernel: CTA c handles work items c, c + gridDim.x, ... where
+// item j = (m = j / nrb, ring block rb = j % nrb): heavy (small m) items first.
 template <bool BF16, int NPA, int NPB>
-__global__ void __launch_bounds__(kThreads, 2)
-legendre_tc_kernel(const DevPlan P, const __grid_constant__ CUtensorMap tmB, const int *__restrict__ seg_off,
+__global__ void __launch_bounds__(kWarps * 32, 1)
+legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, const int *__restrict__ seg_off,
                    float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status)
 {
     using C = Cfg<BF16, NPA, NPB>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned stage area
     const uint32_t base_u32 = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (base_u32 & 1023u)) & 1023u;
     unsigned char *stage0 = smem_raw + pad;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + C::NS * C::STAGE_BYTES);
-    // bars: full_a[NS], full_b[NS], empty[NS], acc_full
+    float *tot = reinterpret_cast<float *>(stage0 + C::NS * C::STAGE_BYTES);  // [256][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + C::NS * C::STAGE_BYTES + C::TOT_BYTES);
+    // bars: full_a[NS], full_b[NS], empty[NS], set_full[2], set_empty[2], mma_drain
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
 
-    const int m = blockIdx.y;
     const int L = P.lmax;
-    const int pair_base = blockIdx.x * kRows;
+    const int nrb = (P.npairs + kRows - 1) / kRows;
+    const int nitems = nrb * (P.mmax + 1);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int nstages = (L - m + 1 + 2 * C::KC - 1) / (2 * C::KC);
 
     auto bar_full_a = [&](int s) { return smem_u32(&bars[s]); };
     auto bar_full_b = [&](int s) { return smem_u32(&bars[C::NS + s]); };
     auto bar_empty = [&](int s) { return smem_u32(&bars[2 * C::NS + s]); };
-    const uint32_t bar_acc = smem_u32(&bars[3 * C::NS]);
+    auto bar_set_full = [&](int j) { return smem_u32(&bars[3 * C::NS + j]); };
+    auto bar_set_empty = [&](int j) { return smem_u32(&bars[3 * C::NS + 2 + j]); };
+    const uint32_t bar_mma_drain = smem_u32(&bars[3 * C::NS + 4]);
     auto a_tile = [&](int s, int par, int piece) {
         return stage0 + s * C::STAGE_BYTES + (par * NPA + piece) * kTileBytes;
     };
     auto b_tile = [&](int s, int par, int piece) {
         return stage0 + s * C::STAGE_BYTES + (C::A_TILES + par * NPB + piece) * kTileBytes;
     };
+    auto nstages_of = [&](int m) { return (L - m + 1 + C::STEPS - 1) / C::STEPS; };
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -282,14 +381,18 @@ legendre_tc_kernel(const DevPlan P, const __grid_constant__ CUtensorMap tmB, con
             mbar_init(bar_full_b(s), 1);
             mbar_init(bar_empty(s), 1);
         }
-        mbar_init(bar_acc, 1);
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(bar_set_full(j), 1);
+            mbar_init(bar_set_empty(j), 4);
+        }
+        mbar_init(bar_mma_drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
-        // tensor memory: E in columns [0, ncols), O in [ncols, 2 ncols)
-        const uint32_t cols = tmem_cols(ncols);
+    if (warp == 8) {
+        // two accumulator sets of 256 columns: set j holds E in [256 j, 256 j + ncols)
+        // and O in [256 j + ncols, 256 j + 2 ncols)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(cols));
+                     "r"(512u));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -299,172 +402,183 @@ legendre_tc_kernel(const DevPlan P, const __grid_constant__ CUtensorMap tmB, con
 
     if (warp < 4) {
         // ------------------------------------------------------ producers --
-        const int t = threadIdx.x;  // row = ring pair within the block
-        const int pair = pair_base + t;
-        const bool live = pair < P.npairs;
-        double x = 0.0, p0 = 0.0, p1 = 0.0;
-        int k = 0;
-        if (live) {
-            x = P.pair_x[pair];
-            p1 = P.start_v[(size_t)m * P.npairs + pair];
-            k = P.start_k[(size_t)m * P.npairs + pair];
-        }
-        const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
-        // swizzled byte offset of row t, chunk c inside a tile
-        auto chunk_off = [&](int c) { return t * kRowBytes + ((c ^ ((t >> 2) & 1)) << 4); };
-        int l = m;
+        const int t = threadIdx.x;
+        uint32_t gs = 0;
         bool ok = true;
-        for (int i = 0; i < nstages && ok; ++i) {
-            const int s = i % C::NS;
-            const uint32_t ph = (uint32_t)(i / C::NS) & 1u;
-            ok = mbar_wait(bar_empty(s), ph ^ 1u, &s_abort);
-            if (!ok) break;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int m = item / nrb;
+            const int pair = (item % nrb) * kRows + t;
+            const bool live = pair < P.npairs;
+            double x = 0.0, p0 = 0.0, p1 = 0.0;
+            int k = 0;
+            if (live) {
+                x = P.pair_x[pair];
+                p1 = P.start_v[(size_t)m * P.npairs + pair];
+                k = P.start_k[(size_t)m * P.npairs + pair];
+            }
+            const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
+            const int nst = nstages_of(m);
+            // A_{l+1} for the stage's degrees, one per lane, prefetched a stage ahead
+            auto coef = [&](int lq) { return (lane < C::STEPS && lq <= L) ? __ldg(&P.coefA[mofs + (lq - m)]) : 0.0; };
+            double a_cur = coef(m + 1 + lane);
+            int l = m;
+            for (int i = 0; i < nst; ++i) {
+                const int s = (int)(gs % C::NS);
+                const uint32_t ph = (gs / C::NS) & 1u;
+                const double a_next = coef(m + (i + 1) * C::STEPS + 1 + lane);
+                ok = __all_sync(0xffffffffu, mbar_wait(bar_empty(s), ph ^ 1u, &s_abort));
+                if (!ok) break;
+                if (__any_sync(0xffffffffu, k < 0))
+                    produce_stage<BF16, NPA, true>(a_tile(s, 0, 0), t, x, a_cur, l, L, p0, p1, k);
+                else
+                    produce_stage<BF16, NPA, false>(a_tile(s, 0, 0), t, x, a_cur, l, L, p0, p1, k);
+                l += C::STEPS;
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_full_a(s));
+                ++gs;
+                a_cur = a_next;
+            }
+        }
+    } else if (warp < 8) {
+        // ----------------------------------------------------------- drain --
+        const int row = (warp - 4) * 32 + lane;  // tensor-memory lane = ring pair in the block
+        const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+        uint32_t gg = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int m = item / nrb;
+            const int pair = (item % nrb) * kRows + row;
+            const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP;
+            for (int g = 0; g < ngroups; ++g) {
+                const int set = (int)(gg & 1u);
+                ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
+                if (!ok) break;
+                tc_fence_after();
+                for (int c0 = 0; c0 < 2 * ncols; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(256 * set + c0), v);
+                    float *tp = tot + (size_t)c0 * kRows + row;
+                    if (g == 0) {
 #pragma unroll
-            for (int c = 0; c < C::NCHUNK; ++c) {
-                uint32_t pe[NPA][C::VEC], po[NPA][C::VEC];
-#pragma unroll
-                for (int v = 0; v < C::VEC; ++v) {
-#pragma unroll
-                    for (int par = 0; par < 2; ++par) {
-                        const double val = (k == 0 && l <= L) ? p1 : 0.0;
-                        uint32_t pc[NPA];
-                        split_pieces<BF16, NPA>(rn_f32(val), pc);
-#pragma unroll
-                        for (int q = 0; q < NPA; ++q) {
-                            if (par == 0) pe[q][v] = pc[q];
-                            else po[q][v] = pc[q];
-                        }
-                        // advance to l + 1
-                        const double A = (l + 1 <= L) ? __ldg(&P.coefA[mofs + (l + 1 - m)]) : 0.0;
-                        const double tt = fma(A * x, p1, -p0);
-                        p0 = p1;
-                        p1 = tt;
-                        if (k < 0 && above_hi(p1)) {
-                            p1 *= 0x1p-512;
-                            p0 *= 0x1p-512;
-                            k += 1;
-                        }
-                        ++l;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < NPA; ++q) {
-                    uint4 we, wo;
-                    if (BF16) {
-                        we = make_uint4((pe[q][0] >> 16) | (pe[q][1] & 0xFFFF0000u),
-                                        (pe[q][2] >> 16) | (pe[q][3] & 0xFFFF0000u),
-                                        (pe[q][4 % C::VEC] >> 16) | (pe[q][5 % C::VEC] & 0xFFFF0000u),
-                                        (pe[q][6 % C::VEC] >> 16) | (pe[q][7 % C::VEC] & 0xFFFF0000u));
-                        wo = make_uint4((po[q][0] >> 16) | (po[q][1] & 0xFFFF0000u),
-                                        (po[q][2] >> 16) | (po[q][3] & 0xFFFF0000u),
-                                        (po[q][4 % C::VEC] >> 16) | (po[q][5 % C::VEC] & 0xFFFF0000u),
-                                        (po[q][6 % C::VEC] >> 16) | (po[q][7 % C::VEC] & 0xFFFF0000u));
+                        for (int j = 0; j < 32; ++j) tp[j * kRows] = __uint_as_float(v[j]);
                     } else {
-                        we = make_uint4(pe[q][0], pe[q][1], pe[q][2 % C::VEC], pe[q][3 % C::VEC]);
-                        wo = make_uint4(po[q][0], po[q][1], po[q][2 % C::VEC], po[q][3 % C::VEC]);
-                    }
-                    *reinterpret_cast<uint4 *>(a_tile(s, 0, q) + chunk_off(c)) = we;
-                    *reinterpret_cast<uint4 *>(a_tile(s, 1, q) + chunk_off(c)) = wo;
-                }
-            }
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_full_a(s));
-        }
-        // ------------------------------------------------------- epilogue --
-        if (ok) ok = mbar_wait(bar_acc, 0u, &s_abort);
-        if (ok) {
-            tc_fence_after();
-            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-            const int2 rr = live ? P.pair_ring[pair] : make_int2(0, -1);
-            const int M1 = P.mmax + 1;
-            for (int c0 = 0; c0 < ncols; c0 += 32) {
-                uint32_t ev[32], ov[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)c0, ev);
-                tmem_ld32(tmem + lane_base + (uint32_t)(ncols + c0), ov);
-                if (live) {
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        const int b = (c0 + j) >> 1;
-                        if (b < nmaps) {
-                            const float er = __uint_as_float(ev[j]), ei = __uint_as_float(ev[j + 1]);
-                            const float orr = __uint_as_float(ov[j]), oi = __uint_as_float(ov[j + 1]);
-                            float2 *d = delta + (size_t)b * P.nrings * M1;
-                            d[(size_t)rr.x * M1 + m] = make_float2(er + orr, (m == 0) ? 0.f : ei + oi);
-                            if (rr.y >= 0)
-                                d[(size_t)rr.y * M1 + m] = make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
-                        }
+                        for (int j = 0; j < 32; ++j) tp[j * kRows] += __uint_as_float(v[j]);
                     }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_set_empty(set));
+                ++gg;
+            }
+            if (!ok) break;
+            // Delta_m(north) = E + O, Delta_m(south) = E - O for this item's rows
+            if (pair < P.npairs) {
+                const int2 rr = P.pair_ring[pair];
+                const int M1 = P.mmax + 1;
+                for (int b = 0; b < nmaps; ++b) {
+                    const float er = tot[(2 * b) * kRows + row], ei = tot[(2 * b + 1) * kRows + row];
+                    const float orr = tot[(ncols + 2 * b) * kRows + row];
+                    const float oi = tot[(ncols + 2 * b + 1) * kRows + row];
+                    float2 *d = delta + (size_t)b * P.nrings * M1;
+                    d[(size_t)rr.x * M1 + m] = make_float2(er + orr, (m == 0) ? 0.f : ei + oi);
+                    if (rr.y >= 0) d[(size_t)rr.y * M1 + m] = make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
                 }
             }
         }
-    } else if (warp == 4) {
-        // ------------------------------------------------------ TMA loads --
-        int issued = 0;
+    } else if (warp == 8) {
+        // ------------------------------------------------------ B loads --
+        // The operand prep wrote the B tiles of every (m, stage) as one
+        // contiguous block in the shared-memory image ([parity][piece] tiles
+        // of 4 KB, swizzled), so one bulk copy fills a stage.
         if (lane == 0) {
-            const int off0 = seg_off[2 * m], off1 = seg_off[2 * m + 1];
-            const uint32_t bytes = (uint32_t)(2 * NPB * ncols * kRowBytes);
-            for (int i = 0; i < nstages; ++i) {
-                const int s = i % C::NS;
-                const uint32_t ph = (uint32_t)(i / C::NS) & 1u;
-                if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) break;
-                mbar_expect_tx(bar_full_b(s), bytes);
-#pragma unroll
-                for (int q = 0; q < NPB; ++q) {
-                    tma_load_2d(smem_u32(b_tile(s, 0, q)), &tmB, off0 + i * C::KC, q * ncols, bar_full_b(s));
-                    tma_load_2d(smem_u32(b_tile(s, 1, q)), &tmB, off1 + i * C::KC, q * ncols, bar_full_b(s));
+            constexpr uint32_t SB = (uint32_t)C::B_TILES * kTileBytes;
+            uint32_t gs = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int m = item / nrb;
+                const unsigned char *blk = bbuf + (size_t)(seg_off[2 * m] / C::STEPS) * SB;
+                const int nst = nstages_of(m);
+                for (int i = 0; i < kPrefetch && i < nst; ++i) bulk_prefetch_l2(blk + (size_t)i * SB, SB);
+                for (int i = 0; i < nst; ++i) {
+                    const int s = (int)(gs % C::NS);
+                    const uint32_t ph = (gs / C::NS) & 1u;
+                    if (i + kPrefetch < nst) bulk_prefetch_l2(blk + (size_t)(i + kPrefetch) * SB, SB);
+                    if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(bar_full_b(s), SB);
+                    bulk_load(smem_u32(b_tile(s, 0, 0)), blk + (size_t)i * SB, SB, bar_full_b(s));
+                    ++gs;
                 }
-                ++issued;
             }
-            // after an abort, let the copies in flight land before the CTA exits
             if (s_abort) {
-                for (int i = (issued > C::NS ? issued - C::NS : 0); i < issued; ++i) {
-                    const int s = i % C::NS;
-                    mbar_drain(bar_full_b(s), (uint32_t)(i / C::NS) & 1u);
-                }
+                // let the copies in flight land before the CTA exits
+                const uint32_t first = gs > (uint32_t)C::NS ? gs - C::NS : 0u;
+                for (uint32_t j = first; j < gs; ++j) mbar_drain(bar_full_b((int)(j % C::NS)), (j / C::NS) & 1u);
             }
         }
     } else {
         // ----------------------------------------------------------- MMA --
         if (lane == 0) {
             const uint32_t id = idesc<BF16>(ncols);
-            int done = 0;
-            for (int i = 0; i < nstages; ++i) {
-                const int s = i % C::NS;
-                const uint32_t ph = (uint32_t)(i / C::NS) & 1u;
-                if (!mbar_wait(bar_full_a(s), ph, &s_abort)) break;
-                if (!mbar_wait(bar_full_b(s), ph, &s_abort)) break;
-                tc_fence_after();
-#pragma unroll
-                for (int par = 0; par < 2; ++par) {
-                    const uint32_t d = tmem + (uint32_t)(par * ncols);
-#pragma unroll
-                    for (int pr = 0; pr < C::NPROD; ++pr) {
-                        int ia, ib;
-                        product_pieces<NPA, NPB>(pr, ia, ib);
-                        const uint64_t ad = sdesc_sw32(smem_u32(a_tile(s, par, ia)));
-                        const uint64_t bd = sdesc_sw32(smem_u32(b_tile(s, par, ib)));
-                        tc_mma<BF16>(d, ad, bd, id, (i > 0 || pr > 0) ? 1u : 0u);
+            uint32_t gs = 0, gg = 0;
+            bool ok = true, issued = false;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int m = item / nrb;
+                const int nst = nstages_of(m);
+                for (int i0 = 0; i0 < nst && ok; i0 += C::GROUP) {
+                    const int set = (int)(gg & 1u);
+                    if (!mbar_wait(bar_set_empty(set), ((gg >> 1) & 1u) ^ 1u, &s_abort)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const int i1 = min(nst, i0 + C::GROUP);
+                    for (int i = i0; i < i1; ++i) {
+                        const int s = (int)(gs % C::NS);
+                        const uint32_t ph = (gs / C::NS) & 1u;
+                        if (!mbar_wait(bar_full_a(s), ph, &s_abort) || !mbar_wait(bar_full_b(s), ph, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+#pragma unroll
+                        for (int par = 0; par < 2; ++par) {
+                            const uint32_t d = tmem + (uint32_t)(256 * set + par * ncols);
+#pragma unroll
+                            for (int pr = 0; pr < C::NPROD; ++pr) {
+                                int ia, ib;
+                                product_pieces<NPA, NPB>(pr, ia, ib);
+                                const uint64_t ad = sdesc_sw32(smem_u32(a_tile(s, par, ia)));
+                                const uint64_t bd = sdesc_sw32(smem_u32(b_tile(s, par, ib)));
+                                tc_mma<BF16>(d, ad, bd, id, (i > i0 || pr > 0) ? 1u : 0u);
+                            }
+                        }
+                        issued = true;
+                        tc_commit(bar_empty(s));
+                        ++gs;
+                    }
+                    if (!ok) break;
+                    tc_commit(bar_set_full(set));
+                    ++gg;
                 }
-                tc_commit(bar_empty(s));
-                ++done;
             }
-            if (done == nstages) tc_commit(bar_acc);
-            else if (done > 0) {
-                // drain: the last commit releases its stage once all earlier MMAs finished
-                const int i = done - 1;
-                mbar_drain(bar_empty(i % C::NS), (uint32_t)(i / C::NS) & 1u);
+            if (!ok && issued) {
+                // wait (bounded) for the MMAs already issued before tensor memory is freed
+                tc_commit(bar_mma_drain);
+                mbar_drain(bar_mma_drain, 0u);
             }
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == 8) {
         tc_fence_after();
-        const uint32_t cols = tmem_cols(ncols);
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
     }
     if (threadIdx.x == 0 && s_abort) atomicExch(status, SHT_ETIMEOUT);
 }
@@ -472,21 +586,31 @@ legendre_tc_kernel(const DevPlan P, const __grid_constant__ CUtensorMap tmB, con
 // ------------------------------------------------------------ operand prep --
 // B[c][seg(m, par) + k] = pieces of C_l a_lm(map c/2, re or im), l = m + par + 2k,
 // zero for l > lmax, for maps beyond nmaps and for Im of m = 0.
+// B operand image: for every (m, stage) a contiguous block of 2 x NPB tiles
+// ([parity][piece], 4 KB each) laid out exactly as the kernel's shared-memory
+// B tiles: row c (= 2 map + {re, im}) of 32 bytes holds the stage's KC
+// degrees of one parity, 16-byte chunks swizzled by bit 2 of the row.  Entry
+// (par, c, k) holds the pieces of C_l a_lm(map c/2, re or im), l = m + par + 2k,
+// zero for l > lmax, for maps beyond nmaps and for Im of m = 0.
 template <bool BF16, int NPB>
 __global__ void prep_b_kernel(const DevPlan P, const double2 *__restrict__ alm, const int *__restrict__ seg_off,
-                              void *__restrict__ bout, long long kall, int nmaps, int ncols, int kc)
+                              unsigned char *__restrict__ bout, int nmaps, int ncols)
 {
+    constexpr int KC = BF16 ? 16 : 8;
+    constexpr int ESZ = BF16 ? 2 : 4;
+    constexpr size_t SB = (size_t)2 * NPB * kTileBytes;
     const int m = blockIdx.y;
     const int L = P.lmax;
-    const int nst = (L - m + 1 + 2 * kc - 1) / (2 * kc);
-    const int kpad = nst * kc;
+    const int nst = (L - m + 1 + 2 * KC - 1) / (2 * KC);
     const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
-    const int total = 2 * kpad * ncols;  // (par, c, k)
+    unsigned char *blk = bout + (size_t)(seg_off[2 * m] / (2 * KC)) * SB;
+    const int total = nst * 2 * ncols * KC;  // (stage, par, c, kk), kk fastest
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int k = idx % kpad;
-        const int c = (idx / kpad) % ncols;
-        const int par = idx / (kpad * ncols);
-        const int l = m + par + 2 * k;
+        const int kk = idx % KC;
+        const int c = (idx / KC) % ncols;
+        const int par = (idx / (KC * ncols)) % 2;
+        const int i = idx / (KC * ncols * 2);
+        const int l = m + par + 2 * (i * KC + kk);
         const int b = c >> 1;
         float v = 0.f;
         if (l <= L && b < nmaps && !(m == 0 && (c & 1))) {
@@ -495,42 +619,26 @@ __global__ void prep_b_kernel(const DevPlan P, const double2 *__restrict__ alm, 
         }
         uint32_t pc[NPB];
         split_pieces<BF16, NPB>(v, pc);
-        const long long col = seg_off[2 * m + par] + k;
+        const int byte = kk * ESZ;
+        const int off = c * kRowBytes + ((((byte >> 4) ^ ((c >> 2) & 1))) << 4) + (byte & 15);
 #pragma unroll
         for (int q = 0; q < NPB; ++q) {
-            const long long row = (long long)q * ncols + c;
+            unsigned char *dst = blk + (size_t)i * SB + (size_t)(par * NPB + q) * kTileBytes + off;
             if (BF16)
-                reinterpret_cast<uint16_t *>(bout)[row * kall + col] = (uint16_t)(pc[q] >> 16);
+                *reinterpret_cast<uint16_t *>(dst) = (uint16_t)(pc[q] >> 16);
             else
-                reinterpret_cast<uint32_t *>(bout)[row * kall + col] = pc[q];
+                *reinterpret_cast<uint32_t *>(dst) = pc[q];
         }
     }
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
 }
 
 template <bool BF16, int NPA, int NPB>
 cudaError_t run_prep(const DevPlan &P, const TcWork &W, const double2 *alm, int nmaps, cudaStream_t st)
 {
-    using C = Cfg<BF16, NPA, NPB>;
     const int ncols = tc_ncols(nmaps);
     const int *seg = BF16 ? W.seg_bf16 : W.seg_tf32;
-    const long long kall = BF16 ? W.kall_bf16 : W.kall_tf32;
     dim3 grid(64, P.mmax + 1);
-    prep_b_kernel<BF16, NPB><<<grid, 256, 0, st>>>(P, alm, seg, W.bbuf, kall, nmaps, ncols, C::KC);
+    prep_b_kernel<BF16, NPB><<<grid, 256, 0, st>>>(P, alm, seg, static_cast<unsigned char *>(W.bbuf), nmaps, ncols);
     return cudaGetLastError();
 }
 
@@ -540,24 +648,16 @@ cudaError_t run_main(const DevPlan &P, const TcWork &W, float2 *delta, int nmaps
     using C = Cfg<BF16, NPA, NPB>;
     const int ncols = tc_ncols(nmaps);
     const int *seg = BF16 ? W.seg_bf16 : W.seg_tf32;
-    const long long kall = BF16 ? W.kall_bf16 : W.kall_tf32;
-    // tensor map over the B pieces: rows (piece, c), columns K
-    auto enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    CUtensorMap tm;
-    const cuuint64_t dims[2] = {(cuuint64_t)kall, (cuuint64_t)(NPB * ncols)};
-    const cuuint64_t strides[1] = {(cuuint64_t)kall * (BF16 ? 2 : 4)};
-    const cuuint32_t box[2] = {(cuuint32_t)C::KC, (cuuint32_t)ncols};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&tm, BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, W.bbuf, dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     auto kern = legendre_tc_kernel<BF16, NPA, NPB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    dim3 grid((P.npairs + kRows - 1) / kRows, P.mmax + 1);
-    kern<<<grid, kThreads, C::SMEM, st>>>(P, tm, seg, delta, nmaps, ncols, W.status);
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long nitems = (long long)((P.npairs + kRows - 1) / kRows) * (P.mmax + 1);
+    const int grid = (int)std::min<long long>(nitems, nsm);  // persistent: one CTA per SM
+    kern<<<grid, kWarps * 32, C::SMEM, st>>>(P, static_cast<const unsigned char *>(W.bbuf), seg, delta, nmaps,
+                                             ncols, W.status);
     return cudaGetLastError();
 }
 

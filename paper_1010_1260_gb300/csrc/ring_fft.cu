@@ -88,18 +88,17 @@ __device__ int factorize(int N, int *rad)
 
 // Self-sorting (Stockham) mixed-radix complex DFT of length N in shared
 // memory, ping-ponging between src and dst; returns the buffer holding the
-// result.  INV: sign + (inverse, unnormalised) or - (forward).  w_N^q is
-// T[q * tstep] (conjugated for the forward sign).  Pass with radix R and
-// sub-transform size Ns:
+// result.  INV: sign + (inverse, unnormalised) or - (forward).  W is the
+// shared-memory table w_N^q = e^{2 pi i q / N}, q < N (conjugated for the
+// forward sign).  Pass with radix R and sub-transform size Ns:
 //   Y[(j/Ns) Ns R + j%Ns + q Ns] = sum_r X[j + r N/R] w_{Ns R}^{r (j%Ns)} w_R^{r q}.
 template <bool INV, typename R, typename C>
-__device__ C *stockham(C *src, C *dst, const int N, const C *__restrict__ T, const int tstep,
-                       const int *rad, const int npass)
+__device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, const int npass)
 {
     const int tid = threadIdx.x;
     const R sg = INV ? (R)1 : (R)-1;
     auto tw = [&](int q) {
-        C w = T[q * tstep];
+        C w = W[q];
         if (!INV) w.y = -w.y;
         return w;
     };
@@ -229,6 +228,7 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf0 = reinterpret_cast<C *>(smem_raw);
     C *buf1 = buf0 + P.fft_cap;
+    C *W = buf1 + P.fft_cap;  // w_N^q, q < N
     __shared__ int s_rad[32];
     __shared__ int s_np;
 
@@ -247,6 +247,7 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
     const int tstep = even ? 4 : 2;                 // T index of w_N^1
 
     if (tid == 0) s_np = factorize(N, s_rad);
+    for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
 
     // 1. phase shift + fold onto the half spectrum, into buf1[0..nb)
     for (int k = tid; k < nb; k += kThreads) {
@@ -292,7 +293,7 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
     __syncthreads();
 
     // 3. inverse complex DFT of length N
-    C *src = stockham<true, R>(buf0, buf1, N, T, tstep, s_rad, s_np);
+    C *src = stockham<true, R>(buf0, buf1, N, W, s_rad, s_np);
 
     // 4. store the ring
     R *out = map + (size_t)b * P.npix + P.ofs[r];
@@ -321,6 +322,7 @@ ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf0 = reinterpret_cast<C *>(smem_raw);
     C *buf1 = buf0 + P.fft_cap;
+    C *W = buf1 + P.fft_cap;  // w_N^q, q < N
     __shared__ int s_rad[32];
     __shared__ int s_np;
 
@@ -339,6 +341,7 @@ ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
     const R *in = map + (size_t)b * P.npix + P.ofs[r];
 
     if (tid == 0) s_np = factorize(N, s_rad);
+    for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
     if (even) {
         for (int j = tid; j < N; j += kThreads) buf0[j] = mk<R>(in[2 * j], in[2 * j + 1]);
     } else {
@@ -346,7 +349,7 @@ ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
     }
     __syncthreads();
 
-    C *res = stockham<false, R>(buf0, buf1, N, T, tstep, s_rad, s_np);
+    C *res = stockham<false, R>(buf0, buf1, N, W, s_rad, s_np);
     C *Y = (res == buf0) ? buf1 : buf0;
     if (even) {
         for (int k = tid; k < nb; k += kThreads) {

@@ -94,7 +94,7 @@ cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, float2 *
 size_t ring_smem_bytes(const DevPlan &P, bool fp64);
 inline size_t ring_smem_bytes_for_cap(int cap, bool fp64)
 {
-    return (size_t)2 * cap * (fp64 ? 16 : 8);
+    return (size_t)3 * cap * (fp64 ? 16 : 8);  // two FFT buffers + twiddle table
 }
 
 }  // namespace sht
