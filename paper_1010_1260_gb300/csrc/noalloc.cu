@@ -93,7 +93,8 @@ extern "C" int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_
         if (e == cudaSuccess) {
             sht::count_launch();
             e = sht::launch_ring_synth_fp64(P, scratch, static_cast<double *>(map_dev), nbatch, st);
-            if (e == cudaSuccess) sht::count_launch();
+            if (e == cudaSuccess)
+                for (int i = 0; i < sht::ring_launches(P); ++i) sht::count_launch();
         }
         if (e != cudaSuccess) rc = sht::record_cuda_error(e, "sht_alm2map_noalloc launch");
     }

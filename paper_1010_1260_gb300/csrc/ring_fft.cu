@@ -21,6 +21,9 @@ namespace sht {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kRingGroup = 8;  // maps per CTA: the ring's twiddles are built once per group
+
+int ring_group(int nmaps) { return nmaps < kRingGroup ? nmaps : kRingGroup; }
 
 template <typename R> struct C2T;
 template <> struct C2T<double> { using type = double2; };
@@ -70,11 +73,18 @@ template <typename C> __device__ __forceinline__ C cmuli(C a)
 template <typename R> __device__ __forceinline__ const typename C2T<R>::type *tw_table(const DevPlan &P);
 template <> __device__ __forceinline__ const double2 *tw_table<double>(const DevPlan &P) { return P.tw64; }
 template <> __device__ __forceinline__ const float2 *tw_table<float>(const DevPlan &P) { return P.tw32; }
+template <typename R> __device__ __forceinline__ const typename C2T<R>::type *bhat_table(const DevPlan &P);
+template <> __device__ __forceinline__ const double2 *bhat_table<double>(const DevPlan &P) { return P.bhat64; }
+template <> __device__ __forceinline__ const float2 *bhat_table<float>(const DevPlan &P) { return P.bhat32; }
+template <typename R> __device__ __forceinline__ const typename C2T<R>::type *w2_table(const DevPlan &P);
+template <> __device__ __forceinline__ const double2 *w2_table<double>(const DevPlan &P) { return P.w2_64; }
+template <> __device__ __forceinline__ const float2 *w2_table<float>(const DevPlan &P) { return P.w2_32; }
 
-// Factor N into radices: 4s first, then 2, 3, 5, then remaining primes.
+// Factor N into radices: 8s first, then 4, 2, 3, 5, then remaining primes.
 __device__ int factorize(int N, int *rad)
 {
     int np = 0;
+    while (N % 8 == 0) { rad[np++] = 8; N /= 8; }
     while (N % 4 == 0) { rad[np++] = 4; N /= 4; }
     while (N % 2 == 0) { rad[np++] = 2; N /= 2; }
     while (N % 3 == 0) { rad[np++] = 3; N /= 3; }
@@ -114,29 +124,76 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
         const int Rr = rad[pi];
         const int NR = N / Rr;
         const int tscale = N / (Ns * Rr);  // w_{Ns R}^e = w_N^{e tscale}
-        if (Rr == 2) {
+        // j / Ns: a shift while Ns is a power of two (all earlier radices 8, 4, 2)
+        const bool ns_pow2 = (Ns & (Ns - 1)) == 0;
+        const int ns_sh = __ffs(Ns) - 1;
+        // r kk tscale < R Ns N / (Ns R) = N: twiddle indices need no reduction
+        if (Rr == 8) {
+            const R c8 = (R)0.70710678118654752440084436210485;  // 1/sqrt(2)
             for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
+                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
+                const int kk = j - g * Ns;
+                C v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[r] = src[j + r * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+#pragma unroll
+                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw(r * e));
+                }
+                // X_{2q} = DFT4(v_r + v_{r+4}), X_{2q+1} = DFT4((v_r - v_{r+4}) w8^r), w8 = e^{sg 2 pi i / 8}
+                C a[4], b[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    a[r] = cadd(v[r], v[r + 4]);
+                    b[r] = csub(v[r], v[r + 4]);
+                }
+                b[1] = mk<R>(c8 * (b[1].x - sg * b[1].y), c8 * (b[1].y + sg * b[1].x));
+                b[2] = muli(b[2]);
+                b[3] = mk<R>(c8 * (-b[3].x - sg * b[3].y), c8 * (sg * b[3].x - b[3].y));
+                const int o = g * Ns * 8 + kk;
+                {
+                    const C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+                    const C s13 = cadd(a[1], a[3]), d13 = muli(csub(a[1], a[3]));
+                    dst[o] = cadd(s02, s13);
+                    dst[o + 2 * Ns] = cadd(d02, d13);
+                    dst[o + 4 * Ns] = csub(s02, s13);
+                    dst[o + 6 * Ns] = csub(d02, d13);
+                }
+                {
+                    const C s02 = cadd(b[0], b[2]), d02 = csub(b[0], b[2]);
+                    const C s13 = cadd(b[1], b[3]), d13 = muli(csub(b[1], b[3]));
+                    dst[o + Ns] = cadd(s02, s13);
+                    dst[o + 3 * Ns] = cadd(d02, d13);
+                    dst[o + 5 * Ns] = csub(s02, s13);
+                    dst[o + 7 * Ns] = csub(d02, d13);
+                }
+            }
+        } else if (Rr == 2) {
+            for (int j = tid; j < NR; j += kThreads) {
+                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
+                const int kk = j - g * Ns;
                 C v0 = src[j], v1 = src[j + NR];
-                if (kk) v1 = cmul(v1, tw((kk * tscale) % N));
-                const int o = (j / Ns) * Ns * 2 + kk;
+                if (kk) v1 = cmul(v1, tw(kk * tscale));
+                const int o = g * Ns * 2 + kk;
                 dst[o] = cadd(v0, v1);
                 dst[o + Ns] = csub(v0, v1);
             }
         } else if (Rr == 4) {
             for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
+                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
+                const int kk = j - g * Ns;
                 C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR];
                 if (kk) {
                     const int e = kk * tscale;
-                    v1 = cmul(v1, tw(e % N));
-                    v2 = cmul(v2, tw((2 * e) % N));
-                    v3 = cmul(v3, tw((3 * e) % N));
+                    v1 = cmul(v1, tw(e));
+                    v2 = cmul(v2, tw(2 * e));
+                    v3 = cmul(v3, tw(3 * e));
                 }
                 // radix 4 with w_4 = sg * i
                 const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
                 const C a2 = cadd(v1, v3), a3 = muli(csub(v1, v3));
-                const int o = (j / Ns) * Ns * 4 + kk;
+                const int o = g * Ns * 4 + kk;
                 dst[o] = cadd(a0, a2);
                 dst[o + Ns] = cadd(a1, a3);
                 dst[o + 2 * Ns] = csub(a0, a2);
@@ -146,18 +203,19 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
             const R c3 = (R)-0.5;
             const R s3 = sg * (R)0.86602540378443864676372317075294;  // sg sin(2 pi / 3)
             for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
+                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
+                const int kk = j - g * Ns;
                 C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR];
                 if (kk) {
                     const int e = kk * tscale;
-                    v1 = cmul(v1, tw(e % N));
-                    v2 = cmul(v2, tw((2 * e) % N));
+                    v1 = cmul(v1, tw(e));
+                    v2 = cmul(v2, tw(2 * e));
                 }
                 const C t1 = cadd(v1, v2);
                 const C t2 = csub(v1, v2);
                 const C m1 = mk<R>(v0.x + c3 * t1.x, v0.y + c3 * t1.y);
                 const C m2 = mk<R>(-s3 * t2.y, s3 * t2.x);  // i s3 (v1 - v2)
-                const int o = (j / Ns) * Ns * 3 + kk;
+                const int o = g * Ns * 3 + kk;
                 dst[o] = cadd(v0, t1);
                 dst[o + Ns] = cadd(m1, m2);
                 dst[o + 2 * Ns] = csub(m1, m2);
@@ -168,15 +226,16 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
             const R s1 = sg * (R)0.95105651629515357211643933337938;   // sg sin(2 pi / 5)
             const R s2 = sg * (R)0.58778525229247312916870595463907;   // sg sin(4 pi / 5)
             for (int j = tid; j < NR; j += kThreads) {
-                const int kk = j % Ns;
+                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
+                const int kk = j - g * Ns;
                 C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR],
                   v4 = src[j + 4 * NR];
                 if (kk) {
                     const int e = kk * tscale;
-                    v1 = cmul(v1, tw(e % N));
-                    v2 = cmul(v2, tw((2 * e) % N));
-                    v3 = cmul(v3, tw((3 * e) % N));
-                    v4 = cmul(v4, tw((4 * e) % N));
+                    v1 = cmul(v1, tw(e));
+                    v2 = cmul(v2, tw(2 * e));
+                    v3 = cmul(v3, tw(3 * e));
+                    v4 = cmul(v4, tw(4 * e));
                 }
                 const C a1 = cadd(v1, v4), b1 = csub(v1, v4);
                 const C a2 = cadd(v2, v3), b2 = csub(v2, v3);
@@ -185,7 +244,7 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
                 // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
                 const C n1 = mk<R>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
                 const C n2 = mk<R>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
-                const int o = (j / Ns) * Ns * 5 + kk;
+                const int o = g * Ns * 5 + kk;
                 dst[o] = cadd(v0, cadd(a1, a2));
                 dst[o + Ns] = cadd(m1, n1);
                 dst[o + 2 * Ns] = cadd(m2, n2);
@@ -196,10 +255,11 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
             // direct pass for a general prime radix: one thread per output,
             // Y[o + q Ns] = sum_r X[j + r NR] w_N^{r (kk tscale + q NR)}
             for (int t = tid; t < N; t += kThreads) {
-                const int j = t % NR;
                 const int q = t / NR;
-                const int kk = j % Ns;
-                const int e = (kk * tscale + q * NR) % N;
+                const int j = t - q * NR;
+                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
+                const int kk = j - g * Ns;
+                const int e = kk * tscale + q * NR;  // < N
                 C acc = src[j];
                 int idx = e;
                 for (int rr = 1; rr < Rr; ++rr) {
@@ -207,7 +267,7 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
                     idx += e;
                     if (idx >= N) idx -= N;
                 }
-                dst[(j / Ns) * Ns * Rr + kk + q * Ns] = acc;
+                dst[g * Ns * Rr + kk + q * Ns] = acc;
             }
         }
         __syncthreads();
@@ -219,92 +279,146 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
     return src;
 }
 
-template <typename R>
+// Bluestein's DFT of length N (sign + if INV) of x in a[0..N): with the
+// chirp c_j = e^{sg i pi j^2 / N} (j^2 reduced mod 2N, read from the ring's
+// table T[q] = e^{i pi q / n}, n = 2N or N), X_k = c_k sum_j (x_j c_j) conj(c_{k-j}),
+// a circular convolution of length Mb >= 2N - 1 done as
+// IFFT_Mb(FFT_Mb(x c) * Bh) with Bh = FFT_Mb(e^{-i pi t^2 / N}, wrapped) / Mb
+// from the plan (the forward sign uses conj(Bh[-k])).  a and b hold Mb
+// elements; W2 is w_Mb^q, q < Mb.  Returns the buffer holding X[0..N).
+template <bool INV, typename R, typename C>
+__device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const C *__restrict__ T, int n, int N,
+                        int Mb, const int *rad2, int np2)
+{
+    const int tid = threadIdx.x;
+    const int cstep = n / N;  // T index of e^{i pi / N}
+    auto chirp = [&](int j) {
+        const int q = (int)(((long long)j * j) % (2LL * N));
+        C c = T[q * cstep];
+        if (!INV) c.y = -c.y;
+        return c;
+    };
+    for (int j = tid; j < Mb; j += kThreads) a[j] = (j < N) ? cmul(a[j], chirp(j)) : mk<R>(0, 0);
+    __syncthreads();
+    C *f = stockham<false, R>(a, b, Mb, W2, rad2, np2);
+    for (int k = tid; k < Mb; k += kThreads) {
+        const C h = INV ? Bh[k] : cconj(Bh[k == 0 ? 0 : Mb - k]);
+        f[k] = cmul(f[k], h);
+    }
+    __syncthreads();
+    C *y = stockham<true, R>(f, (f == a) ? b : a, Mb, W2, rad2, np2);
+    for (int k = tid; k < N; k += kThreads) y[k] = cmul(y[k], chirp(k));
+    __syncthreads();
+    return y;
+}
+
+template <typename R, bool BLUE>
 __global__ void __launch_bounds__(kThreads)
 ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ delta,
-                  R *__restrict__ map)
+                  R *__restrict__ map, int nmaps, int gmaps)
 {
     using C = typename C2T<R>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int cap = BLUE ? P.blue_cap : P.fft_cap;
     C *buf0 = reinterpret_cast<C *>(smem_raw);
-    C *buf1 = buf0 + P.fft_cap;
-    C *W = buf1 + P.fft_cap;  // w_N^q, q < N
+    C *buf1 = buf0 + cap;
+    C *W = buf1 + cap;  // w_N^q, q < N (direct) or w_Mb^q, q < Mb (Bluestein)
     __shared__ int s_rad[32];
     __shared__ int s_np;
 
-    const int r = blockIdx.x;
-    const int b = blockIdx.y;
+    const int r = BLUE ? P.rings_blue[blockIdx.x] : P.rings_smooth[blockIdx.x];
     const int tid = threadIdx.x;
     const int n = P.nphi[r];
     const int M = P.mmax;
-    const C *D = delta + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
     const C *T = tw_table<R>(P) + P.twofs[r];  // T[q] = e^{i pi q / n}, q < 2n
     const int ps = P.ps[r];
     const double phi0 = P.phi0[r];
     const bool even = (n % 2) == 0;
-    const int N = even ? n / 2 : n;                 // complex DFT length
+    const int N = even ? n / 2 : n;                     // complex DFT length
     const int nb = even ? n / 2 + 1 : (n - 1) / 2 + 1;  // half-spectrum bins
-    const int tstep = even ? 4 : 2;                 // T index of w_N^1
+    const int tstep = even ? 4 : 2;                     // T index of w_N^1
+    const int Mb = BLUE ? P.blue_mb[r] : 0;
+    const C *Bh = BLUE ? bhat_table<R>(P) + P.blue_ofs[r] : nullptr;
 
-    if (tid == 0) s_np = factorize(N, s_rad);
-    for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
-
-    // 1. phase shift + fold onto the half spectrum, into buf1[0..nb)
-    for (int k = tid; k < nb; k += kThreads) {
-        C acc = mk<R>(0, 0);
-        for (int m = k; m <= M; m += n) {
-            C ph;
-            if (ps >= 0) {
-                ph = T[(int)(((long long)m * ps) % (2 * n))];
-            } else {
-                double s, c;
-                sincos((double)m * phi0, &s, &c);
-                ph = mk<R>((R)c, (R)s);
-            }
-            acc = cadd(acc, cmul(D[m], ph));
-        }
-        for (int m = n - k; m <= M; m += n) {
-            if (m < 1) continue;
-            C ph;
-            if (ps >= 0) {
-                ph = T[(int)(((long long)m * ps) % (2 * n))];
-            } else {
-                double s, c;
-                sincos((double)m * phi0, &s, &c);
-                ph = mk<R>((R)c, (R)s);
-            }
-            acc = cadd(acc, cconj(cmul(D[m], ph)));
-        }
-        buf1[k] = acc;
-    }
-    __syncthreads();
-
-    // 2. spectrum of the complex DFT, into buf0[0..N)
-    if (even) {
-        for (int k = tid; k < N; k += kThreads) {
-            const C f = buf1[k];
-            const C g = cconj(buf1[N - k]);
-            const C w = T[2 * k];  // e^{2 pi i k / n}
-            buf0[k] = cadd(cadd(f, g), cmuli(cmul(w, csub(f, g))));
-        }
+    if (BLUE) {
+        if (tid == 0) s_np = factorize(Mb, s_rad);
+        const C *w2 = w2_table<R>(P);
+        const int wstep = kBlueMaxMb / Mb;
+        for (int q = tid; q < Mb; q += kThreads) W[q] = w2[q * wstep];
     } else {
-        for (int k = tid; k < N; k += kThreads) buf0[k] = (k < nb) ? buf1[k] : cconj(buf1[N - k]);
+        if (tid == 0) s_np = factorize(N, s_rad);
+        for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
     }
-    __syncthreads();
 
-    // 3. inverse complex DFT of length N
-    C *src = stockham<true, R>(buf0, buf1, N, W, s_rad, s_np);
-
-    // 4. store the ring
-    R *out = map + (size_t)b * P.npix + P.ofs[r];
-    if (even) {
-        for (int j = tid; j < N; j += kThreads) {
-            const C z = src[j];
-            out[2 * j] = z.x;
-            out[2 * j + 1] = z.y;
+    const int b_end = min(nmaps, (int)(blockIdx.y + 1) * gmaps);
+    for (int b = blockIdx.y * gmaps; b < b_end; ++b) {
+        const C *D = delta + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
+        // 1. phase shift + fold onto the half spectrum, into buf1[0..nb);
+        //    the phase index (m ps) mod 2n advances by (n ps) mod 2n along m = k, k + n, ...
+        const int pstep = (ps >= 0) ? (int)(((long long)n * ps) % (2 * n)) : 0;
+        for (int k = tid; k < nb; k += kThreads) {
+            C acc = mk<R>(0, 0);
+            int pi = (ps >= 0) ? (int)(((long long)k * ps) % (2 * n)) : 0;
+            for (int m = k; m <= M; m += n) {
+                C ph;
+                if (ps >= 0) {
+                    ph = T[pi];
+                    pi += pstep;
+                    if (pi >= 2 * n) pi -= 2 * n;
+                } else {
+                    double sn, cs;
+                    sincos((double)m * phi0, &sn, &cs);
+                    ph = mk<R>((R)cs, (R)sn);
+                }
+                acc = cadd(acc, cmul(D[m], ph));
+            }
+            pi = (ps >= 0) ? (int)(((long long)(n - k) * ps) % (2 * n)) : 0;
+            for (int m = n - k; m <= M; m += n) {
+                C ph;
+                if (ps >= 0) {
+                    ph = T[pi];
+                    pi += pstep;
+                    if (pi >= 2 * n) pi -= 2 * n;
+                } else {
+                    double sn, cs;
+                    sincos((double)m * phi0, &sn, &cs);
+                    ph = mk<R>((R)cs, (R)sn);
+                }
+                if (m >= 1) acc = cadd(acc, cconj(cmul(D[m], ph)));
+            }
+            buf1[k] = acc;
         }
-    } else {
-        for (int j = tid; j < N; j += kThreads) out[j] = src[j].x;
+        __syncthreads();
+
+        // 2. spectrum of the complex DFT, into buf0[0..N)
+        if (even) {
+            for (int k = tid; k < N; k += kThreads) {
+                const C f = buf1[k];
+                const C g = cconj(buf1[N - k]);
+                const C w = T[2 * k];  // e^{2 pi i k / n}
+                buf0[k] = cadd(cadd(f, g), cmuli(cmul(w, csub(f, g))));
+            }
+        } else {
+            for (int k = tid; k < N; k += kThreads) buf0[k] = (k < nb) ? buf1[k] : cconj(buf1[N - k]);
+        }
+        __syncthreads();
+
+        // 3. inverse complex DFT of length N
+        C *src = BLUE ? bluestein<true, R>(buf0, buf1, W, Bh, T, n, N, Mb, s_rad, s_np)
+                      : stockham<true, R>(buf0, buf1, N, W, s_rad, s_np);
+
+        // 4. store the ring
+        R *out = map + (size_t)b * P.npix + P.ofs[r];
+        if (even) {
+            for (int j = tid; j < N; j += kThreads) {
+                const C z = src[j];
+                out[2 * j] = z.x;
+                out[2 * j + 1] = z.y;
+            }
+        } else {
+            for (int j = tid; j < N; j += kThreads) out[j] = src[j].x;
+        }
+        __syncthreads();
     }
 }
 
@@ -313,21 +427,21 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
 // where Y is the forward real DFT of the ring (Y_{n-k} = conj Y_k).  For even
 // n the real DFT runs as one complex DFT of z_j = y_{2j} + i y_{2j+1}, length
 // h = n/2: Y_k = (Z_k + conj Z_{h-k})/2 - (i/2) w^{-k} (Z_k - conj Z_{h-k}).
-template <typename R>
+template <typename R, bool BLUE>
 __global__ void __launch_bounds__(kThreads)
 ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
-                     typename C2T<R>::type *__restrict__ qout)
+                     typename C2T<R>::type *__restrict__ qout, int nmaps, int gmaps)
 {
     using C = typename C2T<R>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int cap = BLUE ? P.blue_cap : P.fft_cap;
     C *buf0 = reinterpret_cast<C *>(smem_raw);
-    C *buf1 = buf0 + P.fft_cap;
-    C *W = buf1 + P.fft_cap;  // w_N^q, q < N
+    C *buf1 = buf0 + cap;
+    C *W = buf1 + cap;
     __shared__ int s_rad[32];
     __shared__ int s_np;
 
-    const int r = blockIdx.x;
-    const int b = blockIdx.y;
+    const int r = BLUE ? P.rings_blue[blockIdx.x] : P.rings_smooth[blockIdx.x];
     const int tid = threadIdx.x;
     const int n = P.nphi[r];
     const int M = P.mmax;
@@ -338,83 +452,95 @@ ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
     const int N = even ? n / 2 : n;
     const int nb = even ? n / 2 + 1 : (n - 1) / 2 + 1;
     const int tstep = even ? 4 : 2;
-    const R *in = map + (size_t)b * P.npix + P.ofs[r];
+    const int Mb = BLUE ? P.blue_mb[r] : 0;
+    const C *Bh = BLUE ? bhat_table<R>(P) + P.blue_ofs[r] : nullptr;
 
-    if (tid == 0) s_np = factorize(N, s_rad);
-    for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
-    if (even) {
-        for (int j = tid; j < N; j += kThreads) buf0[j] = mk<R>(in[2 * j], in[2 * j + 1]);
+    if (BLUE) {
+        if (tid == 0) s_np = factorize(Mb, s_rad);
+        const C *w2 = w2_table<R>(P);
+        const int wstep = kBlueMaxMb / Mb;
+        for (int q = tid; q < Mb; q += kThreads) W[q] = w2[q * wstep];
     } else {
-        for (int j = tid; j < N; j += kThreads) buf0[j] = mk<R>(in[j], (R)0);
+        if (tid == 0) s_np = factorize(N, s_rad);
+        for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
     }
-    __syncthreads();
 
-    C *res = stockham<false, R>(buf0, buf1, N, W, s_rad, s_np);
-    C *Y = (res == buf0) ? buf1 : buf0;
-    if (even) {
-        for (int k = tid; k < nb; k += kThreads) {
-            const C z = res[k % N];
-            const C zc = cconj(res[(N - k) % N]);
-            C w = T[2 * k];  // e^{2 pi i k / n}; conjugated below
-            w.y = -w.y;
-            const C e = cadd(z, zc);
-            const C o = cmul(w, csub(z, zc));
-            // Y_k = e/2 - (i/2) o
-            Y[k] = mk<R>((R)0.5 * (e.x + o.y), (R)0.5 * (e.y - o.x));
-        }
-    } else {
-        for (int k = tid; k < nb; k += kThreads) Y[k] = res[k];
-    }
-    __syncthreads();
-
-    C *q = qout + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
-    for (int m = tid; m <= M; m += kThreads) {
-        const int k = m % n;
-        const C yk = (k < nb) ? Y[k] : cconj(Y[n - k]);
-        C ph;
-        if (ps >= 0) {
-            ph = T[(int)(((long long)m * ps) % (2 * n))];
+    const int b_end = min(nmaps, (int)(blockIdx.y + 1) * gmaps);
+    for (int b = blockIdx.y * gmaps; b < b_end; ++b) {
+        const R *in = map + (size_t)b * P.npix + P.ofs[r];
+        if (even) {
+            for (int j = tid; j < N; j += kThreads) buf0[j] = mk<R>(in[2 * j], in[2 * j + 1]);
         } else {
-            double sn, cs;
-            sincos((double)m * phi0, &sn, &cs);
-            ph = mk<R>((R)cs, (R)sn);
+            for (int j = tid; j < N; j += kThreads) buf0[j] = mk<R>(in[j], (R)0);
         }
-        q[m] = cmul(yk, cconj(ph));
+        __syncthreads();
+
+        C *res = BLUE ? bluestein<false, R>(buf0, buf1, W, Bh, T, n, N, Mb, s_rad, s_np)
+                      : stockham<false, R>(buf0, buf1, N, W, s_rad, s_np);
+        C *Y = (res == buf0) ? buf1 : buf0;
+        if (even) {
+            for (int k = tid; k < nb; k += kThreads) {
+                const C z = res[k == N ? 0 : k];
+                const C zc = cconj(res[k == 0 ? 0 : N - k]);
+                C w = T[2 * k];  // e^{2 pi i k / n}; conjugated below
+                w.y = -w.y;
+                const C e = cadd(z, zc);
+                const C o = cmul(w, csub(z, zc));
+                // Y_k = e/2 - (i/2) o
+                Y[k] = mk<R>((R)0.5 * (e.x + o.y), (R)0.5 * (e.y - o.x));
+            }
+        } else {
+            for (int k = tid; k < nb; k += kThreads) Y[k] = res[k];
+        }
+        __syncthreads();
+
+        C *q = qout + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
+        for (int m = tid; m <= M; m += kThreads) {
+            const int k = m % n;
+            const C yk = (k < nb) ? Y[k] : cconj(Y[n - k]);
+            C ph;
+            if (ps >= 0) {
+                ph = T[(int)(((long long)m * ps) % (2 * n))];
+            } else {
+                double sn, cs;
+                sincos((double)m * phi0, &sn, &cs);
+                ph = mk<R>((R)cs, (R)sn);
+            }
+            q[m] = cmul(yk, cconj(ph));
+        }
+        __syncthreads();
     }
 }
 
-template <typename R>
-cudaError_t launch_analysis(const DevPlan &P, const R *map, typename C2T<R>::type *q, int nmaps,
-                            cudaStream_t st)
+// Launch one ring kernel over the smooth ring list and one over the
+// Bluestein ring list (each with its own shared-memory size).
+template <typename K, typename... Args>
+cudaError_t launch_two(K smooth, K blue, const DevPlan &P, bool fp64, int nmaps, cudaStream_t st, Args... args)
 {
     if (nmaps <= 0) return cudaSuccess;
-    const size_t smem = ring_smem_bytes(P, sizeof(R) == 8);
-    auto kern = ring_analysis_kernel<R>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    const int g = ring_group(nmaps);
+    const int gy = (nmaps + g - 1) / g;
+    if (P.n_smooth > 0) {
+        const size_t smem = ring_smem_bytes_for_cap(P.fft_cap, fp64);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(smooth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        smooth<<<dim3(P.n_smooth, gy), kThreads, smem, st>>>(P, args..., nmaps, g);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    dim3 grid(P.nrings, nmaps);
-    kern<<<grid, kThreads, smem, st>>>(P, map, q);
-    return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_synth(const DevPlan &P, const typename C2T<R>::type *delta, R *map, int nmaps,
-                         cudaStream_t st)
-{
-    if (nmaps <= 0) return cudaSuccess;
-    const size_t smem = ring_smem_bytes(P, sizeof(R) == 8);
-    auto kern = ring_synth_kernel<R>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    if (P.n_blue > 0) {
+        const size_t smem = ring_smem_bytes_for_cap(P.blue_cap, fp64);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(blue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        blue<<<dim3(P.n_blue, gy), kThreads, smem, st>>>(P, args..., nmaps, g);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    dim3 grid(P.nrings, nmaps);
-    kern<<<grid, kThreads, smem, st>>>(P, delta, map);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -427,27 +553,29 @@ size_t ring_smem_bytes(const DevPlan &P, bool fp64)
 cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps,
                                    cudaStream_t st)
 {
-    return launch_synth<double>(P, delta, map, nmaps, st);
+    return launch_two(ring_synth_kernel<double, false>, ring_synth_kernel<double, true>, P, true, nmaps, st, delta,
+                      map);
 }
 
 cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float *map, int nmaps,
                                    cudaStream_t st)
 {
-    return launch_synth<float>(P, delta, map, nmaps, st);
+    return launch_two(ring_synth_kernel<float, false>, ring_synth_kernel<float, true>, P, false, nmaps, st, delta,
+                      map);
 }
 
-}  // namespace sht
-
-namespace sht {
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
                                       cudaStream_t st)
 {
-    return launch_analysis<double>(P, map, q, nmaps, st);
+    return launch_two(ring_analysis_kernel<double, false>, ring_analysis_kernel<double, true>, P, true, nmaps, st,
+                      map, q);
 }
 
 cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
                                       cudaStream_t st)
 {
-    return launch_analysis<float>(P, map, q, nmaps, st);
+    return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, st,
+                      map, q);
 }
+
 }  // namespace sht

@@ -232,9 +232,9 @@ struct StageScope {
             cudaEventRecord(a, st);
         }
     }
-    void done(cudaError_t launch_rc)
+    void done(cudaError_t launch_rc, int kernels = 1)
     {
-        if (launch_rc == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (launch_rc == cudaSuccess) g_launches.fetch_add(kernels, std::memory_order_relaxed);
         if (a) {
             cudaEvent_t b = prof_event(p);
             cudaEventRecord(b, st);
@@ -245,6 +245,47 @@ struct StageScope {
 };
 
 inline long long mofs(int lmax, int m) { return (long long)m * (2LL * lmax + 3 - m) / 2; }
+
+int largest_prime_factor(int N)
+{
+    int best = 1;
+    for (int p = 2; (long long)p * p <= N; ++p)
+        while (N % p == 0) {
+            best = p;
+            N /= p;
+        }
+    return N > 1 ? std::max(best, N) : best;
+}
+
+// In-place iterative radix-2 FFT, forward sign, power-of-two length (plan time only).
+void fft_pow2_forward(std::vector<double> &re, std::vector<double> &im)
+{
+    const size_t n = re.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            std::swap(re[i], re[j]);
+            std::swap(im[i], im[j]);
+        }
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        for (size_t k = 0; k < len / 2; ++k) {
+            const double a = -2.0 * kPi * (double)k / (double)len;
+            const double wr = std::cos(a), wi = std::sin(a);
+            for (size_t i = k; i < n; i += len) {
+                const size_t j = i + len / 2;
+                const double xr = re[j] * wr - im[j] * wi;
+                const double xi = re[j] * wi + im[j] * wr;
+                re[j] = re[i] - xr;
+                im[j] = im[i] - xi;
+                re[i] += xr;
+                im[i] += xi;
+            }
+        }
+    }
+}
 
 int build_tables(sht_plan_s *p, const Rings &R)
 {
@@ -370,6 +411,59 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if (sht::ring_smem_bytes_for_cap(cap, true) > kMaxDynSmem)
         return fail(SHT_EUNSUPPORTED, "ring of %d pixels too long for the shared-memory FFT", maxn);
 
+    // Bluestein rings and their chirp spectra
+    std::vector<int> rsmooth, rblue, bmb(nr, 0);
+    std::vector<long long> bofs(nr, -1);
+    std::vector<double2> bh64;
+    std::vector<float2> bh32;
+    std::map<int, long long> bwhere;
+    int bcap = 0;
+    for (int r = 0; r < nr; ++r) {
+        const int n = R.nphi[r];
+        const int N = (n % 2 == 0) ? n / 2 : n;
+        int Mb = 1;
+        while (Mb < 2 * N - 1) Mb <<= 1;
+        if (largest_prime_factor(N) < sht::kBlueMinPrime || Mb > sht::kBlueMaxMb) {
+            rsmooth.push_back(r);
+            continue;
+        }
+        rblue.push_back(r);
+        bmb[r] = Mb;
+        bcap = std::max(bcap, Mb);
+        auto it = bwhere.find(N);
+        if (it != bwhere.end()) {
+            bofs[r] = it->second;
+            continue;
+        }
+        const long long o = (long long)bh64.size();
+        bwhere[N] = o;
+        bofs[r] = o;
+        std::vector<double> re(Mb, 0.0), im(Mb, 0.0);
+        for (int t = 0; t < N; ++t) {
+            // b_t = e^{-i pi t^2 / N}, with t^2 reduced mod 2N for an exact angle
+            const long long q = ((long long)t * t) % (2LL * N);
+            const double a = -kPi * (double)q / (double)N;
+            re[t] = std::cos(a);
+            im[t] = std::sin(a);
+            if (t > 0) {
+                re[Mb - t] = re[t];
+                im[Mb - t] = im[t];
+            }
+        }
+        fft_pow2_forward(re, im);
+        for (int k = 0; k < Mb; ++k) {
+            bh64.push_back(make_double2(re[k] / Mb, im[k] / Mb));
+            bh32.push_back(make_float2((float)(re[k] / Mb), (float)(im[k] / Mb)));
+        }
+    }
+    std::vector<double2> w2d(sht::kBlueMaxMb);
+    std::vector<float2> w2f(sht::kBlueMaxMb);
+    for (int q = 0; q < sht::kBlueMaxMb; ++q) {
+        const double a = 2.0 * kPi * (double)q / sht::kBlueMaxMb;
+        w2d[q] = make_double2(std::cos(a), std::sin(a));
+        w2f[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+
     DevPlan &d = p->dp;
     d.lmax = L;
     d.mmax = M;
@@ -393,6 +487,17 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, twofs, &d.twofs))) return rc;
     if ((rc = upload(p, tw64, &d.tw64))) return rc;
     if ((rc = upload(p, tw32, &d.tw32))) return rc;
+    d.n_smooth = (int)rsmooth.size();
+    d.n_blue = (int)rblue.size();
+    d.blue_cap = bcap;
+    if ((rc = upload(p, rsmooth, &d.rings_smooth))) return rc;
+    if ((rc = upload(p, rblue, &d.rings_blue))) return rc;
+    if ((rc = upload(p, bmb, &d.blue_mb))) return rc;
+    if ((rc = upload(p, bofs, &d.blue_ofs))) return rc;
+    if ((rc = upload(p, bh64, &d.bhat64))) return rc;
+    if ((rc = upload(p, bh32, &d.bhat32))) return rc;
+    if ((rc = upload(p, w2d, &d.w2_64))) return rc;
+    if ((rc = upload(p, w2f, &d.w2_32))) return rc;
 
     // tensor-core forms: (m, parity) segments of the B operand, padded to
     // whole stages of KC degrees per parity (KC = 8 for TF32, 16 for BF16)
@@ -509,7 +614,7 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc launch");
         StageScope s2(p, SHT_STAGE_RING, st);
         e = sht::launch_ring_synth_fp32(p->dp, delta, map + (size_t)b0 * p->npix, nb, st);
-        s2.done(e);
+        s2.done(e, sht::ring_launches(p->dp));
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp32 launch");
     }
     return SHT_OK;
@@ -639,7 +744,7 @@ int sht_alm2map_batch(sht_plan_t p, int nbatch, const void *alm_dev, void *map_d
         if (e != cudaSuccess) return cuda_fail(e, "legendre_fwd_fp64 launch");
         StageScope s2(p, SHT_STAGE_RING, st);
         e = sht::launch_ring_synth_fp64(p->dp, delta, map + (size_t)b0 * p->npix, nb, st);
-        s2.done(e);
+        s2.done(e, sht::ring_launches(p->dp));
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp64 launch");
     }
     return SHT_OK;
@@ -679,7 +784,7 @@ int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, voi
         const int nb = std::min(chunk, nbatch - b0);
         StageScope s1(p, SHT_STAGE_ADJ_RING, st);
         cudaError_t e = sht::launch_ring_analysis_fp64(p->dp, map + (size_t)b0 * p->npix, q, nb, st);
-        s1.done(e);
+        s1.done(e, sht::ring_launches(p->dp));
         if (e != cudaSuccess) return cuda_fail(e, "ring_analysis_fp64 launch");
         StageScope s2(p, SHT_STAGE_ADJ_LEGENDRE, st);
         e = sht::launch_legendre_adj_fp64(p->dp, q, alm + (size_t)b0 * p->nalm, nb, st);

@@ -42,7 +42,23 @@ struct DevPlan {
     const long long *twofs;  // [nrings] offset of the ring's table in tw64 / tw32
     const double2 *tw64;     // per distinct nphi = n: e^{i pi q / n}, q in [0, 2n)
     const float2 *tw32;
+    // Rings whose FFT length N has a large prime factor run Bluestein's
+    // algorithm (two power-of-two FFTs of length Mb >= 2N - 1 around a
+    // pointwise product with the FFT of the chirp); the others the direct
+    // mixed-radix transform.  Each set is launched over its own ring list.
+    int n_smooth, n_blue;
+    const int *rings_smooth;   // [n_smooth]
+    const int *rings_blue;     // [n_blue]
+    const int *blue_mb;        // [nrings] Mb (0 for smooth rings)
+    const long long *blue_ofs; // [nrings] offset of the ring's chirp spectrum in bhat64 / bhat32
+    const double2 *bhat64;     // per distinct Bluestein N: FFT_Mb(e^{-i pi t^2 / N}, wrapped) / Mb
+    const float2 *bhat32;
+    const double2 *w2_64;      // e^{2 pi i q / kBlueMaxMb}, q < kBlueMaxMb
+    const float2 *w2_32;
+    int blue_cap;              // largest Mb (0 if none)
 };
+constexpr int kBlueMinPrime = 29;  // a prime factor at least this large selects Bluestein
+constexpr int kBlueMaxMb = 4096;   // largest Bluestein FFT length (shared-memory bound)
 
 // Legendre step, FP64 (recurrence and contraction in FP64).
 //   delta[b][ring][m] (complex) = Delta_m(theta_ring) for maps b in [0, nmaps).
@@ -89,6 +105,9 @@ cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const do
                            cudaStream_t st);
 cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, float2 *delta, int nmaps,
                            cudaStream_t st);
+
+// Kernels one ring-step launch issues (one per non-empty ring list).
+inline int ring_launches(const DevPlan &P) { return (P.n_smooth > 0) + (P.n_blue > 0); }
 
 // Shared-memory bytes the ring kernels need for this plan.
 size_t ring_smem_bytes(const DevPlan &P, bool fp64);
