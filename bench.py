@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp64", "fp32_tc", "bf16x3_tc", "bf16x6_tc"], default="fp64")
+    ap.add_argument("--prec", choices=["fp64", "fp32_tc", "bf16x3_tc", "bf16x6_tc"], default="bf16x6_tc",
+                    help="form timed for the headline value (default: split-BF16, 3 pieces, 6 products)")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 path on the same batch (0: skip)")
     ap.add_argument("--nside", type=int, default=1024)
     ap.add_argument("--lmax", type=int, default=2048)
     ap.add_argument("--maps", type=int, default=64)
@@ -258,6 +261,29 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
 
+    # the plain FP64 GPU path on the same batch, for the headline comparison
+    fp64_path = None
+    if args.prec != "fp64" and args.fp64_steps > 0:
+        out64 = torch.empty((B, plan.npix), dtype=torch.float64, device=dev)
+        plan.alm2map(alm, "fp64", out=out64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            plan.alm2map(alm, "fp64", out=out64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms64], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms64 = float(t.item())
+        fp64_path = {"value": world * B / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                     "steps": args.fp64_steps, "speedup_of_headline": ms64 / ms}
+        del out64
+
     # per-map accuracy on a sample of rings against the CPU oracle (rank 0)
     accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -351,7 +377,8 @@ def run_ours(args):
             "config": dict(workload(args), parallelism="replicas x%d" % world, precision=args.prec),
             "roofline": roof,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
-            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy}
+            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy,
+            "fp64_path": fp64_path}
     if world == 1 and not args.no_cpu_baseline:
         v, dt, nt, desc = cpu_oracle_sample(args, args.cpu_rings)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc,
