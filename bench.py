@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
+    ap.add_argument("--workload", choices=["batch", "requests"], default="batch",
+                    help="batch: 64 maps at lmax 2048 (the headline); requests: 256 one-map requests, "
+                         "lmax log-uniform in [64, 2048], nside = lmax // 2, in one multi-request call")
+    ap.add_argument("--requests", type=int, default=256)
     return ap.parse_args()
 
 
@@ -397,10 +401,72 @@ def _peaks():
         return {}
 
 
+def run_requests(args):
+    """The batching form: many uneven one-map requests per call (replicas under torchrun)."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1010_1260_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1010_1260_gb300 import inputs, sht
+    lmaxs = inputs.request_lmax(args.requests, 4)
+    plans = [sht.Plan(sht.healpix(max(1, int(L) // 2)), int(L)) for L in lmaxs]
+    alms = [torch.from_numpy(inputs.gaussian_alm(int(L), int(L), (4, rank * args.requests + i))[0]).cuda()
+            for i, L in enumerate(lmaxs)]
+    res = {}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "fp32_tc"):
+        multi = sht.Multi(plans, prec)
+        outs = multi.outputs()
+        for _ in range(args.warmup):
+            multi.alm2map(alms, outs)
+        torch.cuda.synchronize()
+        n0 = sht.kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            multi.alm2map(alms, outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        res[prec] = {"ms_per_step": ms, "requests_per_s": world * args.requests / (ms * 1e-3),
+                     "gpu_launches_per_step": (sht.kernel_launches() - n0) / args.steps}
+        multi.close()
+    if rank == 0:
+        line = {"metric": "alm2map requests/s (256 one-map requests, lmax log-uniform [64, 2048], nside = lmax // 2)",
+                "value": res["fp64"]["requests_per_s"], "unit": "requests/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["fp64"]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "batching form: %d requests" % args.requests,
+                           "lmax_min": int(lmaxs.min()), "lmax_max": int(lmaxs.max()),
+                           "total_alm": int(sum(p.nalm for p in plans)), "total_pixels": int(sum(p.npix for p in plans))},
+                "forms": res}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "requests":
+        return run_requests(args)
     return run_ours(args)
 
 

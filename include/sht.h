@@ -136,6 +136,25 @@ int sht_map2alm_adjoint_batch(sht_plan_t plan, int nbatch, const void *map_dev, 
  * entry a call reads is first written by that call. */
 int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *map_dev, void *stream);
 
+/* Many requests of different grids and band limits (one map each) in one
+ * call: the batching form.  Request i transforms alm_dev[i] (plans[i]'s
+ * nalm complex128) into map_dev[i] (plans[i]'s npix reals).  FP64: the
+ * Legendre step of all requests runs as one persistent launch whose CTAs
+ * take (request, m, ring block) work items, sorted by decreasing cost, from
+ * an atomic counter, then one launch per ring list does all rings; the
+ * context is capturable in a CUDA graph (no allocation or host sync inside
+ * sht_multi_alm2map; pointers are kernel parameters, so a captured graph
+ * replays with the pointers it was captured with).  Tensor-core forms run
+ * each request through its plan in turn.  1 <= nreq <= 256; all plans on one
+ * device; the plans must outlive the context.
+ * sht_alm2map_multi = create + run + stream synchronize + destroy. */
+typedef struct sht_multi_s *sht_multi_t;
+int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht_multi_t *out);
+int sht_multi_alm2map(sht_multi_t multi, const void *const *alm_dev, void *const *map_dev, void *stream);
+int sht_multi_destroy(sht_multi_t multi);
+int sht_alm2map_multi(int nreq, const sht_plan_t *plans, const void *const *alm_dev, void *const *map_dev,
+                      int prec, void *stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *sht_last_error(void);
 

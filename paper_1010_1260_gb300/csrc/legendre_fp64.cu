@@ -36,19 +36,16 @@ __device__ __forceinline__ bool above_hi(double v)
     return e > 1023 + kScaleHi;
 }
 
+// One work item: order m, ring pairs [pair_block * 128, + 128), maps [b0, b0 + BC).
+// Every thread of the CTA must call it (it synchronises the CTA).
 template <int BC>
-__global__ void __launch_bounds__(kThreads)
-legendre_fwd_fp64_kernel(const DevPlan P, const double2 *__restrict__ alm,
-                         double2 *__restrict__ delta, int nmaps)
+__device__ __forceinline__ void legendre_item(const DevPlan &P, const double2 *__restrict__ alm,
+                                              double2 *__restrict__ delta, int nmaps, int m, int pair_block,
+                                              int b0, double *sA, double2 (*sa)[BC])
 {
-    const int m = blockIdx.y;
     const int L = P.lmax;
-    const int pair = blockIdx.x * kThreads + threadIdx.x;
-    const int b0 = blockIdx.z * BC;
+    const int pair = pair_block * kThreads + threadIdx.x;
     const bool live = pair < P.npairs;
-
-    __shared__ double sA[kChunk];        // A_{l+1} for l in the chunk
-    __shared__ double2 sa[kChunk][BC];   // C_l a_lm for the CTA's maps
 
     double x = 0.0, p0 = 0.0, p1 = 0.0;
     int k = 0;
@@ -157,6 +154,38 @@ legendre_fwd_fp64_kernel(const DevPlan P, const double2 *__restrict__ alm,
 }
 
 template <int BC>
+__global__ void __launch_bounds__(kThreads)
+legendre_fwd_fp64_kernel(const __grid_constant__ DevPlan P, const double2 *__restrict__ alm,
+                         double2 *__restrict__ delta, int nmaps)
+{
+    __shared__ double sA[kChunk];        // A_{l+1} for l in the chunk
+    __shared__ double2 sa[kChunk][BC];   // C_l a_lm for the CTA's maps
+    legendre_item<BC>(P, alm, delta, nmaps, blockIdx.y, blockIdx.x, blockIdx.z * BC, sA, sa);
+}
+
+// Many requests (one map each) in one persistent launch: CTAs take work
+// items (request, m, ring block) from a list sorted by decreasing cost
+// through an atomic counter, so uneven requests balance over the SMs.
+__global__ void __launch_bounds__(kThreads)
+legendre_multi_fp64_kernel(const DevPlan *__restrict__ plans, const int4 *__restrict__ items, int nitems,
+                           int *__restrict__ counter, const MultiPtrs ptrs)
+{
+    __shared__ double sA[kChunk];
+    __shared__ double2 sa[kChunk][1];
+    __shared__ int s_item;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int4 w = items[it];  // (request, m, ring block, -)
+        legendre_item<1>(plans[w.x], static_cast<const double2 *>(ptrs.alm[w.x]),
+                         static_cast<double2 *>(ptrs.delta[w.x]), 1, w.y, w.z, 0, sA, sa);
+    }
+}
+
+template <int BC>
 cudaError_t launch_bc(const DevPlan &P, const double2 *alm, double2 *delta, int nmaps,
                       cudaStream_t st)
 {
@@ -166,6 +195,14 @@ cudaError_t launch_bc(const DevPlan &P, const double2 *alm, double2 *delta, int 
 }
 
 }  // namespace
+
+cudaError_t launch_legendre_multi_fp64(const DevPlan *plans, const int4 *items, int nitems, int *counter,
+                                       const MultiPtrs &ptrs, int nctas, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    legendre_multi_fp64_kernel<<<nctas, kThreads, 0, st>>>(plans, items, nitems, counter, ptrs);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, double2 *delta,
                                      int nmaps, cudaStream_t st)

@@ -312,21 +312,19 @@ __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const
     return y;
 }
 
+// Synthesis of ring r of plan P for maps [b_begin, b_end): delta is the
+// plan's Delta array [map][ring][m], map the first pixel of map 0.  smem
+// holds three buffers of cap complex elements.  All threads of the CTA call it.
 template <typename R, bool BLUE>
-__global__ void __launch_bounds__(kThreads)
-ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ delta,
-                  R *__restrict__ map, int nmaps, int gmaps)
+__device__ __forceinline__ void ring_synth_body(const DevPlan &P, int r, const typename C2T<R>::type *__restrict__ delta,
+                                                R *__restrict__ map, int b_begin, int b_end, int cap,
+                                                unsigned char *smem_raw, int *s_rad, int *s_np_ptr)
 {
     using C = typename C2T<R>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int cap = BLUE ? P.blue_cap : P.fft_cap;
     C *buf0 = reinterpret_cast<C *>(smem_raw);
     C *buf1 = buf0 + cap;
     C *W = buf1 + cap;  // w_N^q, q < N (direct) or w_Mb^q, q < Mb (Bluestein)
-    __shared__ int s_rad[32];
-    __shared__ int s_np;
-
-    const int r = BLUE ? P.rings_blue[blockIdx.x] : P.rings_smooth[blockIdx.x];
+    int &s_np = *s_np_ptr;
     const int tid = threadIdx.x;
     const int n = P.nphi[r];
     const int M = P.mmax;
@@ -350,8 +348,7 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
         for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
     }
 
-    const int b_end = min(nmaps, (int)(blockIdx.y + 1) * gmaps);
-    for (int b = blockIdx.y * gmaps; b < b_end; ++b) {
+    for (int b = b_begin; b < b_end; ++b) {
         const C *D = delta + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
         // 1. phase shift + fold onto the half spectrum, into buf1[0..nb);
         //    the phase index (m ps) mod 2n advances by (n ps) mod 2n along m = k, k + n, ...
@@ -420,6 +417,34 @@ ring_synth_kernel(const DevPlan P, const typename C2T<R>::type *__restrict__ del
         }
         __syncthreads();
     }
+}
+
+template <typename R, bool BLUE>
+__global__ void __launch_bounds__(kThreads)
+ring_synth_kernel(const __grid_constant__ DevPlan P, const typename C2T<R>::type *__restrict__ delta,
+                  R *__restrict__ map, int nmaps, int gmaps)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_rad[32];
+    __shared__ int s_np;
+    const int r = BLUE ? P.rings_blue[blockIdx.x] : P.rings_smooth[blockIdx.x];
+    ring_synth_body<R, BLUE>(P, r, delta, map, blockIdx.y * gmaps, min(nmaps, (int)(blockIdx.y + 1) * gmaps),
+                             BLUE ? P.blue_cap : P.fft_cap, smem_raw, s_rad, &s_np);
+}
+
+// Ring step of many one-map requests: CTA i synthesises ring items[i].y of
+// request items[i].x; cap is the largest buffer over the requests.
+template <typename R, bool BLUE>
+__global__ void __launch_bounds__(kThreads)
+ring_synth_multi_kernel(const DevPlan *__restrict__ plans, const int2 *__restrict__ items, const MultiPtrs ptrs,
+                        int cap)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_rad[32];
+    __shared__ int s_np;
+    const int2 w = items[blockIdx.x];
+    ring_synth_body<R, BLUE>(plans[w.x], w.y, static_cast<const typename C2T<R>::type *>(ptrs.delta[w.x]),
+                             static_cast<R *>(ptrs.map[w.x]), 0, 1, cap, smem_raw, s_rad, &s_np);
 }
 
 // Ring step of the transpose (map2alm_adjoint): for every ring r and m <= M,
@@ -562,6 +587,35 @@ cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float 
 {
     return launch_two(ring_synth_kernel<float, false>, ring_synth_kernel<float, true>, P, false, nmaps, st, delta,
                       map);
+}
+
+cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smooth_items, int n_smooth,
+                                         int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
+                                         const MultiPtrs &ptrs, cudaStream_t st)
+{
+    if (n_smooth > 0) {
+        auto k = ring_synth_multi_kernel<double, false>;
+        const size_t smem = ring_smem_bytes_for_cap(smooth_cap, true);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k<<<n_smooth, kThreads, smem, st>>>(plans, smooth_items, ptrs, smooth_cap);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_blue > 0) {
+        auto k = ring_synth_multi_kernel<double, true>;
+        const size_t smem = ring_smem_bytes_for_cap(blue_cap, true);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k<<<n_blue, kThreads, smem, st>>>(plans, blue_items, ptrs, blue_cap);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -34,6 +35,7 @@ struct sht_plan_s {
     std::vector<void *> allocs;
     void *ws = nullptr;  // Delta workspace
     size_t ws_bytes = 0;
+    std::vector<int> rings_smooth_h, rings_blue_h;  // host copies of the ring lists
     sht::TcWork tc;      // tensor-core forms: segment tables, status word, B-operand buffer
     size_t tc_bytes = 0;
     std::mutex mu;
@@ -487,6 +489,8 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, twofs, &d.twofs))) return rc;
     if ((rc = upload(p, tw64, &d.tw64))) return rc;
     if ((rc = upload(p, tw32, &d.tw32))) return rc;
+    p->rings_smooth_h = rsmooth;
+    p->rings_blue_h = rblue;
     d.n_smooth = (int)rsmooth.size();
     d.n_blue = (int)rblue.size();
     d.blue_cap = bcap;
@@ -861,6 +865,189 @@ int sht_map2alm_adjoint(sht_plan_t p, const void *map_dev, void *alm_dev, int pr
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------- multi-request --
+
+struct sht_multi_s {
+    int nreq = 0, prec = 0, device = 0, nctas = 0;
+    std::vector<sht_plan_t> plans;
+    std::vector<size_t> delta_ofs;  // bytes, per request
+    std::vector<void *> allocs;
+    sht::DevPlan *d_plans = nullptr;
+    int4 *d_items = nullptr;
+    int nitems = 0;
+    int2 *d_smooth = nullptr, *d_blue = nullptr;
+    int n_smooth = 0, n_blue = 0, smooth_cap = 0, blue_cap = 0;
+    int *d_counter = nullptr;
+    void *d_delta = nullptr;
+};
+
+namespace {
+
+void free_multi(sht_multi_s *q)
+{
+    if (!q) return;
+    {
+        DeviceGuard g(q->device);
+        cudaDeviceSynchronize();
+        for (void *d : q->allocs) cudaFree(d);
+    }
+    delete q;
+}
+
+template <typename T>
+int multi_upload(sht_multi_s *q, const std::vector<T> &h, T **out)
+{
+    *out = nullptr;
+    if (h.empty()) return SHT_OK;
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, h.size() * sizeof(T));
+    if (e != cudaSuccess) return fail(SHT_ENOMEM, "cudaMalloc(%zu): %s", h.size() * sizeof(T), cudaGetErrorString(e));
+    q->allocs.push_back(d);
+    e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    *out = static_cast<T *>(d);
+    return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht_multi_t *out)
+{
+    g_err.clear();
+    if (!out) return fail(SHT_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (nreq < 1 || nreq > sht::kMaxReq) return fail(SHT_EINVAL, "need 1 <= nreq <= %d", sht::kMaxReq);
+    if (!plans) return fail(SHT_EINVAL, "null plan array");
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
+        return fail(SHT_EINVAL, "unknown precision %d", prec);
+    for (int i = 0; i < nreq; ++i) {
+        if (!plans[i]) return fail(SHT_EINVAL, "null plan %d", i);
+        if (plans[i]->device != plans[0]->device) return fail(SHT_EINVAL, "plans on different devices");
+    }
+    auto *q = new (std::nothrow) sht_multi_s();
+    if (!q) return fail(SHT_ENOMEM, "multi allocation");
+    q->nreq = nreq;
+    q->prec = prec;
+    q->device = plans[0]->device;
+    q->plans.assign(plans, plans + nreq);
+    DeviceGuard dg(q->device);
+    int rc = SHT_OK;
+    if (prec == SHT_FP64) {
+        // work list (request, m, ring block) by decreasing cost, ring items, Delta offsets
+        struct Item {
+            long long cost;
+            int4 w;
+        };
+        std::vector<Item> items;
+        std::vector<int2> smooth, blue;
+        std::vector<sht::DevPlan> dp(nreq);
+        size_t dofs = 0;
+        for (int i = 0; i < nreq; ++i) {
+            const sht_plan_s *p = plans[i];
+            dp[i] = p->dp;
+            const int nrb = (p->npairs + 127) / 128;
+            for (int m = 0; m <= p->mmax; ++m)
+                for (int rb = 0; rb < nrb; ++rb) {
+                    const long long rows = std::min(128, p->npairs - rb * 128);
+                    items.push_back({(long long)(p->lmax - m + 1) * rows, make_int4(i, m, rb, 0)});
+                }
+            for (int r : p->rings_smooth_h) smooth.push_back(make_int2(i, r));
+            for (int r : p->rings_blue_h) blue.push_back(make_int2(i, r));
+            q->smooth_cap = std::max(q->smooth_cap, p->dp.fft_cap);
+            q->blue_cap = std::max(q->blue_cap, p->dp.blue_cap);
+            q->delta_ofs.push_back(dofs);
+            dofs += (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
+            dofs = (dofs + 255) & ~(size_t)255;
+        }
+        std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+        std::vector<int4> w(items.size());
+        for (size_t j = 0; j < items.size(); ++j) w[j] = items[j].w;
+        q->nitems = (int)w.size();
+        q->n_smooth = (int)smooth.size();
+        q->n_blue = (int)blue.size();
+        if ((rc = multi_upload(q, dp, &q->d_plans)) || (rc = multi_upload(q, w, &q->d_items)) ||
+            (rc = multi_upload(q, smooth, &q->d_smooth)) || (rc = multi_upload(q, blue, &q->d_blue))) {
+            std::string keep = g_err;
+            free_multi(q);
+            g_err = keep;
+            return rc;
+        }
+        cudaError_t e = cudaMalloc(&q->d_counter, sizeof(int));
+        if (e == cudaSuccess) {
+            q->allocs.push_back(q->d_counter);
+            e = cudaMalloc(&q->d_delta, dofs);
+            if (e == cudaSuccess) q->allocs.push_back(q->d_delta);
+        }
+        if (e != cudaSuccess) {
+            free_multi(q);
+            return fail(SHT_ENOMEM, "multi workspace: %s", cudaGetErrorString(e));
+        }
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, q->device);
+        q->nctas = std::max(1, nsm) * 8;  // persistent CTAs: several per SM hide the FP64 latency
+    }
+    *out = q;
+    return SHT_OK;
+}
+
+extern "C" int sht_multi_destroy(sht_multi_t q)
+{
+    free_multi(q);
+    return SHT_OK;
+}
+
+extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void *const *map_dev, void *stream)
+{
+    g_err.clear();
+    if (!q) return fail(SHT_EINVAL, "null multi handle");
+    if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null pointer array");
+    for (int i = 0; i < q->nreq; ++i)
+        if (!alm_dev[i] || !map_dev[i]) return fail(SHT_EINVAL, "null device pointer for request %d", i);
+    if (q->prec != SHT_FP64) {
+        // tensor-core forms: each request through its own plan (groups of one map)
+        for (int i = 0; i < q->nreq; ++i) {
+            const int rc = sht_alm2map_batch(q->plans[i], 1, alm_dev[i], map_dev[i], q->prec, stream);
+            if (rc) return rc;
+        }
+        return SHT_OK;
+    }
+    DeviceGuard dg(q->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    sht::MultiPtrs ptrs{};
+    for (int i = 0; i < q->nreq; ++i) {
+        ptrs.alm[i] = alm_dev[i];
+        ptrs.map[i] = map_dev[i];
+        ptrs.delta[i] = static_cast<char *>(q->d_delta) + q->delta_ofs[i];
+    }
+    cudaError_t e = cudaMemsetAsync(q->d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = sht::launch_legendre_multi_fp64(q->d_plans, q->d_items, q->nitems, q->d_counter, ptrs, q->nctas, st);
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    else return cuda_fail(e, "legendre_multi_fp64 launch");
+    e = sht::launch_ring_synth_multi_fp64(q->d_plans, q->d_smooth, q->n_smooth, q->smooth_cap, q->d_blue, q->n_blue,
+                                          q->blue_cap, ptrs, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ring_synth_multi launch");
+    g_launches.fetch_add((q->n_smooth > 0) + (q->n_blue > 0), std::memory_order_relaxed);
+    return SHT_OK;
+}
+
+extern "C" int sht_alm2map_multi(int nreq, const sht_plan_t *plans, const void *const *alm_dev,
+                                 void *const *map_dev, int prec, void *stream)
+{
+    sht_multi_t q = nullptr;
+    int rc = sht_multi_create(nreq, plans, prec, &q);
+    if (rc) return rc;
+    rc = sht_multi_alm2map(q, alm_dev, map_dev, stream);
+    if (rc == SHT_OK) {
+        cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    std::string keep = g_err;
+    sht_multi_destroy(q);
+    g_err = keep;
+    return rc;
+}
 
 // Internal hooks for other translation units of the library (not C ABI).
 namespace sht {

@@ -60,10 +60,28 @@ struct DevPlan {
 constexpr int kBlueMinPrime = 29;  // a prime factor at least this large selects Bluestein
 constexpr int kBlueMaxMb = 4096;   // largest Bluestein FFT length (shared-memory bound)
 
+// Per-request device pointers of a multi-request call (kernel parameter).
+constexpr int kMaxReq = 256;
+struct MultiPtrs {
+    const void *alm[kMaxReq];
+    void *map[kMaxReq];
+    void *delta[kMaxReq];
+};
+
 // Legendre step, FP64 (recurrence and contraction in FP64).
 //   delta[b][ring][m] (complex) = Delta_m(theta_ring) for maps b in [0, nmaps).
 cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, double2 *delta,
                                      int nmaps, cudaStream_t st);
+
+// Legendre step of many one-map requests in one persistent launch over the
+// work list items[] = (request, m, ring block, -); counter must be 0 at launch.
+cudaError_t launch_legendre_multi_fp64(const DevPlan *plans, const int4 *items, int nitems, int *counter,
+                                       const MultiPtrs &ptrs, int nctas, cudaStream_t st);
+// Ring step of many requests: one launch over items (request, ring) of rings
+// with a direct transform, one over rings run with Bluestein's algorithm.
+cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smooth_items, int n_smooth,
+                                         int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
+                                         const MultiPtrs &ptrs, cudaStream_t st);
 
 // Ring step: phase shift, fold of m onto the ring's bins, real inverse DFT of
 // each ring.  T = double (FP64 path) or float (tensor-core paths).

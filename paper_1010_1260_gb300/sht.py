@@ -75,11 +75,17 @@ def lib():
             L.sht_profile.argtypes = [P, I]
             L.sht_profile_read.argtypes = [P, I, V, V]
             L.sht_sync.argtypes = [P]
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            L.sht_multi_create.argtypes = [I, PP, I, PP]
+            L.sht_multi_alm2map.argtypes = [P, PP, PP, V]
+            L.sht_multi_destroy.argtypes = [P]
+            L.sht_alm2map_multi.argtypes = [I, PP, PP, PP, I, V]
             L.sht_kernel_launches.argtypes = []
             L.sht_kernel_launches.restype = ctypes.c_ulonglong
             for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
                       "sht_alm2map_batch", "sht_map2alm_adjoint_batch", "sht_profile",
-                      "sht_profile_read", "sht_sync"):
+                      "sht_profile_read", "sht_sync", "sht_multi_create", "sht_multi_alm2map",
+                      "sht_multi_destroy", "sht_alm2map_multi"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -243,3 +249,46 @@ class Plan:
         out.copy_(d_map, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return out
+
+
+class Multi:
+    """Many one-map requests of different plans in one call (the batching form)."""
+
+    def __init__(self, plans, prec: str = "fp64"):
+        self.plans = list(plans)  # keeps the plans alive
+        self.prec = prec
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p.handle for p in self.plans])
+        h = ctypes.c_void_p()
+        check(lib().sht_multi_create(n, arr, PREC[prec], ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sht_multi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, device=None):
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        return [torch.empty(p.npix, dtype=MAP_DTYPE[self.prec], device=dev) for p in self.plans]
+
+    def alm2map(self, alms, outs=None, stream=None):
+        """alms[i]: cuda complex128 [nalm_i]; returns (or fills) outs[i]: [npix_i]."""
+        n = len(self.plans)
+        if len(alms) != n:
+            raise ValueError("need one coefficient tensor per request")
+        for a, p in zip(alms, self.plans):
+            if not (a.is_cuda and a.dtype == torch.complex128 and a.is_contiguous() and a.numel() == p.nalm):
+                raise TypeError("bad coefficient tensor")
+        if outs is None:
+            outs = self.outputs(alms[0].device)
+        a_arr = (ctypes.c_void_p * n)(*[a.data_ptr() for a in alms])
+        m_arr = (ctypes.c_void_p * n)(*[m.data_ptr() for m in outs])
+        check(lib().sht_multi_alm2map(self._h, a_arr, m_arr, _stream_ptr(stream)))
+        return outs

@@ -1,0 +1,110 @@
+"""The batching form: many one-map requests of uneven grids and band limits
+in one persistent launch (FP64) -- equal to the per-plan path bit for bit,
+equal to the oracle, and replayable from a captured CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1010_1260_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sht():
+    from paper_1010_1260_gb300 import sht as s
+    s.lib()
+    return s
+
+
+def _requests(sht, lmaxs):
+    plans = [sht.Plan(sht.healpix(max(1, L // 2)), int(L)) for L in lmaxs]
+    alms = [torch.from_numpy(inputs.gaussian_alm(int(L), int(L), (4, i))[0]).cuda() for i, L in enumerate(lmaxs)]
+    return plans, alms
+
+
+def test_multi_equals_per_plan_bitwise(sht):
+    lmaxs = [64, 75, 130, 33, 200, 64, 97]
+    plans, alms = _requests(sht, lmaxs)
+    multi = sht.Multi(plans, "fp64")
+    outs = multi.alm2map(alms)
+    torch.cuda.synchronize()
+    for p, a, o in zip(plans, alms, outs):
+        assert torch.equal(o, p.alm2map(a))
+
+
+def test_multi_matches_oracle(oracle_mod, sht):
+    lmaxs = [16, 40, 23, 64]
+    plans, alms = _requests(sht, lmaxs)
+    outs = sht.Multi(plans, "fp64").alm2map(alms)
+    torch.cuda.synchronize()
+    for L, a, o in zip(lmaxs, alms, outs):
+        g = oracle_mod.healpix_grid(max(1, L // 2))
+        want = oracle_mod.alm2map(g, L, L, a.cpu().numpy()[None])[0]
+        got = o.cpu().numpy()
+        assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 1e-10
+
+
+def test_multi_graph_replay_equals_eager(sht):
+    lmaxs = [64, 128, 90, 256]
+    plans, alms = _requests(sht, lmaxs)
+    multi = sht.Multi(plans, "fp64")
+    eager = [o.clone() for o in multi.alm2map(alms)]
+    outs = multi.outputs()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        multi.alm2map(alms, outs)          # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    for o in outs:
+        o.zero_()
+    with torch.cuda.graph(g):
+        multi.alm2map(alms, outs)
+    for _ in range(3):
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for o, e in zip(outs, eager):
+            assert torch.equal(o, e)
+
+
+def test_multi_tensor_core_form(sht):
+    lmaxs = [64, 100, 48]
+    plans, alms = _requests(sht, lmaxs)
+    outs = sht.Multi(plans, "fp32_tc").alm2map(alms)
+    torch.cuda.synchronize()
+    for p, a, o in zip(plans, alms, outs):
+        ref = p.alm2map(a).float()
+        assert float(torch.linalg.norm(o - ref) / torch.linalg.norm(ref)) < 1e-5
+
+
+def test_multi_log_uniform_requests(oracle_mod, sht):
+    """256 requests, lmax log-uniform in [64, 2048], nside = lmax // 2: bit for
+    bit equal to the per-plan path on a sample, and to the oracle on the
+    smallest request."""
+    lmaxs = inputs.request_lmax(256, 4)
+    plans, alms = _requests(sht, lmaxs)
+    multi = sht.Multi(plans, "fp64")
+    outs = multi.alm2map(alms)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    for i in sorted(set(rng.choice(256, 6, replace=False).tolist()) | {int(np.argmin(lmaxs))}):
+        assert torch.equal(outs[i], plans[i].alm2map(alms[i]))
+    i = int(np.argmin(lmaxs))
+    L = int(lmaxs[i])
+    g = oracle_mod.healpix_grid(L // 2)
+    want = oracle_mod.alm2map(g, L, L, alms[i].cpu().numpy()[None])[0]
+    assert np.max(np.abs(outs[i].cpu().numpy() - want)) / np.max(np.abs(want)) < 1e-10
+
+
+def test_multi_rejects_bad_arguments(sht):
+    import ctypes
+    L = sht.lib()
+    h = ctypes.c_void_p()
+    assert L.sht_multi_create(0, None, 0, ctypes.byref(h)) == sht.SHT_EINVAL
+    plan = sht.Plan(sht.healpix(4), 8)
+    arr = (ctypes.c_void_p * 1)(plan.handle)
+    assert L.sht_multi_create(1, arr, 9, ctypes.byref(h)) == sht.SHT_EINVAL
+    assert L.sht_multi_alm2map(None, None, None, None) == sht.SHT_EINVAL
