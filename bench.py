@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
+    ap.add_argument("--lambda-cache", action="store_true",
+                    help="tensor-core forms: build the plan-time Lambda operand before timing")
     ap.add_argument("--workload", choices=["batch", "requests"], default="batch",
                     help="batch: 64 maps at lmax 2048 (the headline); requests: 256 one-map requests, "
                          "lmax log-uniform in [64, 2048], nside = lmax // 2, in one multi-request call")
@@ -231,6 +233,13 @@ def run_ours(args):
     out = torch.empty((B, plan.npix), dtype=sht.MAP_DTYPE[args.prec], device=dev)
     stream = torch.cuda.current_stream()
 
+    lcache = None
+    if args.lambda_cache and args.prec != "fp64":
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.lambda_cache(args.prec)
+        lcache = {"bytes": plan.lambda_cache_bytes(args.prec), "build_s": time.perf_counter() - t0}
+
     for _ in range(args.warmup):
         plan.alm2map(alm, args.prec, out=out)
     torch.cuda.synchronize()
@@ -347,6 +356,23 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_fwd_fp64"),
                 "peak_source": "nominal FP64 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2070 MHz); ncu fp64 pipe active is the cross-check",
                 "flops_per_launch": fl, "ms_per_launch": dom_ms}
+    elif dom == "legendre" and lcache is not None:
+        # cached Lambda operand: the kernel streams it once per launch (plus
+        # the B operand and the Delta writes); HBM bounds it
+        nlm = (L + 1) * (L + 2) // 2
+        by = lcache["bytes"] + B * (16 * nlm + (4 * args.nside - 1) * (L + 1) * 8)
+        ach = by / (dom_ms * 1e-3) / 1e9
+        peak = _peaks().get("hbm_gbs", 6800.0)
+        roof = {"kernel": "legendre_tc cached (+ operand prep)", "bound": "hbm", "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "traffic": traffic_for("legendre_tc_cached"),
+                "bytes_per_launch": by, "ms_per_launch": dom_ms,
+                "bytes": "Lambda operand + a_lm (complex128) + Delta (complex64)"}
+        tpk = _peaks().get("bf16_tflops_sustained", 1691.3) * TENSOR_PEAK_RATIO[args.prec]
+        fl_t = 4.0 * R * nlm * B
+        roof["tensor"] = {"algorithmic_tflops": fl_t / (dom_ms * 1e-3) / 1e12,
+                          "executed_tflops": PRODUCTS[args.prec] * fl_t / (dom_ms * 1e-3) / 1e12,
+                          "peak": tpk, "peak_source": "MEASURED_PEAKS bf16 sustained x nominal dtype ratio",
+                          "frac_executed": PRODUCTS[args.prec] * fl_t / (dom_ms * 1e-3) / 1e12 / tpk}
     elif dom == "legendre":
         # tensor-core forms: the FP64 recurrence bounds the kernel; the
         # contraction's tensor-pipe figure is reported beside it
@@ -378,7 +404,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": maps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
-            "config": dict(workload(args), parallelism="replicas x%d" % world, precision=args.prec),
+            "config": dict(workload(args), parallelism="replicas x%d" % world, precision=args.prec,
+                           lambda_cache=lcache is not None),
+            "lambda_cache": lcache,
             "roofline": roof,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
             "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy,

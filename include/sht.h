@@ -115,6 +115,29 @@ int sht_alm2map_batch(sht_plan_t plan, int nbatch, const void *alm_dev, void *ma
 int sht_map2alm_adjoint_batch(sht_plan_t plan, int nbatch, const void *map_dev, void *alm_dev,
                               int prec, void *stream);
 
+/* Plan-time Lambda operand for one tensor-core form (SHT_FP32_TC,
+ * SHT_BF16X3_TC, SHT_BF16X6_TC).  The paper evaluates the recurrence of
+ * Eq. assLegRec on the fly inside alm2map (sec. 2.2.2, and the trade of
+ * computation against memory traffic in sec. 5); this caches its result
+ * instead: every lambda_lm(x_r) of the plan, rounded and split into the
+ * form's tensor-core pieces exactly as the recurrence launch makes them, is
+ * written once to device memory in the kernel's tile layout.  Later
+ * sht_alm2map / sht_alm2map_batch calls of that form on this plan stream the
+ * tiles instead of running the recurrence; their results are bit-identical.
+ * Size: sht_lambda_cache_bytes(plan, prec) bytes of device memory, about
+ * npairs x N_lm x (8, 4, 6) bytes for (FP32_TC, BF16X3_TC, BF16X6_TC): 17-35 GB
+ * at lmax 2048 on a 4095-ring grid.
+ * enable != 0 builds it (a no-op if present): allocates, launches the build on
+ * `stream` and synchronises that stream before returning.  enable == 0 frees
+ * it (synchronises the device first).  The plan owns the memory; sht_plan_destroy
+ * frees it.  Errors: SHT_EINVAL (no plan, prec not a tensor-core form),
+ * SHT_ENOMEM (allocation failed; the plan is unchanged), SHT_ECUDA. */
+int sht_lambda_cache(sht_plan_t plan, int prec, int enable, void *stream);
+
+/* Bytes the Lambda operand of form prec needs on this plan; 0 for a NULL plan
+ * or a form without one. */
+long long sht_lambda_cache_bytes(sht_plan_t plan, int prec);
+
 /* FP64 alm2map that allocates nothing (the paper has no counterpart: this is
  * an interface for callers that must not allocate device memory once their
  * processing loop runs, e.g. a host framework that has reserved nearly all

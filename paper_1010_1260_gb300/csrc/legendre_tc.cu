@@ -260,6 +260,43 @@ __device__ __forceinline__ void product_pieces(int i, int &ia, int &ib)
 // the chain's latency.  With SLOW = true rescaled rings contribute zeros and
 // the rescale test runs once per chunk of 2 VEC degrees (the values grow by
 // far less than 2^512 over a chunk).
+// Store the packed pieces of one 16-byte chunk (VEC values per parity).
+template <bool BF16, int NPA, int VEC>
+__device__ __forceinline__ void store_chunk(unsigned char *sbase, int t, int c, const uint32_t (&pe)[NPA][VEC],
+                                            const uint32_t (&po)[NPA][VEC])
+{
+    const int off = t * kRowBytes + ((c ^ ((t >> 2) & 1)) << 4);
+#pragma unroll
+    for (int i = 0; i < NPA; ++i) {
+        uint4 we, wo;
+        if (BF16) {
+            we = make_uint4((pe[i][0] >> 16) | (pe[i][1] & 0xFFFF0000u), (pe[i][2] >> 16) | (pe[i][3] & 0xFFFF0000u),
+                            (pe[i][4 % VEC] >> 16) | (pe[i][5 % VEC] & 0xFFFF0000u),
+                            (pe[i][6 % VEC] >> 16) | (pe[i][7 % VEC] & 0xFFFF0000u));
+            wo = make_uint4((po[i][0] >> 16) | (po[i][1] & 0xFFFF0000u), (po[i][2] >> 16) | (po[i][3] & 0xFFFF0000u),
+                            (po[i][4 % VEC] >> 16) | (po[i][5 % VEC] & 0xFFFF0000u),
+                            (po[i][6 % VEC] >> 16) | (po[i][7 % VEC] & 0xFFFF0000u));
+        } else {
+            we = make_uint4(pe[i][0], pe[i][1], pe[i][2 % VEC], pe[i][3 % VEC]);
+            wo = make_uint4(po[i][0], po[i][1], po[i][2 % VEC], po[i][3 % VEC]);
+        }
+        *reinterpret_cast<uint4 *>(sbase + (0 * NPA + i) * kTileBytes + off) = we;
+        *reinterpret_cast<uint4 *>(sbase + (1 * NPA + i) * kTileBytes + off) = wo;
+    }
+}
+
+// One producer stage: 2 KC consecutive degrees of one ring pair (row t),
+// written as NPA pieces into the stage's A tiles ([parity][piece], 4 KB
+// each, K-major rows of 32 bytes with the 32-byte swizzle).  a_cur holds
+// A_{l+1} for the stage's degrees, one per lane.
+// SLOW = false (no ring of the warp still rescaled): software-pipelined for
+// one warp per SM sub-partition issuing in order -- each degree issues its
+// DFMA (the only dependent chain), the DMUL of the degree two ahead (which
+// keeps the FP64 pipe busy during the DFMA latency), the shuffle of the
+// coefficient three ahead, then the integer / FP32 conversion of the current
+// value, so the conversions hide under the FP64 work instead of following it.
+// SLOW = true: rescaled rings contribute zeros and the rescale test runs once
+// per chunk of 2 VEC degrees (the values grow by far less than 2^512 over a chunk).
 template <bool BF16, int NPA, bool SLOW>
 __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, double x, double a_cur, int l, int L,
                                               double &p0, double &p1, int &k)
@@ -268,33 +305,67 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
     constexpr int VEC = BF16 ? 8 : 4;
     constexpr int NCH = KC / VEC;
     constexpr int STEPS = 2 * KC;
+    if (!SLOW) {
+        // A_{l+1} x two degrees ahead, A_{l+1} three degrees ahead: the DFMA of
+        // a degree never waits for its DMUL, nor the DMUL for its shuffle.
+        double ax0 = __shfl_sync(0xffffffffu, a_cur, 0) * x;
+        double ax1 = __shfl_sync(0xffffffffu, a_cur, 1) * x;
+        double an = __shfl_sync(0xffffffffu, a_cur, 2);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            uint32_t pe[NPA][VEC], po[NPA][VEC];
+#pragma unroll
+            for (int vv = 0; vv < VEC; vv += 2) {
+                // four degrees (two even, two odd l - m), then the four
+                // conversions: independent integer/FP32 chains that the
+                // scheduler interleaves under the FP64 latency
+                double val[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = c * 2 * VEC + 2 * vv + u;
+                    val[u] = p1;
+                    const double tt = fma(ax0, p1, -p0);
+                    ax0 = ax1;
+                    if (q + 2 < STEPS) ax1 = an * x;
+                    if (q + 3 < STEPS) an = __shfl_sync(0xffffffffu, a_cur, q + 3);
+                    p0 = p1;
+                    p1 = tt;
+                }
+                uint32_t cv[4][NPA];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = c * 2 * VEC + 2 * vv + u;
+                    split_pieces<BF16, NPA>(rn_f32(l + q <= L ? val[u] : 0.0), cv[u]);
+                }
+#pragma unroll
+                for (int i = 0; i < NPA; ++i) {
+                    pe[i][vv] = cv[0][i];
+                    po[i][vv] = cv[1][i];
+                    pe[i][vv + 1] = cv[2][i];
+                    po[i][vv + 1] = cv[3][i];
+                }
+            }
+            store_chunk<BF16, NPA, VEC>(sbase, t, c, pe, po);
+        }
+        return;
+    }
     double ax[STEPS], vv[STEPS];
 #pragma unroll
     for (int q = 0; q < STEPS; ++q) ax[q] = __shfl_sync(0xffffffffu, a_cur, q) * x;
-    if (!SLOW) {
 #pragma unroll
-        for (int q = 0; q < STEPS; ++q) {
-            vv[q] = p1;
+    for (int c = 0; c < NCH; ++c) {
+        const bool live_k = (k == 0);
+#pragma unroll
+        for (int q = c * 2 * VEC; q < (c + 1) * 2 * VEC; ++q) {
+            vv[q] = live_k ? p1 : 0.0;
             const double tt = fma(ax[q], p1, -p0);
             p0 = p1;
             p1 = tt;
         }
-    } else {
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            const bool live_k = (k == 0);
-#pragma unroll
-            for (int q = c * 2 * VEC; q < (c + 1) * 2 * VEC; ++q) {
-                vv[q] = live_k ? p1 : 0.0;
-                const double tt = fma(ax[q], p1, -p0);
-                p0 = p1;
-                p1 = tt;
-            }
-            if (k < 0 && above_hi(p1)) {
-                p1 *= 0x1p-512;
-                p0 *= 0x1p-512;
-                k += 1;
-            }
+        if (k < 0 && above_hi(p1)) {
+            p1 *= 0x1p-512;
+            p0 *= 0x1p-512;
+            k += 1;
         }
     }
 #pragma unroll
@@ -312,24 +383,7 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
                 po[i][v] = co[i];
             }
         }
-        const int off = t * kRowBytes + ((c ^ ((t >> 2) & 1)) << 4);
-#pragma unroll
-        for (int i = 0; i < NPA; ++i) {
-            uint4 we, wo;
-            if (BF16) {
-                we = make_uint4((pe[i][0] >> 16) | (pe[i][1] & 0xFFFF0000u), (pe[i][2] >> 16) | (pe[i][3] & 0xFFFF0000u),
-                                (pe[i][4 % VEC] >> 16) | (pe[i][5 % VEC] & 0xFFFF0000u),
-                                (pe[i][6 % VEC] >> 16) | (pe[i][7 % VEC] & 0xFFFF0000u));
-                wo = make_uint4((po[i][0] >> 16) | (po[i][1] & 0xFFFF0000u), (po[i][2] >> 16) | (po[i][3] & 0xFFFF0000u),
-                                (po[i][4 % VEC] >> 16) | (po[i][5 % VEC] & 0xFFFF0000u),
-                                (po[i][6 % VEC] >> 16) | (po[i][7 % VEC] & 0xFFFF0000u));
-            } else {
-                we = make_uint4(pe[i][0], pe[i][1], pe[i][2 % VEC], pe[i][3 % VEC]);
-                wo = make_uint4(po[i][0], po[i][1], po[i][2 % VEC], po[i][3 % VEC]);
-            }
-            *reinterpret_cast<uint4 *>(sbase + (0 * NPA + i) * kTileBytes + off) = we;
-            *reinterpret_cast<uint4 *>(sbase + (1 * NPA + i) * kTileBytes + off) = wo;
-        }
+        store_chunk<BF16, NPA, VEC>(sbase, t, c, pe, po);
     }
 }
 
@@ -338,10 +392,13 @@ constexpr int kPrefetch = 8;  // stages of B tiles prefetched into L2 ahead of t
 
 // Persistent kernel: CTA c handles work items c, c + gridDim.x, ... where
 // item j = (m = j / nrb, ring block rb = j % nrb): heavy (small m) items first.
-template <bool BF16, int NPA, int NPB>
+// CACHED: the A tiles come from the plan-time Lambda operand (acache, see
+// lambda_build_kernel) by bulk copy, and the producer warps stay idle.
+template <bool BF16, int NPA, int NPB, bool CACHED>
 __global__ void __launch_bounds__(kWarps * 32, 1)
-legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, const int *__restrict__ seg_off,
-                   float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status)
+legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, const unsigned char *__restrict__ acache,
+                   const int *__restrict__ seg_off, float2 *__restrict__ delta, int nmaps, int ncols,
+                   int *__restrict__ status)
 {
     using C = Cfg<BF16, NPA, NPB>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -400,7 +457,9 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    if (warp < 4) {
+    if (CACHED && warp < 4) {
+        // producers idle: the A tiles come with the B tiles by bulk copy
+    } else if (warp < 4) {
         // ------------------------------------------------------ producers --
         const int t = threadIdx.x;
         uint32_t gs = 0;
@@ -492,24 +551,37 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
         // The operand prep wrote the B tiles of every (m, stage) as one
         // contiguous block in the shared-memory image ([parity][piece] tiles
         // of 4 KB, swizzled), so one bulk copy fills a stage.
+        // With CACHED the stage's A tiles (one contiguous block of the
+        // Lambda operand) arrive on the same barrier.
         if (lane == 0) {
             constexpr uint32_t SB = (uint32_t)C::B_TILES * kTileBytes;
+            constexpr uint32_t SA = (uint32_t)C::A_TILES * kTileBytes;
             uint32_t gs = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const int m = item / nrb;
-                const unsigned char *blk = bbuf + (size_t)(seg_off[2 * m] / C::STEPS) * SB;
+                const size_t st0 = (size_t)(seg_off[2 * m] / C::STEPS);  // stages of the orders below m
+                const unsigned char *blk = bbuf + st0 * SB;
                 const int nst = nstages_of(m);
-                for (int i = 0; i < kPrefetch && i < nst; ++i) bulk_prefetch_l2(blk + (size_t)i * SB, SB);
+                const unsigned char *ablk =
+                    CACHED ? acache + (st0 * nrb + (size_t)(item % nrb) * nst) * SA : nullptr;
+                for (int i = 0; i < kPrefetch && i < nst; ++i) {
+                    bulk_prefetch_l2(blk + (size_t)i * SB, SB);
+                    if (CACHED) bulk_prefetch_l2(ablk + (size_t)i * SA, SA);
+                }
                 for (int i = 0; i < nst; ++i) {
                     const int s = (int)(gs % C::NS);
                     const uint32_t ph = (gs / C::NS) & 1u;
-                    if (i + kPrefetch < nst) bulk_prefetch_l2(blk + (size_t)(i + kPrefetch) * SB, SB);
+                    if (i + kPrefetch < nst) {
+                        bulk_prefetch_l2(blk + (size_t)(i + kPrefetch) * SB, SB);
+                        if (CACHED) bulk_prefetch_l2(ablk + (size_t)(i + kPrefetch) * SA, SA);
+                    }
                     if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(bar_full_b(s), SB);
+                    mbar_expect_tx(bar_full_b(s), CACHED ? SB + SA : SB);
+                    if (CACHED) bulk_load(smem_u32(a_tile(s, 0, 0)), ablk + (size_t)i * SA, SA, bar_full_b(s));
                     bulk_load(smem_u32(b_tile(s, 0, 0)), blk + (size_t)i * SB, SB, bar_full_b(s));
                     ++gs;
                 }
@@ -540,7 +612,8 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
                     for (int i = i0; i < i1; ++i) {
                         const int s = (int)(gs % C::NS);
                         const uint32_t ph = (gs / C::NS) & 1u;
-                        if (!mbar_wait(bar_full_a(s), ph, &s_abort) || !mbar_wait(bar_full_b(s), ph, &s_abort)) {
+                        if ((!CACHED && !mbar_wait(bar_full_a(s), ph, &s_abort)) ||
+                            !mbar_wait(bar_full_b(s), ph, &s_abort)) {
                             ok = false;
                             break;
                         }
@@ -642,13 +715,56 @@ cudaError_t run_prep(const DevPlan &P, const TcWork &W, const double2 *alm, int 
     return cudaGetLastError();
 }
 
-template <bool BF16, int NPA, int NPB>
-cudaError_t run_main(const DevPlan &P, const TcWork &W, float2 *delta, int nmaps, cudaStream_t st)
+// ------------------------------------------------- plan-time Lambda operand --
+// The A tiles of every (m, ring block rb, stage i) exactly as the producers
+// write them into shared memory (same recurrence, same rounding, same pieces,
+// same swizzle), one contiguous block of 2 x NPA tiles per stage at
+//   ((stages of the orders below m) x nrb + rb x nstages(m) + i) x block size,
+// so that a cached launch copies a stage with one bulk copy and gives results
+// identical to the recurrence launch.  One CTA of 128 threads per (rb, m).
+template <bool BF16, int NPA>
+__global__ void __launch_bounds__(kRows)
+lambda_build_kernel(const DevPlan P, const int *__restrict__ seg_off, unsigned char *__restrict__ aout)
+{
+    constexpr int STEPS = BF16 ? 32 : 16;
+    constexpr size_t SA = (size_t)2 * NPA * kTileBytes;
+    const int L = P.lmax;
+    const int nrb = (P.npairs + kRows - 1) / kRows;
+    const int rb = blockIdx.x;
+    const int m = blockIdx.y;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int pair = rb * kRows + t;
+    double x = 0.0, p0 = 0.0, p1 = 0.0;
+    int k = 0;
+    if (pair < P.npairs) {
+        x = P.pair_x[pair];
+        p1 = P.start_v[(size_t)m * P.npairs + pair];
+        k = P.start_k[(size_t)m * P.npairs + pair];
+    }
+    const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
+    const int nst = (L - m + 1 + STEPS - 1) / STEPS;
+    unsigned char *blk = aout + ((size_t)(seg_off[2 * m] / STEPS) * nrb + (size_t)rb * nst) * SA;
+    auto coef = [&](int lq) { return (lane < STEPS && lq <= L) ? __ldg(&P.coefA[mofs + (lq - m)]) : 0.0; };
+    int l = m;
+    for (int i = 0; i < nst; ++i) {
+        const double a_cur = coef(l + 1 + lane);
+        if (__any_sync(0xffffffffu, k < 0))
+            produce_stage<BF16, NPA, true>(blk + (size_t)i * SA, t, x, a_cur, l, L, p0, p1, k);
+        else
+            produce_stage<BF16, NPA, false>(blk + (size_t)i * SA, t, x, a_cur, l, L, p0, p1, k);
+        l += STEPS;
+    }
+}
+
+template <bool BF16, int NPA, int NPB, bool CACHED>
+cudaError_t run_main_t(const DevPlan &P, const TcWork &W, const void *acache, float2 *delta, int nmaps,
+                       cudaStream_t st)
 {
     using C = Cfg<BF16, NPA, NPB>;
     const int ncols = tc_ncols(nmaps);
     const int *seg = BF16 ? W.seg_bf16 : W.seg_tf32;
-    auto kern = legendre_tc_kernel<BF16, NPA, NPB>;
+    auto kern = legendre_tc_kernel<BF16, NPA, NPB, CACHED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
@@ -656,9 +772,18 @@ cudaError_t run_main(const DevPlan &P, const TcWork &W, float2 *delta, int nmaps
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const long long nitems = (long long)((P.npairs + kRows - 1) / kRows) * (P.mmax + 1);
     const int grid = (int)std::min<long long>(nitems, nsm);  // persistent: one CTA per SM
-    kern<<<grid, kWarps * 32, C::SMEM, st>>>(P, static_cast<const unsigned char *>(W.bbuf), seg, delta, nmaps,
-                                             ncols, W.status);
+    kern<<<grid, kWarps * 32, C::SMEM, st>>>(P, static_cast<const unsigned char *>(W.bbuf),
+                                             static_cast<const unsigned char *>(acache), seg, delta, nmaps, ncols,
+                                             W.status);
     return cudaGetLastError();
+}
+
+template <bool BF16, int NPA, int NPB>
+cudaError_t run_main(const DevPlan &P, const TcWork &W, const void *acache, float2 *delta, int nmaps,
+                     cudaStream_t st)
+{
+    if (acache) return run_main_t<BF16, NPA, NPB, true>(P, W, acache, delta, nmaps, st);
+    return run_main_t<BF16, NPA, NPB, false>(P, W, nullptr, delta, nmaps, st);
 }
 
 }  // namespace
@@ -671,6 +796,31 @@ size_t tc_bbuf_bytes(const TcWork &W, int prec)
     return (size_t)3 * 128 * W.kall_bf16 * 2;
 }
 
+size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec)
+{
+    // stages of all orders x ring blocks x (2 parities x pieces x 4 KB)
+    const size_t nrb = (size_t)((P.npairs + kRows - 1) / kRows);
+    if (prec == SHT_FP32_TC) return (size_t)(W.kall_tf32 / 16) * nrb * 2 * 2 * kTileBytes;
+    if (prec == SHT_BF16X3_TC) return (size_t)(W.kall_bf16 / 32) * nrb * 2 * 2 * kTileBytes;
+    if (prec == SHT_BF16X6_TC) return (size_t)(W.kall_bf16 / 32) * nrb * 2 * 3 * kTileBytes;
+    return 0;
+}
+
+cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, void *out, cudaStream_t st)
+{
+    dim3 grid((P.npairs + kRows - 1) / kRows, P.mmax + 1);
+    unsigned char *o = static_cast<unsigned char *>(out);
+    if (prec == SHT_FP32_TC)
+        lambda_build_kernel<false, 2><<<grid, kRows, 0, st>>>(P, W.seg_tf32, o);
+    else if (prec == SHT_BF16X3_TC)
+        lambda_build_kernel<true, 2><<<grid, kRows, 0, st>>>(P, W.seg_bf16, o);
+    else if (prec == SHT_BF16X6_TC)
+        lambda_build_kernel<true, 3><<<grid, kRows, 0, st>>>(P, W.seg_bf16, o);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const double2 *alm, int nmaps, cudaStream_t st)
 {
     if (nmaps <= 0) return cudaSuccess;
@@ -680,13 +830,14 @@ cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const do
     return run_prep<true, 3, 3>(P, W, alm, nmaps, st);
 }
 
-cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, float2 *delta, int nmaps, cudaStream_t st)
+cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, const void *acache, float2 *delta, int nmaps,
+                           cudaStream_t st)
 {
     if (nmaps <= 0) return cudaSuccess;
     if (nmaps > kTcMaxMaps) return cudaErrorInvalidValue;
-    if (prec == SHT_FP32_TC) return run_main<false, 2, 2>(P, W, delta, nmaps, st);
-    if (prec == SHT_BF16X3_TC) return run_main<true, 2, 2>(P, W, delta, nmaps, st);
-    return run_main<true, 3, 3>(P, W, delta, nmaps, st);
+    if (prec == SHT_FP32_TC) return run_main<false, 2, 2>(P, W, acache, delta, nmaps, st);
+    if (prec == SHT_BF16X3_TC) return run_main<true, 2, 2>(P, W, acache, delta, nmaps, st);
+    return run_main<true, 3, 3>(P, W, acache, delta, nmaps, st);
 }
 
 }  // namespace sht

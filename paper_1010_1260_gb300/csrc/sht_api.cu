@@ -38,6 +38,8 @@ struct sht_plan_s {
     std::vector<int> rings_smooth_h, rings_blue_h;  // host copies of the ring lists
     sht::TcWork tc;      // tensor-core forms: segment tables, status word, B-operand buffer
     size_t tc_bytes = 0;
+    void *lcache[4] = {};  // plan-time Lambda operand per tensor-core form (sht_lambda_cache)
+    size_t lcache_bytes[4] = {};
     std::mutex mu;
 };
 
@@ -197,6 +199,8 @@ void free_plan(sht_plan_s *p)
         for (void *d : p->allocs) cudaFree(d);
         if (p->ws) cudaFree(p->ws);
         if (p->tc.bbuf) cudaFree(p->tc.bbuf);
+        for (void *c : p->lcache)
+            if (c) cudaFree(c);
         for (auto &e : p->prof_pending) {
             cudaEventDestroy(e.a);
             cudaEventDestroy(e.b);
@@ -591,8 +595,9 @@ int check_plan(sht_plan_t p)
     return SHT_OK;
 }
 
-// Precision forms: FP64 recurrence + tensor-core contraction (groups of at
-// most 64 maps), FP32 Delta, FP32 ring step, float32 maps.
+// Precision forms: FP64 recurrence (or the plan-time Lambda operand, when
+// cached) + tensor-core contraction (groups of at most 64 maps), FP32 Delta,
+// FP32 ring step, float32 maps.
 int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, int prec, void *stream)
 {
     std::lock_guard<std::mutex> lk(p->mu);
@@ -613,7 +618,7 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
         s0.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
         StageScope s1(p, SHT_STAGE_LEGENDRE, st);
-        e = sht::launch_tc_main(p->dp, p->tc, prec, delta, nb, st);
+        e = sht::launch_tc_main(p->dp, p->tc, prec, p->lcache[prec], delta, nb, st);
         s1.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc launch");
         StageScope s2(p, SHT_STAGE_RING, st);
@@ -702,6 +707,53 @@ int sht_plan(const sht_grid *g, int lmax, int mmax, sht_plan_t *out)
         return rc;
     }
     *out = p;
+    return SHT_OK;
+}
+
+long long sht_lambda_cache_bytes(sht_plan_t p, int prec)
+{
+    if (!p || (prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)) return 0;
+    return (long long)sht::tc_lambda_bytes(p->dp, p->tc, prec);
+}
+
+int sht_lambda_cache(sht_plan_t p, int prec, int enable, void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
+        return fail(SHT_EINVAL, "the Lambda operand exists for the tensor-core forms only (prec %d)", prec);
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!enable) {
+        if (!p->lcache[prec]) return SHT_OK;
+        cudaError_t e = cudaDeviceSynchronize();  // no launch may still read it
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        cudaFree(p->lcache[prec]);
+        p->lcache[prec] = nullptr;
+        p->lcache_bytes[prec] = 0;
+        return SHT_OK;
+    }
+    if (p->lcache[prec]) return SHT_OK;
+    const size_t need = sht::tc_lambda_bytes(p->dp, p->tc, prec);
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SHT_ENOMEM, "Lambda operand cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+    }
+    e = sht::launch_lambda_build(p->dp, p->tc, prec, buf, st);
+    if (e == cudaSuccess) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_fail(e, "lambda_build");
+    }
+    p->lcache[prec] = buf;
+    p->lcache_bytes[prec] = need;
     return SHT_OK;
 }
 

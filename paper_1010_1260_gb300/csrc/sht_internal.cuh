@@ -121,8 +121,12 @@ inline int tc_ncols(int nmaps) { return ((2 * nmaps + 31) / 32) * 32; }
 size_t tc_bbuf_bytes(const TcWork &W, int prec);
 cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const double2 *alm, int nmaps,
                            cudaStream_t st);
-cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, float2 *delta, int nmaps,
-                           cudaStream_t st);
+// acache: the plan-time Lambda operand of form prec (launch_lambda_build), or
+// nullptr to run the FP64 recurrence in the launch.
+cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, const void *acache, float2 *delta,
+                           int nmaps, cudaStream_t st);
+size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
+cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, void *out, cudaStream_t st);
 
 // Kernels one ring-step launch issues (one per non-empty ring list).
 inline int ring_launches(const DevPlan &P) { return (P.n_smooth > 0) + (P.n_blue > 0); }

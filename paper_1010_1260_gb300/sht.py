@@ -80,12 +80,15 @@ def lib():
             L.sht_multi_alm2map.argtypes = [P, PP, PP, V]
             L.sht_multi_destroy.argtypes = [P]
             L.sht_alm2map_multi.argtypes = [I, PP, PP, PP, I, V]
+            L.sht_lambda_cache.argtypes = [P, I, I, V]
+            L.sht_lambda_cache_bytes.argtypes = [P, I]
+            L.sht_lambda_cache_bytes.restype = ctypes.c_longlong
             L.sht_kernel_launches.argtypes = []
             L.sht_kernel_launches.restype = ctypes.c_ulonglong
             for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
                       "sht_alm2map_batch", "sht_map2alm_adjoint_batch", "sht_profile",
                       "sht_profile_read", "sht_sync", "sht_multi_create", "sht_multi_alm2map",
-                      "sht_multi_destroy", "sht_alm2map_multi"):
+                      "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -208,6 +211,17 @@ class Plan:
         check(lib().sht_map2alm_adjoint_batch(self._h, B, y.data_ptr(), out.data_ptr(), PREC[prec],
                                               _stream_ptr(stream)))
         return out.reshape(self.nalm) if single else out.reshape(B, self.nalm)
+
+    # ------------------------------------------------- Lambda operand --
+    def lambda_cache_bytes(self, prec: str) -> int:
+        """Device bytes the plan-time Lambda operand of form ``prec`` needs."""
+        return int(lib().sht_lambda_cache_bytes(self._h, PREC[prec]))
+
+    def lambda_cache(self, prec: str, enable: bool = True, stream=None):
+        """Build (or free) the plan-time Lambda operand of a tensor-core form;
+        later alm2map calls of that form stream it instead of running the
+        recurrence, with identical results."""
+        check(lib().sht_lambda_cache(self._h, PREC[prec], 1 if enable else 0, _stream_ptr(stream)))
 
     def sync(self):
         """Wait for the plan's device; raise ShtError(SHT_ETIMEOUT) if a kernel
