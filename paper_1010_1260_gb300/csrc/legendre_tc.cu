@@ -305,7 +305,7 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
     constexpr int VEC = BF16 ? 8 : 4;
     constexpr int NCH = KC / VEC;
     constexpr int STEPS = 2 * KC;
-    if (!SLOW) {
+    if constexpr (!SLOW) {
         // A_{l+1} x two degrees ahead, A_{l+1} three degrees ahead: the DFMA of
         // a degree never waits for its DMUL, nor the DMUL for its shuffle.
         double ax0 = __shfl_sync(0xffffffffu, a_cur, 0) * x;
@@ -392,13 +392,10 @@ constexpr int kPrefetch = 8;  // stages of B tiles prefetched into L2 ahead of t
 
 // Persistent kernel: CTA c handles work items c, c + gridDim.x, ... where
 // item j = (m = j / nrb, ring block rb = j % nrb): heavy (small m) items first.
-// CACHED: the A tiles come from the plan-time Lambda operand (acache, see
-// lambda_build_kernel) by bulk copy, and the producer warps stay idle.
-template <bool BF16, int NPA, int NPB, bool CACHED>
+template <bool BF16, int NPA, int NPB>
 __global__ void __launch_bounds__(kWarps * 32, 1)
-legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, const unsigned char *__restrict__ acache,
-                   const int *__restrict__ seg_off, float2 *__restrict__ delta, int nmaps, int ncols,
-                   int *__restrict__ status)
+legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, const int *__restrict__ seg_off,
+                   float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status)
 {
     using C = Cfg<BF16, NPA, NPB>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -457,9 +454,7 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    if (CACHED && warp < 4) {
-        // producers idle: the A tiles come with the B tiles by bulk copy
-    } else if (warp < 4) {
+    if (warp < 4) {
         // ------------------------------------------------------ producers --
         const int t = threadIdx.x;
         uint32_t gs = 0;
@@ -532,17 +527,19 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
                 ++gg;
             }
             if (!ok) break;
-            // Delta_m(north) = E + O, Delta_m(south) = E - O for this item's rows
+            // Delta_m(north) = E + O, Delta_m(south) = E - O for this item's
+            // rows; Delta is [ring][m][map], so a row's maps are contiguous
             if (pair < P.npairs) {
                 const int2 rr = P.pair_ring[pair];
                 const int M1 = P.mmax + 1;
+                float2 *dn = delta + ((size_t)rr.x * M1 + m) * nmaps;
+                float2 *ds = delta + ((size_t)max(rr.y, 0) * M1 + m) * nmaps;
                 for (int b = 0; b < nmaps; ++b) {
                     const float er = tot[(2 * b) * kRows + row], ei = tot[(2 * b + 1) * kRows + row];
                     const float orr = tot[(ncols + 2 * b) * kRows + row];
                     const float oi = tot[(ncols + 2 * b + 1) * kRows + row];
-                    float2 *d = delta + (size_t)b * P.nrings * M1;
-                    d[(size_t)rr.x * M1 + m] = make_float2(er + orr, (m == 0) ? 0.f : ei + oi);
-                    if (rr.y >= 0) d[(size_t)rr.y * M1 + m] = make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
+                    dn[b] = make_float2(er + orr, (m == 0) ? 0.f : ei + oi);
+                    if (rr.y >= 0) ds[b] = make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
                 }
             }
         }
@@ -551,37 +548,24 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
         // The operand prep wrote the B tiles of every (m, stage) as one
         // contiguous block in the shared-memory image ([parity][piece] tiles
         // of 4 KB, swizzled), so one bulk copy fills a stage.
-        // With CACHED the stage's A tiles (one contiguous block of the
-        // Lambda operand) arrive on the same barrier.
         if (lane == 0) {
             constexpr uint32_t SB = (uint32_t)C::B_TILES * kTileBytes;
-            constexpr uint32_t SA = (uint32_t)C::A_TILES * kTileBytes;
             uint32_t gs = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const int m = item / nrb;
-                const size_t st0 = (size_t)(seg_off[2 * m] / C::STEPS);  // stages of the orders below m
-                const unsigned char *blk = bbuf + st0 * SB;
+                const unsigned char *blk = bbuf + (size_t)(seg_off[2 * m] / C::STEPS) * SB;
                 const int nst = nstages_of(m);
-                const unsigned char *ablk =
-                    CACHED ? acache + (st0 * nrb + (size_t)(item % nrb) * nst) * SA : nullptr;
-                for (int i = 0; i < kPrefetch && i < nst; ++i) {
-                    bulk_prefetch_l2(blk + (size_t)i * SB, SB);
-                    if (CACHED) bulk_prefetch_l2(ablk + (size_t)i * SA, SA);
-                }
+                for (int i = 0; i < kPrefetch && i < nst; ++i) bulk_prefetch_l2(blk + (size_t)i * SB, SB);
                 for (int i = 0; i < nst; ++i) {
                     const int s = (int)(gs % C::NS);
                     const uint32_t ph = (gs / C::NS) & 1u;
-                    if (i + kPrefetch < nst) {
-                        bulk_prefetch_l2(blk + (size_t)(i + kPrefetch) * SB, SB);
-                        if (CACHED) bulk_prefetch_l2(ablk + (size_t)(i + kPrefetch) * SA, SA);
-                    }
+                    if (i + kPrefetch < nst) bulk_prefetch_l2(blk + (size_t)(i + kPrefetch) * SB, SB);
                     if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(bar_full_b(s), CACHED ? SB + SA : SB);
-                    if (CACHED) bulk_load(smem_u32(a_tile(s, 0, 0)), ablk + (size_t)i * SA, SA, bar_full_b(s));
+                    mbar_expect_tx(bar_full_b(s), SB);
                     bulk_load(smem_u32(b_tile(s, 0, 0)), blk + (size_t)i * SB, SB, bar_full_b(s));
                     ++gs;
                 }
@@ -612,8 +596,7 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
                     for (int i = i0; i < i1; ++i) {
                         const int s = (int)(gs % C::NS);
                         const uint32_t ph = (gs / C::NS) & 1u;
-                        if ((!CACHED && !mbar_wait(bar_full_a(s), ph, &s_abort)) ||
-                            !mbar_wait(bar_full_b(s), ph, &s_abort)) {
+                        if (!mbar_wait(bar_full_a(s), ph, &s_abort) || !mbar_wait(bar_full_b(s), ph, &s_abort)) {
                             ok = false;
                             break;
                         }
@@ -641,6 +624,240 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
             }
             if (!ok && issued) {
                 // wait (bounded) for the MMAs already issued before tensor memory is freed
+                tc_commit(bar_mma_drain);
+                mbar_drain(bar_mma_drain, 0u);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+    }
+    if (threadIdx.x == 0 && s_abort) atomicExch(status, SHT_ETIMEOUT);
+}
+
+// ------------------------------------------------ streaming (cached) kernel --
+// The same contraction with the A tiles read from the plan-time Lambda
+// operand (lambda_build_kernel) instead of computed: no producer warps, so
+// the drain keeps its FP32 totals in registers and shared memory holds only
+// the stage ring, NS_STREAM stages deep.  Persistent, one CTA per SM:
+//   warps 0-7  drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 32 and
+//              the 32-column chunks q = 2 j + w / 4 of E and O; after every 64
+//              degrees it adds the finished accumulator set into its register
+//              totals (FP32, round to nearest: the order and rounding of the
+//              recurrence kernel's drain, so the results are bit-identical),
+//              and at the end of an item writes Delta for its maps;
+//   warp 8     tensor memory, and one bulk copy each for the stage's A and B
+//              tiles (no L2 prefetch: with NS stages of bulk copies in
+//              flight it only competed with them);
+//   warp 9     the MMAs, as in legendre_tc_kernel.
+template <bool BF16, int NPA, int NPB>
+struct StreamCfg {
+    using C = Cfg<BF16, NPA, NPB>;
+    static constexpr int NS = (200 * 1024) / C::STAGE_BYTES;  // 4 (48 KB stages) or 6 (32 KB)
+    static constexpr int SMEM = NS * C::STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
+};
+
+template <bool BF16, int NPA, int NPB>
+__global__ void __launch_bounds__(kWarps * 32, 1)
+legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf,
+                          const unsigned char *__restrict__ acache, const int *__restrict__ seg_off,
+                          float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status)
+{
+    using C = Cfg<BF16, NPA, NPB>;
+    constexpr int NS = StreamCfg<BF16, NPA, NPB>::NS;
+    constexpr uint32_t SA = (uint32_t)C::A_TILES * kTileBytes;
+    constexpr uint32_t SB = (uint32_t)C::B_TILES * kTileBytes;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    const uint32_t pad = (1024u - (base_u32 & 1023u)) & 1023u;
+    unsigned char *stage0 = smem_raw + pad;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + NS * C::STAGE_BYTES);
+    // bars: full[NS], empty[NS], set_full[2], set_empty[2], mma_drain
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int L = P.lmax;
+    const int nrb = (P.npairs + kRows - 1) / kRows;
+    const int nitems = nrb * (P.mmax + 1);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    auto bar_full = [&](int s) { return smem_u32(&bars[s]); };
+    auto bar_empty = [&](int s) { return smem_u32(&bars[NS + s]); };
+    auto bar_set_full = [&](int j) { return smem_u32(&bars[2 * NS + j]); };
+    auto bar_set_empty = [&](int j) { return smem_u32(&bars[2 * NS + 2 + j]); };
+    const uint32_t bar_mma_drain = smem_u32(&bars[2 * NS + 4]);
+    auto a_tile = [&](int s, int par, int piece) {
+        return stage0 + s * C::STAGE_BYTES + (par * NPA + piece) * kTileBytes;
+    };
+    auto b_tile = [&](int s, int par, int piece) {
+        return stage0 + s * C::STAGE_BYTES + (C::A_TILES + par * NPB + piece) * kTileBytes;
+    };
+    auto nstages_of = [&](int m) { return (L - m + 1 + C::STEPS - 1) / C::STEPS; };
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(bar_full(s), 1);
+            mbar_init(bar_empty(s), 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(bar_set_full(j), 1);
+            mbar_init(bar_set_empty(j), 8);
+        }
+        mbar_init(bar_mma_drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp < 8) {
+        // ----------------------------------------------------------- drain --
+        const int quad = warp & 3;
+        const int half = warp >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        float te[2][32], to[2][32];  // totals of chunks q = 2 j + half of E and O
+        uint32_t gg = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int m = item / nrb;
+            const int pair = (item % nrb) * kRows + row;
+            const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP;
+            for (int g = 0; g < ngroups; ++g) {
+                const int set = (int)(gg & 1u);
+                ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
+                if (!ok) break;
+                tc_fence_after();
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int q = 2 * j + half;
+                    if (32 * q < ncols) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + lane_base + (uint32_t)(256 * set + 32 * q), v);
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) te[j][c] = (g == 0) ? __uint_as_float(v[c]) : te[j][c] + __uint_as_float(v[c]);
+                        tmem_ld32(tmem + lane_base + (uint32_t)(256 * set + ncols + 32 * q), v);
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) to[j][c] = (g == 0) ? __uint_as_float(v[c]) : to[j][c] + __uint_as_float(v[c]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_set_empty(set));
+                ++gg;
+            }
+            if (!ok) break;
+            // Delta_m(north) = E + O, Delta_m(south) = E - O for this row's
+            // maps; Delta is [ring][m][map]: 16 contiguous maps per chunk
+            if (pair < P.npairs) {
+                const int2 rr = P.pair_ring[pair];
+                const int M1 = P.mmax + 1;
+                float2 *dn = delta + ((size_t)rr.x * M1 + m) * nmaps;
+                float2 *ds = delta + ((size_t)max(rr.y, 0) * M1 + m) * nmaps;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int q = 2 * j + half;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int b = 16 * q + c;  // columns 2 b, 2 b + 1 of chunk q
+                        if (32 * q < ncols && b < nmaps) {
+                            const float er = te[j][2 * c], ei = te[j][2 * c + 1];
+                            const float orr = to[j][2 * c], oi = to[j][2 * c + 1];
+                            dn[b] = make_float2(er + orr, (m == 0) ? 0.f : ei + oi);
+                            if (rr.y >= 0) ds[b] = make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == 8) {
+        // ---------------------------------------------------- A + B loads --
+        if (lane == 0) {
+            uint32_t gs = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int m = item / nrb;
+                const size_t st0 = (size_t)(seg_off[2 * m] / C::STEPS);  // stages of the orders below m
+                const int nst = nstages_of(m);
+                const unsigned char *bblk = bbuf + st0 * SB;
+                const unsigned char *ablk = acache + (st0 * nrb + (size_t)(item % nrb) * nst) * SA;
+                for (int i = 0; i < nst; ++i) {
+                    const int s = (int)(gs % NS);
+                    const uint32_t ph = (gs / NS) & 1u;
+                    if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(bar_full(s), SA + SB);
+                    bulk_load(smem_u32(a_tile(s, 0, 0)), ablk + (size_t)i * SA, SA, bar_full(s));
+                    bulk_load(smem_u32(b_tile(s, 0, 0)), bblk + (size_t)i * SB, SB, bar_full(s));
+                    ++gs;
+                }
+            }
+            if (s_abort) {
+                const uint32_t first = gs > (uint32_t)NS ? gs - NS : 0u;
+                for (uint32_t j = first; j < gs; ++j) mbar_drain(bar_full((int)(j % NS)), (j / NS) & 1u);
+            }
+        }
+    } else {
+        // ----------------------------------------------------------- MMA --
+        if (lane == 0) {
+            const uint32_t id = idesc<BF16>(ncols);
+            uint32_t gs = 0, gg = 0;
+            bool ok = true, issued = false;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int m = item / nrb;
+                const int nst = nstages_of(m);
+                for (int i0 = 0; i0 < nst && ok; i0 += C::GROUP) {
+                    const int set = (int)(gg & 1u);
+                    if (!mbar_wait(bar_set_empty(set), ((gg >> 1) & 1u) ^ 1u, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int i1 = min(nst, i0 + C::GROUP);
+                    for (int i = i0; i < i1; ++i) {
+                        const int s = (int)(gs % NS);
+                        const uint32_t ph = (gs / NS) & 1u;
+                        if (!mbar_wait(bar_full(s), ph, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+#pragma unroll
+                        for (int par = 0; par < 2; ++par) {
+                            const uint32_t d = tmem + (uint32_t)(256 * set + par * ncols);
+#pragma unroll
+                            for (int pr = 0; pr < C::NPROD; ++pr) {
+                                int ia, ib;
+                                product_pieces<NPA, NPB>(pr, ia, ib);
+                                const uint64_t ad = sdesc_sw32(smem_u32(a_tile(s, par, ia)));
+                                const uint64_t bd = sdesc_sw32(smem_u32(b_tile(s, par, ib)));
+                                tc_mma<BF16>(d, ad, bd, id, (i > i0 || pr > 0) ? 1u : 0u);
+                            }
+                        }
+                        issued = true;
+                        tc_commit(bar_empty(s));
+                        ++gs;
+                    }
+                    if (!ok) break;
+                    tc_commit(bar_set_full(set));
+                    ++gg;
+                }
+            }
+            if (!ok && issued) {
                 tc_commit(bar_mma_drain);
                 mbar_drain(bar_mma_drain, 0u);
             }
@@ -757,24 +974,47 @@ lambda_build_kernel(const DevPlan P, const int *__restrict__ seg_off, unsigned c
     }
 }
 
-template <bool BF16, int NPA, int NPB, bool CACHED>
-cudaError_t run_main_t(const DevPlan &P, const TcWork &W, const void *acache, float2 *delta, int nmaps,
-                       cudaStream_t st)
+// Delta relayout for the ring step: in[(r, m)][b] (the tensor-core kernels'
+// whole-sector layout) -> out[b][(r, m)], through 32 x 32 shared-memory tiles
+// so that reads and writes are both contiguous.
+__global__ void __launch_bounds__(256)
+delta_relayout_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long long nrows, int nmaps)
 {
-    using C = Cfg<BF16, NPA, NPB>;
-    const int ncols = tc_ncols(nmaps);
-    const int *seg = BF16 ? W.seg_bf16 : W.seg_tf32;
-    auto kern = legendre_tc_kernel<BF16, NPA, NPB, CACHED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    __shared__ float2 tile[32][33];
+    const long long r0 = (long long)blockIdx.x * 32;
+    const int b0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+        const long long r = r0 + ty + i;
+        if (r < nrows && b0 + tx < nmaps) tile[ty + i][tx] = in[r * nmaps + b0 + tx];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+        const int b = b0 + ty + i;
+        if (b < nmaps && r0 + tx < nrows) out[(size_t)b * nrows + r0 + tx] = tile[tx][ty + i];
+    }
+}
+
+template <bool STREAM, typename K>
+cudaError_t launch_persistent(K kern, int smem, const DevPlan &P, const TcWork &W, const void *acache,
+                             const int *seg, float2 *delta, int nmaps, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const long long nitems = (long long)((P.npairs + kRows - 1) / kRows) * (P.mmax + 1);
     const int grid = (int)std::min<long long>(nitems, nsm);  // persistent: one CTA per SM
-    kern<<<grid, kWarps * 32, C::SMEM, st>>>(P, static_cast<const unsigned char *>(W.bbuf),
-                                             static_cast<const unsigned char *>(acache), seg, delta, nmaps, ncols,
-                                             W.status);
+    const unsigned char *b = static_cast<const unsigned char *>(W.bbuf);
+    const int ncols = tc_ncols(nmaps);
+    if constexpr (STREAM)
+        kern<<<grid, kWarps * 32, smem, st>>>(P, b, static_cast<const unsigned char *>(acache), seg, delta, nmaps,
+                                              ncols, W.status);
+    else
+        kern<<<grid, kWarps * 32, smem, st>>>(P, b, seg, delta, nmaps, ncols, W.status);
     return cudaGetLastError();
 }
 
@@ -782,8 +1022,12 @@ template <bool BF16, int NPA, int NPB>
 cudaError_t run_main(const DevPlan &P, const TcWork &W, const void *acache, float2 *delta, int nmaps,
                      cudaStream_t st)
 {
-    if (acache) return run_main_t<BF16, NPA, NPB, true>(P, W, acache, delta, nmaps, st);
-    return run_main_t<BF16, NPA, NPB, false>(P, W, nullptr, delta, nmaps, st);
+    const int *seg = BF16 ? W.seg_bf16 : W.seg_tf32;
+    if (acache)
+        return launch_persistent<true>(legendre_tc_stream_kernel<BF16, NPA, NPB>, StreamCfg<BF16, NPA, NPB>::SMEM, P, W,
+                                 acache, seg, delta, nmaps, st);
+    return launch_persistent<false>(legendre_tc_kernel<BF16, NPA, NPB>, Cfg<BF16, NPA, NPB>::SMEM, P, W, nullptr, seg, delta,
+                             nmaps, st);
 }
 
 }  // namespace
@@ -794,6 +1038,14 @@ size_t tc_bbuf_bytes(const TcWork &W, int prec)
     if (prec == SHT_FP32_TC) return (size_t)2 * 128 * W.kall_tf32 * 4;
     if (prec == SHT_BF16X3_TC) return (size_t)2 * 128 * W.kall_bf16 * 2;
     return (size_t)3 * 128 * W.kall_bf16 * 2;
+}
+
+cudaError_t launch_delta_relayout(const float2 *in, float2 *out, long long nrows, int nmaps, cudaStream_t st)
+{
+    if (nmaps <= 0 || nrows <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((nrows + 31) / 32), (nmaps + 31) / 32);
+    delta_relayout_kernel<<<grid, 256, 0, st>>>(in, out, nrows, nmaps);
+    return cudaGetLastError();
 }
 
 size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec)

@@ -83,8 +83,13 @@ cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smoot
                                          int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
                                          const MultiPtrs &ptrs, cudaStream_t st);
 
+// The tensor-core Legendre kernels write Delta as [ring][m][map] (a row's
+// maps contiguous, so every store fills whole sectors); this relayouts it to
+// the ring step's [map][ring][m] (nrows = nrings x (mmax + 1)).
+cudaError_t launch_delta_relayout(const float2 *in, float2 *out, long long nrows, int nmaps, cudaStream_t st);
+
 // Ring step: phase shift, fold of m onto the ring's bins, real inverse DFT of
-// each ring.  T = double (FP64 path) or float (tensor-core paths).
+// each ring; delta is [map][ring][m].
 cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps,
                                    cudaStream_t st);
 cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float *map, int nmaps,
