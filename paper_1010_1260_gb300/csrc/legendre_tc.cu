@@ -974,29 +974,6 @@ lambda_build_kernel(const DevPlan P, const int *__restrict__ seg_off, unsigned c
     }
 }
 
-// Delta relayout for the ring step: in[(r, m)][b] (the tensor-core kernels'
-// whole-sector layout) -> out[b][(r, m)], through 32 x 32 shared-memory tiles
-// so that reads and writes are both contiguous.
-__global__ void __launch_bounds__(256)
-delta_relayout_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long long nrows, int nmaps)
-{
-    __shared__ float2 tile[32][33];
-    const long long r0 = (long long)blockIdx.x * 32;
-    const int b0 = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-#pragma unroll
-    for (int i = 0; i < 32; i += 8) {
-        const long long r = r0 + ty + i;
-        if (r < nrows && b0 + tx < nmaps) tile[ty + i][tx] = in[r * nmaps + b0 + tx];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 32; i += 8) {
-        const int b = b0 + ty + i;
-        if (b < nmaps && r0 + tx < nrows) out[(size_t)b * nrows + r0 + tx] = tile[tx][ty + i];
-    }
-}
-
 template <bool STREAM, typename K>
 cudaError_t launch_persistent(K kern, int smem, const DevPlan &P, const TcWork &W, const void *acache,
                              const int *seg, float2 *delta, int nmaps, cudaStream_t st)
@@ -1038,14 +1015,6 @@ size_t tc_bbuf_bytes(const TcWork &W, int prec)
     if (prec == SHT_FP32_TC) return (size_t)2 * 128 * W.kall_tf32 * 4;
     if (prec == SHT_BF16X3_TC) return (size_t)2 * 128 * W.kall_bf16 * 2;
     return (size_t)3 * 128 * W.kall_bf16 * 2;
-}
-
-cudaError_t launch_delta_relayout(const float2 *in, float2 *out, long long nrows, int nmaps, cudaStream_t st)
-{
-    if (nmaps <= 0 || nrows <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((nrows + 31) / 32), (nmaps + 31) / 32);
-    delta_relayout_kernel<<<grid, 256, 0, st>>>(in, out, nrows, nmaps);
-    return cudaGetLastError();
 }
 
 size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec)

@@ -17,6 +17,8 @@
 // phi0 = pi * ps / n with an integer ps, so e^{i m phi0} = T_n[(m ps) mod 2n].
 #include "sht_internal.cuh"
 
+#include <algorithm>
+
 namespace sht {
 namespace {
 
@@ -102,8 +104,8 @@ __device__ int factorize(int N, int *rad)
 // shared-memory table w_N^q = e^{2 pi i q / N}, q < N (conjugated for the
 // forward sign).  Pass with radix R and sub-transform size Ns:
 //   Y[(j/Ns) Ns R + j%Ns + q Ns] = sum_r X[j + r N/R] w_{Ns R}^{r (j%Ns)} w_R^{r q}.
-template <bool INV, typename R, typename C>
-__device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, const int npass)
+template <bool INV, typename R, typename C, int G = 1>
+__device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, const int npass, const int gs = 0)
 {
     const int tid = threadIdx.x;
     const R sg = INV ? (R)1 : (R)-1;
@@ -127,147 +129,196 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
         // j / Ns: a shift while Ns is a power of two (all earlier radices 8, 4, 2)
         const bool ns_pow2 = (Ns & (Ns - 1)) == 0;
         const int ns_sh = __ffs(Ns) - 1;
+        // (g, kk) = (j / Ns, j % Ns) for j = tid, advanced by (dq, dr) per kThreads
+        const int g0 = ns_pow2 ? (tid >> ns_sh) : tid / Ns;
+        const int kk0 = tid - g0 * Ns;
+        const int dq = ns_pow2 ? (kThreads >> ns_sh) : kThreads / Ns;
+        const int dr = kThreads - dq * Ns;
         // r kk tscale < R Ns N / (Ns R) = N: twiddle indices need no reduction
         if (Rr == 8) {
             const R c8 = (R)0.70710678118654752440084436210485;  // 1/sqrt(2)
-            for (int j = tid; j < NR; j += kThreads) {
-                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
-                const int kk = j - g * Ns;
-                C v[8];
 #pragma unroll
-                for (int r = 0; r < 8; ++r) v[r] = src[j + r * NR];
-                if (kk) {
-                    const int e = kk * tscale;
+            for (int gm = 0; gm < G; ++gm) {
+                const C *sx = src + (size_t)gm * gs;
+                C *dx = dst + (size_t)gm * gs;
+                int g = g0, kk = kk0;
+                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
+                    if (kk >= Ns) {
+                        kk -= Ns;
+                        ++g;
+                    }
+                    C v[8];
 #pragma unroll
-                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw(r * e));
-                }
-                // X_{2q} = DFT4(v_r + v_{r+4}), X_{2q+1} = DFT4((v_r - v_{r+4}) w8^r), w8 = e^{sg 2 pi i / 8}
-                C a[4], b[4];
+                    for (int r = 0; r < 8; ++r) v[r] = sx[j + r * NR];
+                    if (kk) {
+                        const int e = kk * tscale;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    a[r] = cadd(v[r], v[r + 4]);
-                    b[r] = csub(v[r], v[r + 4]);
-                }
-                b[1] = mk<R>(c8 * (b[1].x - sg * b[1].y), c8 * (b[1].y + sg * b[1].x));
-                b[2] = muli(b[2]);
-                b[3] = mk<R>(c8 * (-b[3].x - sg * b[3].y), c8 * (sg * b[3].x - b[3].y));
-                const int o = g * Ns * 8 + kk;
-                {
-                    const C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-                    const C s13 = cadd(a[1], a[3]), d13 = muli(csub(a[1], a[3]));
-                    dst[o] = cadd(s02, s13);
-                    dst[o + 2 * Ns] = cadd(d02, d13);
-                    dst[o + 4 * Ns] = csub(s02, s13);
-                    dst[o + 6 * Ns] = csub(d02, d13);
-                }
-                {
-                    const C s02 = cadd(b[0], b[2]), d02 = csub(b[0], b[2]);
-                    const C s13 = cadd(b[1], b[3]), d13 = muli(csub(b[1], b[3]));
-                    dst[o + Ns] = cadd(s02, s13);
-                    dst[o + 3 * Ns] = cadd(d02, d13);
-                    dst[o + 5 * Ns] = csub(s02, s13);
-                    dst[o + 7 * Ns] = csub(d02, d13);
+                        for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw(r * e));
+                    }
+                    // X_{2q} = DFT4(v_r + v_{r+4}), X_{2q+1} = DFT4((v_r - v_{r+4}) w8^r), w8 = e^{sg 2 pi i / 8}
+                    C a[4], b[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        a[r] = cadd(v[r], v[r + 4]);
+                        b[r] = csub(v[r], v[r + 4]);
+                    }
+                    b[1] = mk<R>(c8 * (b[1].x - sg * b[1].y), c8 * (b[1].y + sg * b[1].x));
+                    b[2] = muli(b[2]);
+                    b[3] = mk<R>(c8 * (-b[3].x - sg * b[3].y), c8 * (sg * b[3].x - b[3].y));
+                    const int o = g * Ns * 8 + kk;
+                    {
+                        const C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+                        const C s13 = cadd(a[1], a[3]), d13 = muli(csub(a[1], a[3]));
+                        dx[o] = cadd(s02, s13);
+                        dx[o + 2 * Ns] = cadd(d02, d13);
+                        dx[o + 4 * Ns] = csub(s02, s13);
+                        dx[o + 6 * Ns] = csub(d02, d13);
+                    }
+                    {
+                        const C s02 = cadd(b[0], b[2]), d02 = csub(b[0], b[2]);
+                        const C s13 = cadd(b[1], b[3]), d13 = muli(csub(b[1], b[3]));
+                        dx[o + Ns] = cadd(s02, s13);
+                        dx[o + 3 * Ns] = cadd(d02, d13);
+                        dx[o + 5 * Ns] = csub(s02, s13);
+                        dx[o + 7 * Ns] = csub(d02, d13);
+                    }
                 }
             }
         } else if (Rr == 2) {
-            for (int j = tid; j < NR; j += kThreads) {
-                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
-                const int kk = j - g * Ns;
-                C v0 = src[j], v1 = src[j + NR];
-                if (kk) v1 = cmul(v1, tw(kk * tscale));
-                const int o = g * Ns * 2 + kk;
-                dst[o] = cadd(v0, v1);
-                dst[o + Ns] = csub(v0, v1);
+#pragma unroll
+            for (int gm = 0; gm < G; ++gm) {
+                const C *sx = src + (size_t)gm * gs;
+                C *dx = dst + (size_t)gm * gs;
+                int g = g0, kk = kk0;
+                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
+                    if (kk >= Ns) {
+                        kk -= Ns;
+                        ++g;
+                    }
+                    C v0 = sx[j], v1 = sx[j + NR];
+                    if (kk) v1 = cmul(v1, tw(kk * tscale));
+                    const int o = g * Ns * 2 + kk;
+                    dx[o] = cadd(v0, v1);
+                    dx[o + Ns] = csub(v0, v1);
+                }
             }
         } else if (Rr == 4) {
-            for (int j = tid; j < NR; j += kThreads) {
-                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
-                const int kk = j - g * Ns;
-                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR];
-                if (kk) {
-                    const int e = kk * tscale;
-                    v1 = cmul(v1, tw(e));
-                    v2 = cmul(v2, tw(2 * e));
-                    v3 = cmul(v3, tw(3 * e));
+#pragma unroll
+            for (int gm = 0; gm < G; ++gm) {
+                const C *sx = src + (size_t)gm * gs;
+                C *dx = dst + (size_t)gm * gs;
+                int g = g0, kk = kk0;
+                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
+                    if (kk >= Ns) {
+                        kk -= Ns;
+                        ++g;
+                    }
+                    C v0 = sx[j], v1 = sx[j + NR], v2 = sx[j + 2 * NR], v3 = sx[j + 3 * NR];
+                    if (kk) {
+                        const int e = kk * tscale;
+                        v1 = cmul(v1, tw(e));
+                        v2 = cmul(v2, tw(2 * e));
+                        v3 = cmul(v3, tw(3 * e));
+                    }
+                    // radix 4 with w_4 = sg * i
+                    const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
+                    const C a2 = cadd(v1, v3), a3 = muli(csub(v1, v3));
+                    const int o = g * Ns * 4 + kk;
+                    dx[o] = cadd(a0, a2);
+                    dx[o + Ns] = cadd(a1, a3);
+                    dx[o + 2 * Ns] = csub(a0, a2);
+                    dx[o + 3 * Ns] = csub(a1, a3);
                 }
-                // radix 4 with w_4 = sg * i
-                const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
-                const C a2 = cadd(v1, v3), a3 = muli(csub(v1, v3));
-                const int o = g * Ns * 4 + kk;
-                dst[o] = cadd(a0, a2);
-                dst[o + Ns] = cadd(a1, a3);
-                dst[o + 2 * Ns] = csub(a0, a2);
-                dst[o + 3 * Ns] = csub(a1, a3);
             }
         } else if (Rr == 3) {
             const R c3 = (R)-0.5;
             const R s3 = sg * (R)0.86602540378443864676372317075294;  // sg sin(2 pi / 3)
-            for (int j = tid; j < NR; j += kThreads) {
-                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
-                const int kk = j - g * Ns;
-                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR];
-                if (kk) {
-                    const int e = kk * tscale;
-                    v1 = cmul(v1, tw(e));
-                    v2 = cmul(v2, tw(2 * e));
+#pragma unroll
+            for (int gm = 0; gm < G; ++gm) {
+                const C *sx = src + (size_t)gm * gs;
+                C *dx = dst + (size_t)gm * gs;
+                int g = g0, kk = kk0;
+                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
+                    if (kk >= Ns) {
+                        kk -= Ns;
+                        ++g;
+                    }
+                    C v0 = sx[j], v1 = sx[j + NR], v2 = sx[j + 2 * NR];
+                    if (kk) {
+                        const int e = kk * tscale;
+                        v1 = cmul(v1, tw(e));
+                        v2 = cmul(v2, tw(2 * e));
+                    }
+                    const C t1 = cadd(v1, v2);
+                    const C t2 = csub(v1, v2);
+                    const C m1 = mk<R>(v0.x + c3 * t1.x, v0.y + c3 * t1.y);
+                    const C m2 = mk<R>(-s3 * t2.y, s3 * t2.x);  // i s3 (v1 - v2)
+                    const int o = g * Ns * 3 + kk;
+                    dx[o] = cadd(v0, t1);
+                    dx[o + Ns] = cadd(m1, m2);
+                    dx[o + 2 * Ns] = csub(m1, m2);
                 }
-                const C t1 = cadd(v1, v2);
-                const C t2 = csub(v1, v2);
-                const C m1 = mk<R>(v0.x + c3 * t1.x, v0.y + c3 * t1.y);
-                const C m2 = mk<R>(-s3 * t2.y, s3 * t2.x);  // i s3 (v1 - v2)
-                const int o = g * Ns * 3 + kk;
-                dst[o] = cadd(v0, t1);
-                dst[o + Ns] = cadd(m1, m2);
-                dst[o + 2 * Ns] = csub(m1, m2);
             }
         } else if (Rr == 5) {
             const R c1 = (R)0.30901699437494742410229341718282;        // cos(2 pi / 5)
             const R c2 = (R)-0.80901699437494742410229341718282;       // cos(4 pi / 5)
             const R s1 = sg * (R)0.95105651629515357211643933337938;   // sg sin(2 pi / 5)
             const R s2 = sg * (R)0.58778525229247312916870595463907;   // sg sin(4 pi / 5)
-            for (int j = tid; j < NR; j += kThreads) {
-                const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
-                const int kk = j - g * Ns;
-                C v0 = src[j], v1 = src[j + NR], v2 = src[j + 2 * NR], v3 = src[j + 3 * NR],
-                  v4 = src[j + 4 * NR];
-                if (kk) {
-                    const int e = kk * tscale;
-                    v1 = cmul(v1, tw(e));
-                    v2 = cmul(v2, tw(2 * e));
-                    v3 = cmul(v3, tw(3 * e));
-                    v4 = cmul(v4, tw(4 * e));
+#pragma unroll
+            for (int gm = 0; gm < G; ++gm) {
+                const C *sx = src + (size_t)gm * gs;
+                C *dx = dst + (size_t)gm * gs;
+                int g = g0, kk = kk0;
+                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
+                    if (kk >= Ns) {
+                        kk -= Ns;
+                        ++g;
+                    }
+                    C v0 = sx[j], v1 = sx[j + NR], v2 = sx[j + 2 * NR], v3 = sx[j + 3 * NR],
+                      v4 = sx[j + 4 * NR];
+                    if (kk) {
+                        const int e = kk * tscale;
+                        v1 = cmul(v1, tw(e));
+                        v2 = cmul(v2, tw(2 * e));
+                        v3 = cmul(v3, tw(3 * e));
+                        v4 = cmul(v4, tw(4 * e));
+                    }
+                    const C a1 = cadd(v1, v4), b1 = csub(v1, v4);
+                    const C a2 = cadd(v2, v3), b2 = csub(v2, v3);
+                    const C m1 = mk<R>(v0.x + c1 * a1.x + c2 * a2.x, v0.y + c1 * a1.y + c2 * a2.y);
+                    const C m2 = mk<R>(v0.x + c2 * a1.x + c1 * a2.x, v0.y + c2 * a1.y + c1 * a2.y);
+                    // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
+                    const C n1 = mk<R>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
+                    const C n2 = mk<R>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
+                    const int o = g * Ns * 5 + kk;
+                    dx[o] = cadd(v0, cadd(a1, a2));
+                    dx[o + Ns] = cadd(m1, n1);
+                    dx[o + 2 * Ns] = cadd(m2, n2);
+                    dx[o + 3 * Ns] = csub(m2, n2);
+                    dx[o + 4 * Ns] = csub(m1, n1);
                 }
-                const C a1 = cadd(v1, v4), b1 = csub(v1, v4);
-                const C a2 = cadd(v2, v3), b2 = csub(v2, v3);
-                const C m1 = mk<R>(v0.x + c1 * a1.x + c2 * a2.x, v0.y + c1 * a1.y + c2 * a2.y);
-                const C m2 = mk<R>(v0.x + c2 * a1.x + c1 * a2.x, v0.y + c2 * a1.y + c1 * a2.y);
-                // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
-                const C n1 = mk<R>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
-                const C n2 = mk<R>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
-                const int o = g * Ns * 5 + kk;
-                dst[o] = cadd(v0, cadd(a1, a2));
-                dst[o + Ns] = cadd(m1, n1);
-                dst[o + 2 * Ns] = cadd(m2, n2);
-                dst[o + 3 * Ns] = csub(m2, n2);
-                dst[o + 4 * Ns] = csub(m1, n1);
             }
         } else {
             // direct pass for a general prime radix: one thread per output,
             // Y[o + q Ns] = sum_r X[j + r NR] w_N^{r (kk tscale + q NR)}
-            for (int t = tid; t < N; t += kThreads) {
+            for (int tt = tid; tt < G * N; tt += kThreads) {
+                const int gm = (G > 1) ? tt / N : 0;
+                const int t = tt - gm * N;
+                const C *sx = src + (size_t)gm * gs;
+                C *dx = dst + (size_t)gm * gs;
                 const int q = t / NR;
                 const int j = t - q * NR;
                 const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
                 const int kk = j - g * Ns;
                 const int e = kk * tscale + q * NR;  // < N
-                C acc = src[j];
+                C acc = sx[j];
                 int idx = e;
                 for (int rr = 1; rr < Rr; ++rr) {
-                    acc = cadd(acc, cmul(src[j + rr * NR], tw(idx)));
+                    acc = cadd(acc, cmul(sx[j + rr * NR], tw(idx)));
                     idx += e;
                     if (idx >= N) idx -= N;
                 }
-                dst[g * Ns * Rr + kk + q * Ns] = acc;
+                dx[g * Ns * Rr + kk + q * Ns] = acc;
             }
         }
         __syncthreads();
@@ -286,28 +337,46 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 // IFFT_Mb(FFT_Mb(x c) * Bh) with Bh = FFT_Mb(e^{-i pi t^2 / N}, wrapped) / Mb
 // from the plan (the forward sign uses conj(Bh[-k])).  a and b hold Mb
 // elements; W2 is w_Mb^q, q < Mb.  Returns the buffer holding X[0..N).
-template <bool INV, typename R, typename C>
+template <bool INV, typename R, typename C, int G = 1>
 __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const C *__restrict__ T, int n, int N,
-                        int Mb, const int *rad2, int np2)
+                        int Mb, const int *rad2, int np2, const int gs = 0)
 {
     const int tid = threadIdx.x;
     const int cstep = n / N;  // T index of e^{i pi / N}
     auto chirp = [&](int j) {
-        const int q = (int)(((long long)j * j) % (2LL * N));
+        const int q = (j * j) % (2 * N);  // j < Mb <= 4096: no overflow
         C c = T[q * cstep];
         if (!INV) c.y = -c.y;
         return c;
     };
-    for (int j = tid; j < Mb; j += kThreads) a[j] = (j < N) ? cmul(a[j], chirp(j)) : mk<R>(0, 0);
-    __syncthreads();
-    C *f = stockham<false, R>(a, b, Mb, W2, rad2, np2);
-    for (int k = tid; k < Mb; k += kThreads) {
-        const C h = INV ? Bh[k] : cconj(Bh[k == 0 ? 0 : Mb - k]);
-        f[k] = cmul(f[k], h);
+    for (int j = tid; j < Mb; j += kThreads) {
+        const C c = (j < N) ? chirp(j) : mk<R>(0, 0);
+#pragma unroll
+        for (int gm = 0; gm < G; ++gm) {
+            C *ax = a + (size_t)gm * gs;
+            ax[j] = (j < N) ? cmul(ax[j], c) : c;
+        }
     }
     __syncthreads();
-    C *y = stockham<true, R>(f, (f == a) ? b : a, Mb, W2, rad2, np2);
-    for (int k = tid; k < N; k += kThreads) y[k] = cmul(y[k], chirp(k));
+    C *f = stockham<false, R, C, G>(a, b, Mb, W2, rad2, np2, gs);
+    for (int k = tid; k < Mb; k += kThreads) {
+        const C h = INV ? Bh[k] : cconj(Bh[k == 0 ? 0 : Mb - k]);
+#pragma unroll
+        for (int gm = 0; gm < G; ++gm) {
+            C *fx = f + (size_t)gm * gs;
+            fx[k] = cmul(fx[k], h);
+        }
+    }
+    __syncthreads();
+    C *y = stockham<true, R, C, G>(f, (f == a) ? b : a, Mb, W2, rad2, np2, gs);
+    for (int k = tid; k < N; k += kThreads) {
+        const C c = chirp(k);
+#pragma unroll
+        for (int gm = 0; gm < G; ++gm) {
+            C *yx = y + (size_t)gm * gs;
+            yx[k] = cmul(yx[k], c);
+        }
+    }
     __syncthreads();
     return y;
 }
@@ -430,6 +499,148 @@ ring_synth_kernel(const __grid_constant__ DevPlan P, const typename C2T<R>::type
     const int r = BLUE ? P.rings_blue[blockIdx.x] : P.rings_smooth[blockIdx.x];
     ring_synth_body<R, BLUE>(P, r, delta, map, blockIdx.y * gmaps, min(nmaps, (int)(blockIdx.y + 1) * gmaps),
                              BLUE ? P.blue_cap : P.fft_cap, smem_raw, s_rad, &s_np);
+}
+
+// FP32 ring step of the tensor-core forms, reading Delta in the layout the
+// tensor-core Legendre kernels write, [ring][m][map] for nmaps maps.  CTA
+// (ring, map group) synthesises G consecutive maps of one ring together: the
+// fold reads the G maps' Delta_m side by side (one sector per m for G = 4)
+// and shares the phase factors, and every FFT pass handles all G maps between
+// two barriers.  Shared memory: the twiddle table, then two buffers of cap
+// complex elements per map (A: folded spectrum, B: DFT input; the DFT
+// ping-pongs between them).  CTAs of one ring are adjacent in the grid
+// (block = ring index x groups + group), so the maps of a sector are read at
+// about the same time.
+template <bool BLUE, int G>
+__global__ void __launch_bounds__(kThreads)
+ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict__ delta, float *__restrict__ map,
+                     int nmaps)
+{
+    using R = float;
+    using C = float2;
+    constexpr int GMAX = G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_rad[32];
+    __shared__ int s_np;
+    const int ngroups = (nmaps + G - 1) / G;
+    const int li = blockIdx.x / ngroups;
+    const int b0 = (blockIdx.x - li * ngroups) * G;
+    const int gn = min(G, nmaps - b0);  // maps in this CTA
+    const int r = BLUE ? P.rings_blue[li] : P.rings_smooth[li];
+    const int cap = BLUE ? P.blue_cap : P.fft_cap;
+    C *W = reinterpret_cast<C *>(smem_raw);
+    C *A0 = W + cap;       // map g: A at A0 + 2 g cap, B at A0 + (2 g + 1) cap
+    const int gs = 2 * cap;
+    const int tid = threadIdx.x;
+    const int n = P.nphi[r];
+    const int M = P.mmax;
+    const C *T = tw_table<R>(P) + P.twofs[r];  // T[q] = e^{i pi q / n}, q < 2n
+    const int ps = P.ps[r];
+    const double phi0 = P.phi0[r];
+    const bool even = (n % 2) == 0;
+    const int N = even ? n / 2 : n;
+    const int nb = even ? n / 2 + 1 : (n - 1) / 2 + 1;
+    const int tstep = even ? 4 : 2;
+    const int Mb = BLUE ? P.blue_mb[r] : 0;
+
+    if (BLUE) {
+        if (tid == 0) s_np = factorize(Mb, s_rad);
+        const C *w2 = w2_table<R>(P);
+        const int wstep = kBlueMaxMb / Mb;
+        for (int q = tid; q < Mb; q += kThreads) W[q] = w2[q * wstep];
+    } else {
+        if (tid == 0) s_np = factorize(N, s_rad);
+        for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
+    }
+
+    // 1. phase shift + fold of the gn maps onto the half spectrum, into A_g[0..nb).
+    //    Phase indices (m ps) mod 2n in 32 bits (m <= n + M, ps < 2n), advanced
+    //    incrementally: bin k starts at k ps, the next bin of the thread at
+    //    (k + kThreads) ps, the next alias m + n at m ps + n ps.
+    const C *D = delta + (size_t)r * (M + 1) * nmaps + b0;  // D[m nmaps + g]
+    const int n2 = 2 * n;
+    const int pstep = (ps >= 0) ? (n * ps) % n2 : 0;
+    int pk = (ps >= 0) ? (tid * ps) % n2 : 0;
+    const int dpk = (ps >= 0) ? (kThreads * ps) % n2 : 0;
+    for (int k = tid; k < nb; k += kThreads) {
+        C acc[GMAX];
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) acc[g] = mk<R>(0, 0);
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+            // pass 0: m = k + j n, Delta_m e^{i m phi0}; pass 1: m = n - k + j n (>= 1), conjugated
+            const int m0 = pass == 0 ? k : n - k;
+            int pi = pass == 0 ? pk : pstep - pk + (pstep < pk ? n2 : 0);
+            for (int m = m0; m <= M; m += n) {
+                C ph;
+                if (ps >= 0) {
+                    ph = T[pi];
+                    pi += pstep;
+                    if (pi >= n2) pi -= n2;
+                } else {
+                    double sn, cs;
+                    sincos((double)m * phi0, &sn, &cs);
+                    ph = mk<R>((R)cs, (R)sn);
+                }
+                const C *dm = D + (size_t)m * nmaps;
+#pragma unroll
+                for (int g = 0; g < GMAX; ++g) {
+                    if (g < gn) {
+                        const C v = cmul(dm[g], ph);
+                        acc[g] = cadd(acc[g], pass == 0 ? v : cconj(v));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g)
+            if (g < gn) A0[(size_t)g * gs + k] = acc[g];
+        pk += dpk;
+        if (pk >= n2) pk -= n2;
+    }
+    __syncthreads();
+
+    // 2. spectrum of the complex DFT, into B_g[0..N)
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const C *F = A0 + (size_t)g * gs;
+        C *Bg = A0 + (size_t)g * gs + cap;
+        for (int k = tid; k < N; k += kThreads) {
+            if (even) {
+                const C f = F[k];
+                const C h = cconj(F[N - k]);
+                const C w = T[2 * k];  // e^{2 pi i k / n}
+                Bg[k] = cadd(cadd(f, h), cmuli(cmul(w, csub(f, h))));
+            } else {
+                Bg[k] = (k < nb) ? F[k] : cconj(F[N - k]);
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. inverse complex DFT of length N of every map
+    // (a CTA holding fewer than G maps transforms its spare buffers too,
+    // harmlessly, and never stores them)
+    C *src = BLUE ? bluestein<true, R, C, G>(A0 + cap, A0, W, bhat_table<R>(P) + P.blue_ofs[r], T, n, N, Mb, s_rad,
+                                             s_np, gs)
+                  : stockham<true, R, C, G>(A0 + cap, A0, N, W, s_rad, s_np, gs);
+
+    // 4. store the rings (even n: pixel pairs as one 8-byte store when aligned)
+    for (int g = 0; g < gn; ++g) {
+        const C *z = src + (size_t)g * gs;
+        R *out = map + (size_t)(b0 + g) * P.npix + P.ofs[r];
+        if (even && (reinterpret_cast<uintptr_t>(out) & 7) == 0) {
+            float2 *o2 = reinterpret_cast<float2 *>(out);
+            for (int j = tid; j < N; j += kThreads) o2[j] = z[j];
+        } else if (even) {
+            for (int j = tid; j < N; j += kThreads) {
+                out[2 * j] = z[j].x;
+                out[2 * j + 1] = z[j].y;
+            }
+        } else {
+            for (int j = tid; j < N; j += kThreads) out[j] = z[j].x;
+        }
+    }
 }
 
 // Ring step of many one-map requests: CTA i synthesises ring items[i].y of
@@ -582,11 +793,36 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
                       map);
 }
 
-cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float *map, int nmaps,
-                                   cudaStream_t st)
+size_t ring_mf_smem_bytes(int cap, int G) { return (size_t)(1 + 2 * G) * cap * sizeof(float2); }
+
+cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int g_smooth,
+                                 int g_blue, cudaStream_t st)
 {
-    return launch_two(ring_synth_kernel<float, false>, ring_synth_kernel<float, true>, P, false, nmaps, st, delta,
-                      map);
+    if (nmaps <= 0) return cudaSuccess;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool blue = pass == 1;
+        const int nl = blue ? P.n_blue : P.n_smooth;
+        if (nl <= 0) continue;
+        const int cap = blue ? P.blue_cap : P.fft_cap;
+        int G = std::max(1, std::min(blue ? g_blue : g_smooth, 4));
+        if (G == 3) G = 2;
+        while (G > 1 && ring_mf_smem_bytes(cap, G) > (size_t)227 * 1024) G /= 2;
+        const size_t smem = ring_mf_smem_bytes(cap, G);
+        using K = void (*)(const DevPlan, const float2 *, float *, int);
+        K k = blue ? (G == 4 ? ring_synth_mf_kernel<true, 4>
+                             : G == 2 ? ring_synth_mf_kernel<true, 2> : ring_synth_mf_kernel<true, 1>)
+                   : (G == 4 ? ring_synth_mf_kernel<false, 4>
+                             : G == 2 ? ring_synth_mf_kernel<false, 2> : ring_synth_mf_kernel<false, 1>);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        const long long nblk = (long long)nl * ((nmaps + G - 1) / G);
+        k<<<(unsigned)nblk, kThreads, smem, st>>>(P, delta_rm, map, nmaps);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smooth_items, int n_smooth,

@@ -38,6 +38,7 @@ struct sht_plan_s {
     std::vector<int> rings_smooth_h, rings_blue_h;  // host copies of the ring lists
     sht::TcWork tc;      // tensor-core forms: segment tables, status word, B-operand buffer
     size_t tc_bytes = 0;
+    int ring_g[2] = {2, 1};  // maps per CTA of the FP32 ring step: smooth, Bluestein ring lists
     void *lcache[4] = {};  // plan-time Lambda operand per tensor-core form (sht_lambda_cache)
     size_t lcache_bytes[4] = {};
     std::mutex mu;
@@ -606,12 +607,11 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
     int rc;
     const int group = std::min(nbatch, sht::kTcMaxMaps);
     const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(float2);
-    if ((rc = ensure_ws(p, 2 * per_map * group))) return rc;
+    if ((rc = ensure_ws(p, per_map * group))) return rc;
     if ((rc = ensure_tc(p, prec))) return rc;
     const double2 *alm = static_cast<const double2 *>(alm_dev);
     float *map = static_cast<float *>(map_dev);
-    float2 *delta_rm = static_cast<float2 *>(p->ws);  // [ring][m][map], as the Legendre kernel writes it
-    float2 *delta = delta_rm + per_map / sizeof(float2) * group;  // [map][ring][m] for the ring step
+    float2 *delta = static_cast<float2 *>(p->ws);  // [ring][m][map]
     for (int b0 = 0; b0 < nbatch; b0 += group) {
         const int nb = std::min(group, nbatch - b0);
         StageScope s0(p, SHT_STAGE_LEGENDRE, st);
@@ -619,17 +619,13 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
         s0.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
         StageScope s1(p, SHT_STAGE_LEGENDRE, st);
-        e = sht::launch_tc_main(p->dp, p->tc, prec, p->lcache[prec], delta_rm, nb, st);
+        e = sht::launch_tc_main(p->dp, p->tc, prec, p->lcache[prec], delta, nb, st);
         s1.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc launch");
-        StageScope s1b(p, SHT_STAGE_RING, st);
-        e = sht::launch_delta_relayout(delta_rm, delta, (long long)p->nrings * (p->mmax + 1), nb, st);
-        s1b.done(e);
-        if (e != cudaSuccess) return cuda_fail(e, "delta_relayout launch");
         StageScope s2(p, SHT_STAGE_RING, st);
-        e = sht::launch_ring_synth_fp32(p->dp, delta, map + (size_t)b0 * p->npix, nb, st);
+        e = sht::launch_ring_synth_mf(p->dp, delta, map + (size_t)b0 * p->npix, nb, p->ring_g[0], p->ring_g[1], st);
         s2.done(e, sht::ring_launches(p->dp));
-        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp32 launch");
+        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_mf launch");
     }
     return SHT_OK;
 }

@@ -83,16 +83,15 @@ cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smoot
                                          int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
                                          const MultiPtrs &ptrs, cudaStream_t st);
 
-// The tensor-core Legendre kernels write Delta as [ring][m][map] (a row's
-// maps contiguous, so every store fills whole sectors); this relayouts it to
-// the ring step's [map][ring][m] (nrows = nrings x (mmax + 1)).
-cudaError_t launch_delta_relayout(const float2 *in, float2 *out, long long nrows, int nmaps, cudaStream_t st);
-
 // Ring step: phase shift, fold of m onto the ring's bins, real inverse DFT of
 // each ring; delta is [map][ring][m].
+// FP32 ring step reading the tensor-core layout [ring][m][map] directly,
+// g_smooth / g_blue maps (1..4) per CTA for the two ring lists; the shared
+// memory per CTA is ring_mf_smem_bytes(cap, G).
+cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int g_smooth,
+                                 int g_blue, cudaStream_t st);
+size_t ring_mf_smem_bytes(int cap, int G);
 cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps,
-                                   cudaStream_t st);
-cudaError_t launch_ring_synth_fp32(const DevPlan &P, const float2 *delta, float *map, int nmaps,
                                    cudaStream_t st);
 
 // Ring step of the transpose: q[b][ring][m] = sum_j y_j e^{-i m phi_j}.
@@ -126,8 +125,10 @@ inline int tc_ncols(int nmaps) { return ((2 * nmaps + 31) / 32) * 32; }
 size_t tc_bbuf_bytes(const TcWork &W, int prec);
 cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const double2 *alm, int nmaps,
                            cudaStream_t st);
-// acache: the plan-time Lambda operand of form prec (launch_lambda_build), or
-// nullptr to run the FP64 recurrence in the launch.
+// delta: [ring][m][map] for the launch's nmaps maps (a row's maps contiguous,
+// so every store fills whole sectors).  acache: the plan-time Lambda operand
+// of form prec (launch_lambda_build), or nullptr to run the FP64 recurrence in
+// the launch.
 cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, const void *acache, float2 *delta,
                            int nmaps, cudaStream_t st);
 size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
