@@ -657,8 +657,9 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
 template <bool BF16, int NPA, int NPB>
 struct StreamCfg {
     using C = Cfg<BF16, NPA, NPB>;
-    static constexpr int NS = (200 * 1024) / C::STAGE_BYTES;  // 4 (48 KB stages) or 6 (32 KB)
-    static constexpr int SMEM = NS * C::STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
+    static constexpr int STG_BYTES = 8 * 32 * 16 * 8;  // per drain warp: 32 rows x 16 float2
+    static constexpr int NS = (227 * 1024 - 1024 - 256 - STG_BYTES) / C::STAGE_BYTES;  // 4 (48 KB) or 6 (32 KB)
+    static constexpr int SMEM = NS * C::STAGE_BYTES + STG_BYTES + 1024 /* align */ + 256 /* barriers */;
 };
 
 template <bool BF16, int NPA, int NPB>
@@ -675,7 +676,8 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
     const uint32_t base_u32 = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (base_u32 & 1023u)) & 1023u;
     unsigned char *stage0 = smem_raw + pad;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + NS * C::STAGE_BYTES);
+    float2 *stage_d = reinterpret_cast<float2 *>(stage0 + NS * C::STAGE_BYTES);  // Delta staging, 8 x 4 KB
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + NS * C::STAGE_BYTES + StreamCfg<BF16, NPA, NPB>::STG_BYTES);
     // bars: full[NS], empty[NS], set_full[2], set_empty[2], mma_drain
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
@@ -759,26 +761,50 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
                 ++gg;
             }
             if (!ok) break;
-            // Delta_m(north) = E + O, Delta_m(south) = E - O for this row's
-            // maps; Delta is [ring][m][map]: 16 contiguous maps per chunk
-            if (pair < P.npairs) {
-                const int2 rr = P.pair_ring[pair];
-                const int M1 = P.mmax + 1;
-                float2 *dn = delta + ((size_t)rr.x * M1 + m) * nmaps;
-                float2 *ds = delta + ((size_t)max(rr.y, 0) * M1 + m) * nmaps;
+            // Delta_m(north) = E + O, Delta_m(south) = E - O for the warp's 32
+            // rows and its maps; Delta is [ring][m][map].  Each block of 16
+            // maps of a row (128 contiguous bytes) goes through the warp's
+            // staging buffer (row = lane, element c at c ^ (lane & 15): no bank
+            // conflicts) and out as 16-byte stores, four rows per instruction.
+            int2 rr = make_int2(-1, -1);
+            if (pair < P.npairs) rr = P.pair_ring[pair];
+            const int M1 = P.mmax + 1;
+            const bool vec = (nmaps & 1) == 0;
+            float2 *stg = stage_d + warp * (32 * 16);
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int q = 2 * j + half;
+            for (int j = 0; j < 2; ++j) {
+                const int q = 2 * j + half;  // columns 32 q .. 32 q + 31 = maps 16 q .. 16 q + 15
+                if (32 * q >= ncols) continue;
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
-                        const int b = 16 * q + c;  // columns 2 b, 2 b + 1 of chunk q
-                        if (32 * q < ncols && b < nmaps) {
-                            const float er = te[j][2 * c], ei = te[j][2 * c + 1];
-                            const float orr = to[j][2 * c], oi = to[j][2 * c + 1];
-                            dn[b] = make_float2(er + orr, (m == 0) ? 0.f : ei + oi);
-                            if (rr.y >= 0) ds[b] = make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
+                        const float er = te[j][2 * c], ei = te[j][2 * c + 1];
+                        const float orr = to[j][2 * c], oi = to[j][2 * c + 1];
+                        stg[lane * 16 + (c ^ (lane & 15))] =
+                            side == 0 ? make_float2(er + orr, (m == 0) ? 0.f : ei + oi)
+                                      : make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
+                    }
+                    __syncwarp();
+                    const int sg = lane & 7;
+                    const int b = 16 * q + 2 * sg;
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int rw = it * 4 + (lane >> 3);
+                        const int ring = __shfl_sync(0xffffffffu, side == 0 ? rr.x : rr.y, rw);
+                        const float2 v0 = stg[rw * 16 + ((2 * sg) ^ (rw & 15))];
+                        const float2 v1 = stg[rw * 16 + ((2 * sg + 1) ^ (rw & 15))];
+                        if (ring >= 0) {
+                            float2 *d = delta + ((size_t)ring * M1 + m) * nmaps + b;
+                            if (vec && b + 1 < nmaps) {
+                                *reinterpret_cast<float4 *>(d) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                            } else {
+                                if (b < nmaps) d[0] = v0;
+                                if (b + 1 < nmaps) d[1] = v1;
+                            }
                         }
                     }
+                    __syncwarp();
                 }
             }
         }
