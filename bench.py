@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--lambda-cache", action="store_true",
                     help="tensor-core forms: build the plan-time Lambda operand before timing")
     ap.add_argument("--workload", choices=["batch", "requests"], default="batch",
@@ -233,6 +234,10 @@ def run_ours(args):
     out = torch.empty((B, plan.npix), dtype=sht.MAP_DTYPE[args.prec], device=dev)
     stream = torch.cuda.current_stream()
 
+    tiles = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tiles = dict(plan.autotune(args.prec, B), seconds=time.perf_counter() - t0)
     lcache = None
     if args.lambda_cache and args.prec != "fp64":
         torch.cuda.synchronize()
@@ -278,6 +283,8 @@ def run_ours(args):
     fp64_path = None
     if args.prec != "fp64" and args.fp64_steps > 0:
         out64 = torch.empty((B, plan.npix), dtype=torch.float64, device=dev)
+        if not args.no_autotune:
+            plan.autotune("fp64", B)
         plan.alm2map(alm, "fp64", out=out64)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -406,7 +413,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": dict(workload(args), parallelism="replicas x%d" % world, precision=args.prec,
                            lambda_cache=lcache is not None),
-            "lambda_cache": lcache,
+            "lambda_cache": lcache, "tiles": tiles,
             "roofline": roof,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
             "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy,

@@ -138,6 +138,34 @@ int sht_lambda_cache(sht_plan_t plan, int prec, int enable, void *stream);
  * or a form without one. */
 long long sht_lambda_cache_bytes(sht_plan_t plan, int prec);
 
+/* Autotuner: pick this plan's tile shapes for form prec and batches of
+ * nbatch maps by timing every candidate on the plan's own grid (synthetic
+ * zero input in the plan's workspace, CUDA events on `stream`, one untimed
+ * launch each), and keep the fastest.  Tunes, for the tensor-core forms, the
+ * FP32 ring step's maps per CTA for the smooth and Bluestein ring lists
+ * ({1, 2, 4} x {1, 2}) and threads per CTA ({256, 512}); for SHT_FP64, the
+ * Legendre step's maps per CTA ({1, 2, 4, 8}, timed on up to 8 maps) and the
+ * ring step's maps per CTA ({2, 4, 8, 16}).  The transforms' results do not
+ * depend on the tile shapes (every product and fused multiply-add is
+ * explicitly rounded), only their speed.  Blocks until done (well under a
+ * second for the ring candidates; the FP64 Legendre candidates take about
+ * 4 x the time of an 8-map FP64 Legendre launch).  Allocates and frees a
+ * temporary map buffer (and, for SHT_FP64, a coefficient buffer) and may grow
+ * the plan's workspace.  Not to be called during stream capture.  Errors:
+ * SHT_EINVAL (no plan, unknown prec, nbatch < 1), SHT_ENOMEM, SHT_ECUDA. */
+int sht_autotune(sht_plan_t plan, int prec, int nbatch, void *stream);
+
+/* Current tile shapes of the plan: out[0..min(n, 5)) = {FP32 ring maps per
+ * CTA (smooth list), (Bluestein list), FP32 ring threads per CTA, FP64
+ * Legendre maps per CTA, FP64 ring maps per CTA}.  Errors: SHT_EINVAL. */
+int sht_tiles(sht_plan_t plan, int *out, int n);
+
+/* Set the first n (0..5) tile shapes, in the order of sht_tiles (e.g. ones an
+ * earlier sht_autotune picked and the caller saved).  Each value must be one
+ * of the autotuner's candidates ({1, 2, 4}, {1, 2}, {256, 512}, {1, 2, 4, 8},
+ * {1, 2, 4, 8, 16}), else SHT_EINVAL and nothing changes. */
+int sht_set_tiles(sht_plan_t plan, const int *vals, int n);
+
 /* FP64 alm2map that allocates nothing (the paper has no counterpart: this is
  * an interface for callers that must not allocate device memory once their
  * processing loop runs, e.g. a host framework that has reserved nearly all

@@ -205,12 +205,14 @@ cudaError_t launch_legendre_multi_fp64(const DevPlan *plans, const int4 *items, 
 }
 
 cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, double2 *delta,
-                                     int nmaps, cudaStream_t st)
+                                     int nmaps, int bc, cudaStream_t st)
 {
     if (nmaps <= 0) return cudaSuccess;
-    if (nmaps >= 8) return launch_bc<8>(P, alm, delta, nmaps, st);
-    if (nmaps >= 4) return launch_bc<4>(P, alm, delta, nmaps, st);
-    if (nmaps >= 2) return launch_bc<2>(P, alm, delta, nmaps, st);
+    if (bc <= 0) bc = 8;  // default: 8 maps per CTA
+    while (bc > 1 && bc > nmaps) bc /= 2;
+    if (bc >= 8) return launch_bc<8>(P, alm, delta, nmaps, st);
+    if (bc >= 4) return launch_bc<4>(P, alm, delta, nmaps, st);
+    if (bc >= 2) return launch_bc<2>(P, alm, delta, nmaps, st);
     return launch_bc<1>(P, alm, delta, nmaps, st);
 }
 

@@ -89,10 +89,10 @@ extern "C" int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         // The Legendre step writes every (ring, m) entry of the scratch that
         // the ring step reads, so nothing has to be cleared between calls.
-        e = sht::launch_legendre_fwd_fp64(P, static_cast<const double2 *>(alm_dev), scratch, nbatch, st);
+        e = sht::launch_legendre_fwd_fp64(P, static_cast<const double2 *>(alm_dev), scratch, nbatch, 0, st);
         if (e == cudaSuccess) {
             sht::count_launch();
-            e = sht::launch_ring_synth_fp64(P, scratch, static_cast<double *>(map_dev), nbatch, st);
+            e = sht::launch_ring_synth_fp64(P, scratch, static_cast<double *>(map_dev), nbatch, 0, st);
             if (e == cudaSuccess)
                 for (int i = 0; i < sht::ring_launches(P); ++i) sht::count_launch();
         }

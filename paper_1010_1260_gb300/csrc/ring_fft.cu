@@ -39,11 +39,19 @@ __device__ __forceinline__ typename C2T<R>::type mk(R x, R y)
     c.y = y;
     return c;
 }
+// Products and fused multiply-adds with explicit rounding: the compiler may
+// not contract them differently in different instantiations, so results do
+// not depend on the launch shape (maps per CTA, threads per CTA).
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename C> __device__ __forceinline__ C cmul(C a, C b)
 {
     C c;
-    c.x = a.x * b.x - a.y * b.y;
-    c.y = a.x * b.y + a.y * b.x;
+    c.x = rfma(a.x, b.x, -rmul(a.y, b.y));
+    c.y = rfma(a.x, b.y, rmul(a.y, b.x));
     return c;
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b)
@@ -104,13 +112,16 @@ __device__ int factorize(int N, int *rad)
 // shared-memory table w_N^q = e^{2 pi i q / N}, q < N (conjugated for the
 // forward sign).  Pass with radix R and sub-transform size Ns:
 //   Y[(j/Ns) Ns R + j%Ns + q Ns] = sum_r X[j + r N/R] w_{Ns R}^{r (j%Ns)} w_R^{r q}.
-template <bool INV, typename R, typename C, int G = 1>
-__device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, const int npass, const int gs = 0)
+// WG: W is a global table read through the read-only cache with element
+// stride wst (w_N^q = W[q wst]) instead of a shared-memory table.
+template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads>
+__device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, const int npass, const int gs = 0,
+                      const int wst = 1)
 {
     const int tid = threadIdx.x;
     const R sg = INV ? (R)1 : (R)-1;
     auto tw = [&](int q) {
-        C w = W[q];
+        C w = WG ? __ldg(W + q * wst) : W[q];
         if (!INV) w.y = -w.y;
         return w;
     };
@@ -129,134 +140,159 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
         // j / Ns: a shift while Ns is a power of two (all earlier radices 8, 4, 2)
         const bool ns_pow2 = (Ns & (Ns - 1)) == 0;
         const int ns_sh = __ffs(Ns) - 1;
-        // (g, kk) = (j / Ns, j % Ns) for j = tid, advanced by (dq, dr) per kThreads
+        // (g, kk) = (j / Ns, j % Ns) for j = tid, advanced by (dq, dr) per NT
         const int g0 = ns_pow2 ? (tid >> ns_sh) : tid / Ns;
         const int kk0 = tid - g0 * Ns;
-        const int dq = ns_pow2 ? (kThreads >> ns_sh) : kThreads / Ns;
-        const int dr = kThreads - dq * Ns;
-        // r kk tscale < R Ns N / (Ns R) = N: twiddle indices need no reduction
+        const int dq = ns_pow2 ? (NT >> ns_sh) : NT / Ns;
+        const int dr = NT - dq * Ns;
+        // Each butterfly loads the inputs of all G maps first and loads its
+        // twiddles once for all of them; r kk tscale < R Ns N / (Ns R) = N,
+        // so twiddle indices need no reduction.
         if (Rr == 8) {
             const R c8 = (R)0.70710678118654752440084436210485;  // 1/sqrt(2)
+            int g = g0, kk = kk0;
+            for (int j = tid; j < NR; j += NT, kk += dr, g += dq) {
+                if (kk >= Ns) {
+                    kk -= Ns;
+                    ++g;
+                }
+                C v[G][8], w[8];
 #pragma unroll
-            for (int gm = 0; gm < G; ++gm) {
-                const C *sx = src + (size_t)gm * gs;
-                C *dx = dst + (size_t)gm * gs;
-                int g = g0, kk = kk0;
-                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
-                    if (kk >= Ns) {
-                        kk -= Ns;
-                        ++g;
-                    }
-                    C v[8];
+                for (int gm = 0; gm < G; ++gm)
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) v[r] = sx[j + r * NR];
+                    for (int r = 0; r < 8; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+#pragma unroll
+                    for (int r = 1; r < 8; ++r) w[r] = tw(r * e);
+                }
+                const int o = g * Ns * 8 + kk;
+#pragma unroll
+                for (int gm = 0; gm < G; ++gm) {
                     if (kk) {
-                        const int e = kk * tscale;
 #pragma unroll
-                        for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw(r * e));
+                        for (int r = 1; r < 8; ++r) v[gm][r] = cmul(v[gm][r], w[r]);
                     }
                     // X_{2q} = DFT4(v_r + v_{r+4}), X_{2q+1} = DFT4((v_r - v_{r+4}) w8^r), w8 = e^{sg 2 pi i / 8}
                     C a[4], b[4];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        a[r] = cadd(v[r], v[r + 4]);
-                        b[r] = csub(v[r], v[r + 4]);
+                        a[r] = cadd(v[gm][r], v[gm][r + 4]);
+                        b[r] = csub(v[gm][r], v[gm][r + 4]);
                     }
-                    b[1] = mk<R>(c8 * (b[1].x - sg * b[1].y), c8 * (b[1].y + sg * b[1].x));
+                    b[1] = mk<R>(rmul(c8, b[1].x - sg * b[1].y), rmul(c8, b[1].y + sg * b[1].x));
                     b[2] = muli(b[2]);
-                    b[3] = mk<R>(c8 * (-b[3].x - sg * b[3].y), c8 * (sg * b[3].x - b[3].y));
-                    const int o = g * Ns * 8 + kk;
+                    b[3] = mk<R>(rmul(c8, -b[3].x - sg * b[3].y), rmul(c8, sg * b[3].x - b[3].y));
+                    C *d = dst + gm * gs + o;
                     {
                         const C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
                         const C s13 = cadd(a[1], a[3]), d13 = muli(csub(a[1], a[3]));
-                        dx[o] = cadd(s02, s13);
-                        dx[o + 2 * Ns] = cadd(d02, d13);
-                        dx[o + 4 * Ns] = csub(s02, s13);
-                        dx[o + 6 * Ns] = csub(d02, d13);
+                        d[0] = cadd(s02, s13);
+                        d[2 * Ns] = cadd(d02, d13);
+                        d[4 * Ns] = csub(s02, s13);
+                        d[6 * Ns] = csub(d02, d13);
                     }
                     {
                         const C s02 = cadd(b[0], b[2]), d02 = csub(b[0], b[2]);
                         const C s13 = cadd(b[1], b[3]), d13 = muli(csub(b[1], b[3]));
-                        dx[o + Ns] = cadd(s02, s13);
-                        dx[o + 3 * Ns] = cadd(d02, d13);
-                        dx[o + 5 * Ns] = csub(s02, s13);
-                        dx[o + 7 * Ns] = csub(d02, d13);
+                        d[Ns] = cadd(s02, s13);
+                        d[3 * Ns] = cadd(d02, d13);
+                        d[5 * Ns] = csub(s02, s13);
+                        d[7 * Ns] = csub(d02, d13);
                     }
                 }
             }
         } else if (Rr == 2) {
+            int g = g0, kk = kk0;
+            for (int j = tid; j < NR; j += NT, kk += dr, g += dq) {
+                if (kk >= Ns) {
+                    kk -= Ns;
+                    ++g;
+                }
+                C v[G][2];
 #pragma unroll
-            for (int gm = 0; gm < G; ++gm) {
-                const C *sx = src + (size_t)gm * gs;
-                C *dx = dst + (size_t)gm * gs;
-                int g = g0, kk = kk0;
-                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
-                    if (kk >= Ns) {
-                        kk -= Ns;
-                        ++g;
-                    }
-                    C v0 = sx[j], v1 = sx[j + NR];
-                    if (kk) v1 = cmul(v1, tw(kk * tscale));
-                    const int o = g * Ns * 2 + kk;
-                    dx[o] = cadd(v0, v1);
-                    dx[o + Ns] = csub(v0, v1);
+                for (int gm = 0; gm < G; ++gm) {
+                    v[gm][0] = src[gm * gs + j];
+                    v[gm][1] = src[gm * gs + j + NR];
+                }
+                const C w1 = kk ? tw(kk * tscale) : mk<R>(1, 0);
+                const int o = g * Ns * 2 + kk;
+#pragma unroll
+                for (int gm = 0; gm < G; ++gm) {
+                    const C v1 = kk ? cmul(v[gm][1], w1) : v[gm][1];
+                    C *d = dst + gm * gs + o;
+                    d[0] = cadd(v[gm][0], v1);
+                    d[Ns] = csub(v[gm][0], v1);
                 }
             }
         } else if (Rr == 4) {
+            int g = g0, kk = kk0;
+            for (int j = tid; j < NR; j += NT, kk += dr, g += dq) {
+                if (kk >= Ns) {
+                    kk -= Ns;
+                    ++g;
+                }
+                C v[G][4], w[4];
 #pragma unroll
-            for (int gm = 0; gm < G; ++gm) {
-                const C *sx = src + (size_t)gm * gs;
-                C *dx = dst + (size_t)gm * gs;
-                int g = g0, kk = kk0;
-                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
-                    if (kk >= Ns) {
-                        kk -= Ns;
-                        ++g;
-                    }
-                    C v0 = sx[j], v1 = sx[j + NR], v2 = sx[j + 2 * NR], v3 = sx[j + 3 * NR];
+                for (int gm = 0; gm < G; ++gm)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+#pragma unroll
+                    for (int r = 1; r < 4; ++r) w[r] = tw(r * e);
+                }
+                const int o = g * Ns * 4 + kk;
+#pragma unroll
+                for (int gm = 0; gm < G; ++gm) {
                     if (kk) {
-                        const int e = kk * tscale;
-                        v1 = cmul(v1, tw(e));
-                        v2 = cmul(v2, tw(2 * e));
-                        v3 = cmul(v3, tw(3 * e));
+#pragma unroll
+                        for (int r = 1; r < 4; ++r) v[gm][r] = cmul(v[gm][r], w[r]);
                     }
                     // radix 4 with w_4 = sg * i
-                    const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
-                    const C a2 = cadd(v1, v3), a3 = muli(csub(v1, v3));
-                    const int o = g * Ns * 4 + kk;
-                    dx[o] = cadd(a0, a2);
-                    dx[o + Ns] = cadd(a1, a3);
-                    dx[o + 2 * Ns] = csub(a0, a2);
-                    dx[o + 3 * Ns] = csub(a1, a3);
+                    const C a0 = cadd(v[gm][0], v[gm][2]), a1 = csub(v[gm][0], v[gm][2]);
+                    const C a2 = cadd(v[gm][1], v[gm][3]), a3 = muli(csub(v[gm][1], v[gm][3]));
+                    C *d = dst + gm * gs + o;
+                    d[0] = cadd(a0, a2);
+                    d[Ns] = cadd(a1, a3);
+                    d[2 * Ns] = csub(a0, a2);
+                    d[3 * Ns] = csub(a1, a3);
                 }
             }
         } else if (Rr == 3) {
             const R c3 = (R)-0.5;
             const R s3 = sg * (R)0.86602540378443864676372317075294;  // sg sin(2 pi / 3)
+            int g = g0, kk = kk0;
+            for (int j = tid; j < NR; j += NT, kk += dr, g += dq) {
+                if (kk >= Ns) {
+                    kk -= Ns;
+                    ++g;
+                }
+                C v[G][3], w[3];
 #pragma unroll
-            for (int gm = 0; gm < G; ++gm) {
-                const C *sx = src + (size_t)gm * gs;
-                C *dx = dst + (size_t)gm * gs;
-                int g = g0, kk = kk0;
-                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
-                    if (kk >= Ns) {
-                        kk -= Ns;
-                        ++g;
-                    }
-                    C v0 = sx[j], v1 = sx[j + NR], v2 = sx[j + 2 * NR];
+                for (int gm = 0; gm < G; ++gm)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+                    w[1] = tw(e);
+                    w[2] = tw(2 * e);
+                }
+                const int o = g * Ns * 3 + kk;
+#pragma unroll
+                for (int gm = 0; gm < G; ++gm) {
                     if (kk) {
-                        const int e = kk * tscale;
-                        v1 = cmul(v1, tw(e));
-                        v2 = cmul(v2, tw(2 * e));
+                        v[gm][1] = cmul(v[gm][1], w[1]);
+                        v[gm][2] = cmul(v[gm][2], w[2]);
                     }
-                    const C t1 = cadd(v1, v2);
-                    const C t2 = csub(v1, v2);
-                    const C m1 = mk<R>(v0.x + c3 * t1.x, v0.y + c3 * t1.y);
-                    const C m2 = mk<R>(-s3 * t2.y, s3 * t2.x);  // i s3 (v1 - v2)
-                    const int o = g * Ns * 3 + kk;
-                    dx[o] = cadd(v0, t1);
-                    dx[o + Ns] = cadd(m1, m2);
-                    dx[o + 2 * Ns] = csub(m1, m2);
+                    const C t1 = cadd(v[gm][1], v[gm][2]);
+                    const C t2 = csub(v[gm][1], v[gm][2]);
+                    const C m1 = mk<R>(rfma(c3, t1.x, v[gm][0].x), rfma(c3, t1.y, v[gm][0].y));
+                    const C m2 = mk<R>(-rmul(s3, t2.y), rmul(s3, t2.x));  // i s3 (v1 - v2)
+                    C *d = dst + gm * gs + o;
+                    d[0] = cadd(v[gm][0], t1);
+                    d[Ns] = cadd(m1, m2);
+                    d[2 * Ns] = csub(m1, m2);
                 }
             }
         } else if (Rr == 5) {
@@ -264,61 +300,66 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
             const R c2 = (R)-0.80901699437494742410229341718282;       // cos(4 pi / 5)
             const R s1 = sg * (R)0.95105651629515357211643933337938;   // sg sin(2 pi / 5)
             const R s2 = sg * (R)0.58778525229247312916870595463907;   // sg sin(4 pi / 5)
+            int g = g0, kk = kk0;
+            for (int j = tid; j < NR; j += NT, kk += dr, g += dq) {
+                if (kk >= Ns) {
+                    kk -= Ns;
+                    ++g;
+                }
+                C v[G][5], w[5];
 #pragma unroll
-            for (int gm = 0; gm < G; ++gm) {
-                const C *sx = src + (size_t)gm * gs;
-                C *dx = dst + (size_t)gm * gs;
-                int g = g0, kk = kk0;
-                for (int j = tid; j < NR; j += kThreads, kk += dr, g += dq) {
-                    if (kk >= Ns) {
-                        kk -= Ns;
-                        ++g;
-                    }
-                    C v0 = sx[j], v1 = sx[j + NR], v2 = sx[j + 2 * NR], v3 = sx[j + 3 * NR],
-                      v4 = sx[j + 4 * NR];
+                for (int gm = 0; gm < G; ++gm)
+#pragma unroll
+                    for (int r = 0; r < 5; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                if (kk) {
+                    const int e = kk * tscale;
+#pragma unroll
+                    for (int r = 1; r < 5; ++r) w[r] = tw(r * e);
+                }
+                const int o = g * Ns * 5 + kk;
+#pragma unroll
+                for (int gm = 0; gm < G; ++gm) {
                     if (kk) {
-                        const int e = kk * tscale;
-                        v1 = cmul(v1, tw(e));
-                        v2 = cmul(v2, tw(2 * e));
-                        v3 = cmul(v3, tw(3 * e));
-                        v4 = cmul(v4, tw(4 * e));
+#pragma unroll
+                        for (int r = 1; r < 5; ++r) v[gm][r] = cmul(v[gm][r], w[r]);
                     }
-                    const C a1 = cadd(v1, v4), b1 = csub(v1, v4);
-                    const C a2 = cadd(v2, v3), b2 = csub(v2, v3);
-                    const C m1 = mk<R>(v0.x + c1 * a1.x + c2 * a2.x, v0.y + c1 * a1.y + c2 * a2.y);
-                    const C m2 = mk<R>(v0.x + c2 * a1.x + c1 * a2.x, v0.y + c2 * a1.y + c1 * a2.y);
+                    const C a1 = cadd(v[gm][1], v[gm][4]), b1 = csub(v[gm][1], v[gm][4]);
+                    const C a2 = cadd(v[gm][2], v[gm][3]), b2 = csub(v[gm][2], v[gm][3]);
+                    const C v0 = v[gm][0];
+                    const C m1 = mk<R>(rfma(c2, a2.x, rfma(c1, a1.x, v0.x)), rfma(c2, a2.y, rfma(c1, a1.y, v0.y)));
+                    const C m2 = mk<R>(rfma(c1, a2.x, rfma(c2, a1.x, v0.x)), rfma(c1, a2.y, rfma(c2, a1.y, v0.y)));
                     // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
-                    const C n1 = mk<R>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
-                    const C n2 = mk<R>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
-                    const int o = g * Ns * 5 + kk;
-                    dx[o] = cadd(v0, cadd(a1, a2));
-                    dx[o + Ns] = cadd(m1, n1);
-                    dx[o + 2 * Ns] = cadd(m2, n2);
-                    dx[o + 3 * Ns] = csub(m2, n2);
-                    dx[o + 4 * Ns] = csub(m1, n1);
+                    const C n1 = mk<R>(-rfma(s1, b1.y, rmul(s2, b2.y)), rfma(s1, b1.x, rmul(s2, b2.x)));
+                    const C n2 = mk<R>(-rfma(s2, b1.y, -rmul(s1, b2.y)), rfma(s2, b1.x, -rmul(s1, b2.x)));
+                    C *d = dst + gm * gs + o;
+                    d[0] = cadd(v0, cadd(a1, a2));
+                    d[Ns] = cadd(m1, n1);
+                    d[2 * Ns] = cadd(m2, n2);
+                    d[3 * Ns] = csub(m2, n2);
+                    d[4 * Ns] = csub(m1, n1);
                 }
             }
         } else {
             // direct pass for a general prime radix: one thread per output,
             // Y[o + q Ns] = sum_r X[j + r NR] w_N^{r (kk tscale + q NR)}
-            for (int tt = tid; tt < G * N; tt += kThreads) {
-                const int gm = (G > 1) ? tt / N : 0;
-                const int t = tt - gm * N;
-                const C *sx = src + (size_t)gm * gs;
-                C *dx = dst + (size_t)gm * gs;
+            for (int t = tid; t < N; t += NT) {
                 const int q = t / NR;
                 const int j = t - q * NR;
                 const int g = ns_pow2 ? (j >> ns_sh) : j / Ns;
                 const int kk = j - g * Ns;
                 const int e = kk * tscale + q * NR;  // < N
-                C acc = sx[j];
-                int idx = e;
-                for (int rr = 1; rr < Rr; ++rr) {
-                    acc = cadd(acc, cmul(sx[j + rr * NR], tw(idx)));
-                    idx += e;
-                    if (idx >= N) idx -= N;
+#pragma unroll
+                for (int gm = 0; gm < G; ++gm) {
+                    const C *sx = src + gm * gs;
+                    C acc = sx[j];
+                    int idx = e;
+                    for (int rr = 1; rr < Rr; ++rr) {
+                        acc = cadd(acc, cmul(sx[j + rr * NR], tw(idx)));
+                        idx += e;
+                        if (idx >= N) idx -= N;
+                    }
+                    dst[gm * gs + g * Ns * Rr + kk + q * Ns] = acc;
                 }
-                dx[g * Ns * Rr + kk + q * Ns] = acc;
             }
         }
         __syncthreads();
@@ -337,9 +378,9 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 // IFFT_Mb(FFT_Mb(x c) * Bh) with Bh = FFT_Mb(e^{-i pi t^2 / N}, wrapped) / Mb
 // from the plan (the forward sign uses conj(Bh[-k])).  a and b hold Mb
 // elements; W2 is w_Mb^q, q < Mb.  Returns the buffer holding X[0..N).
-template <bool INV, typename R, typename C, int G = 1>
+template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads>
 __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const C *__restrict__ T, int n, int N,
-                        int Mb, const int *rad2, int np2, const int gs = 0)
+                        int Mb, const int *rad2, int np2, const int gs = 0, const int wst = 1)
 {
     const int tid = threadIdx.x;
     const int cstep = n / N;  // T index of e^{i pi / N}
@@ -349,7 +390,7 @@ __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const
         if (!INV) c.y = -c.y;
         return c;
     };
-    for (int j = tid; j < Mb; j += kThreads) {
+    for (int j = tid; j < Mb; j += NT) {
         const C c = (j < N) ? chirp(j) : mk<R>(0, 0);
 #pragma unroll
         for (int gm = 0; gm < G; ++gm) {
@@ -358,8 +399,8 @@ __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const
         }
     }
     __syncthreads();
-    C *f = stockham<false, R, C, G>(a, b, Mb, W2, rad2, np2, gs);
-    for (int k = tid; k < Mb; k += kThreads) {
+    C *f = stockham<false, R, C, G, WG, NT>(a, b, Mb, W2, rad2, np2, gs, wst);
+    for (int k = tid; k < Mb; k += NT) {
         const C h = INV ? Bh[k] : cconj(Bh[k == 0 ? 0 : Mb - k]);
 #pragma unroll
         for (int gm = 0; gm < G; ++gm) {
@@ -368,8 +409,8 @@ __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const
         }
     }
     __syncthreads();
-    C *y = stockham<true, R, C, G>(f, (f == a) ? b : a, Mb, W2, rad2, np2, gs);
-    for (int k = tid; k < N; k += kThreads) {
+    C *y = stockham<true, R, C, G, WG, NT>(f, (f == a) ? b : a, Mb, W2, rad2, np2, gs, wst);
+    for (int k = tid; k < N; k += NT) {
         const C c = chirp(k);
 #pragma unroll
         for (int gm = 0; gm < G; ++gm) {
@@ -506,19 +547,22 @@ ring_synth_kernel(const __grid_constant__ DevPlan P, const typename C2T<R>::type
 // (ring, map group) synthesises G consecutive maps of one ring together: the
 // fold reads the G maps' Delta_m side by side (one sector per m for G = 4)
 // and shares the phase factors, and every FFT pass handles all G maps between
-// two barriers.  Shared memory: the twiddle table, then two buffers of cap
-// complex elements per map (A: folded spectrum, B: DFT input; the DFT
-// ping-pongs between them).  CTAs of one ring are adjacent in the grid
+// two barriers.  Shared memory: two regions of G buffers of cap complex
+// elements (A: folded spectra, B: DFT inputs; the DFT ping-pongs between
+// them).  The ring's Delta block (M + 1 orders x G maps) is first copied into
+// region B with all loads in flight, so that the fold reads shared memory
+// instead of paying a global-memory latency per bin (when M + 1 > cap the
+// fold reads global memory directly).  CTAs of one ring are adjacent in the grid
 // (block = ring index x groups + group), so the maps of a sector are read at
-// about the same time.
-template <bool BLUE, int G>
-__global__ void __launch_bounds__(kThreads)
+// about the same time.  The twiddles come from the plan's global tables
+// through the read-only cache, which leaves shared memory to the buffers.
+template <bool BLUE, int G, int NT>
+__global__ void __launch_bounds__(NT)
 ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict__ delta, float *__restrict__ map,
                      int nmaps)
 {
     using R = float;
     using C = float2;
-    constexpr int GMAX = G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_rad[32];
     __shared__ int s_np;
@@ -528,9 +572,9 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
     const int gn = min(G, nmaps - b0);  // maps in this CTA
     const int r = BLUE ? P.rings_blue[li] : P.rings_smooth[li];
     const int cap = BLUE ? P.blue_cap : P.fft_cap;
-    C *W = reinterpret_cast<C *>(smem_raw);
-    C *A0 = W + cap;       // map g: A at A0 + 2 g cap, B at A0 + (2 g + 1) cap
-    const int gs = 2 * cap;
+    C *A0 = reinterpret_cast<C *>(smem_raw);  // map g: A at A0 + g cap, B at A0 + (G + g) cap
+    C *B0 = A0 + G * cap;
+    const int gs = cap;
     const int tid = threadIdx.x;
     const int n = P.nphi[r];
     const int M = P.mmax;
@@ -543,69 +587,101 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
     const int tstep = even ? 4 : 2;
     const int Mb = BLUE ? P.blue_mb[r] : 0;
 
-    if (BLUE) {
-        if (tid == 0) s_np = factorize(Mb, s_rad);
-        const C *w2 = w2_table<R>(P);
-        const int wstep = kBlueMaxMb / Mb;
-        for (int q = tid; q < Mb; q += kThreads) W[q] = w2[q * wstep];
-    } else {
-        if (tid == 0) s_np = factorize(N, s_rad);
-        for (int q = tid; q < N; q += kThreads) W[q] = T[q * tstep];
-    }
+    if (tid == 0) s_np = factorize(BLUE ? Mb : N, s_rad);
 
-    // 1. phase shift + fold of the gn maps onto the half spectrum, into A_g[0..nb).
-    //    Phase indices (m ps) mod 2n in 32 bits (m <= n + M, ps < 2n), advanced
-    //    incrementally: bin k starts at k ps, the next bin of the thread at
-    //    (k + kThreads) ps, the next alias m + n at m ps + n ps.
+    // 1. phase shift + fold of the gn maps onto the half spectrum, into A_g[0..nb):
+    //    F_k = sum_{m = k mod n} Delta_m e^{i m phi0} + sum_{m >= 1, -m = k mod n} conj(...)
     const C *D = delta + (size_t)r * (M + 1) * nmaps + b0;  // D[m nmaps + g]
+    const bool staged = M + 1 <= cap;
     const int n2 = 2 * n;
-    const int pstep = (ps >= 0) ? (n * ps) % n2 : 0;
-    int pk = (ps >= 0) ? (tid * ps) % n2 : 0;
-    const int dpk = (ps >= 0) ? (kThreads * ps) % n2 : 0;
-    for (int k = tid; k < nb; k += kThreads) {
-        C acc[GMAX];
+    if (staged) {
+        // phase-shifted Delta_m e^{i m phi0} of map g at B0[m G + g]; (m ps) mod 2n
+        // in 32 bits (m <= M, ps < 2n)
+#pragma unroll 4
+        for (int m = tid; m <= M; m += NT) {
+            C ph;
+            if (ps >= 0) {
+                ph = T[(m * ps) % n2];
+            } else {
+                double sn, cs;
+                sincos((double)m * phi0, &sn, &cs);
+                ph = mk<R>((R)cs, (R)sn);
+            }
 #pragma unroll
-        for (int g = 0; g < GMAX; ++g) acc[g] = mk<R>(0, 0);
+            for (int g = 0; g < G; ++g)
+                B0[m * G + g] = (g < gn) ? cmul(D[(size_t)m * nmaps + g], ph) : mk<R>(0, 0);
+        }
+        __syncthreads();
+        for (int k = tid; k < nb; k += NT) {
+            C acc[G];
 #pragma unroll
-        for (int pass = 0; pass < 2; ++pass) {
-            // pass 0: m = k + j n, Delta_m e^{i m phi0}; pass 1: m = n - k + j n (>= 1), conjugated
-            const int m0 = pass == 0 ? k : n - k;
-            int pi = pass == 0 ? pk : pstep - pk + (pstep < pk ? n2 : 0);
-            for (int m = m0; m <= M; m += n) {
-                C ph;
-                if (ps >= 0) {
-                    ph = T[pi];
-                    pi += pstep;
-                    if (pi >= n2) pi -= n2;
-                } else {
-                    double sn, cs;
-                    sincos((double)m * phi0, &sn, &cs);
-                    ph = mk<R>((R)cs, (R)sn);
-                }
-                const C *dm = D + (size_t)m * nmaps;
+            for (int g = 0; g < G; ++g) acc[g] = mk<R>(0, 0);
+            // m = k + j n, then m = n - k + j n (m >= 1) conjugated
+            for (int m = k; m <= M; m += n) {
 #pragma unroll
-                for (int g = 0; g < GMAX; ++g) {
-                    if (g < gn) {
-                        const C v = cmul(dm[g], ph);
-                        acc[g] = cadd(acc[g], pass == 0 ? v : cconj(v));
+                for (int g = 0; g < G; ++g) acc[g] = cadd(acc[g], B0[m * G + g]);
+            }
+            for (int m = n - k; m <= M; m += n) {
+                if (m < 1) continue;
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc[g] = cadd(acc[g], cconj(B0[m * G + g]));
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (g < gn) A0[g * cap + k] = acc[g];
+        }
+    } else {
+        // Delta too long to stage: phases from the table, Delta from global memory.
+        // Phase indices advance incrementally: bin k starts at k ps, the next
+        // bin of the thread at (k + NT) ps, the next alias m + n at m ps + n ps.
+        const int pstep = (ps >= 0) ? (n * ps) % n2 : 0;
+        int pk = (ps >= 0) ? (tid * ps) % n2 : 0;
+        const int dpk = (ps >= 0) ? (NT * ps) % n2 : 0;
+        for (int k = tid; k < nb; k += NT) {
+            C acc[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[g] = mk<R>(0, 0);
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+                const int m0 = pass == 0 ? k : n - k;
+                int pi = pass == 0 ? pk : pstep - pk + (pstep < pk ? n2 : 0);
+                for (int m = m0; m <= M; m += n) {
+                    C ph;
+                    if (ps >= 0) {
+                        ph = T[pi];
+                        pi += pstep;
+                        if (pi >= n2) pi -= n2;
+                    } else {
+                        double sn, cs;
+                        sincos((double)m * phi0, &sn, &cs);
+                        ph = mk<R>((R)cs, (R)sn);
+                    }
+                    if (pass == 1 && m < 1) continue;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        if (g < gn) {
+                            const C v = cmul(D[(size_t)m * nmaps + g], ph);
+                            acc[g] = cadd(acc[g], pass == 0 ? v : cconj(v));
+                        }
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int g = 0; g < GMAX; ++g)
-            if (g < gn) A0[(size_t)g * gs + k] = acc[g];
-        pk += dpk;
-        if (pk >= n2) pk -= n2;
+            for (int g = 0; g < G; ++g)
+                if (g < gn) A0[g * cap + k] = acc[g];
+            pk += dpk;
+            if (pk >= n2) pk -= n2;
+        }
     }
     __syncthreads();
 
     // 2. spectrum of the complex DFT, into B_g[0..N)
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const C *F = A0 + (size_t)g * gs;
-        C *Bg = A0 + (size_t)g * gs + cap;
-        for (int k = tid; k < N; k += kThreads) {
+        const C *F = A0 + g * cap;
+        C *Bg = B0 + g * cap;
+#pragma unroll 4
+        for (int k = tid; k < N; k += NT) {
             if (even) {
                 const C f = F[k];
                 const C h = cconj(F[N - k]);
@@ -621,24 +697,25 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
     // 3. inverse complex DFT of length N of every map
     // (a CTA holding fewer than G maps transforms its spare buffers too,
     // harmlessly, and never stores them)
-    C *src = BLUE ? bluestein<true, R, C, G>(A0 + cap, A0, W, bhat_table<R>(P) + P.blue_ofs[r], T, n, N, Mb, s_rad,
-                                             s_np, gs)
-                  : stockham<true, R, C, G>(A0 + cap, A0, N, W, s_rad, s_np, gs);
+    C *src = BLUE ? bluestein<true, R, C, G, true, NT>(B0, A0, w2_table<R>(P), bhat_table<R>(P) + P.blue_ofs[r], T, n,
+                                                       N, Mb, s_rad, s_np, gs, Mb > 0 ? kBlueMaxMb / Mb : 1)
+                  : stockham<true, R, C, G, true, NT>(B0, A0, N, T, s_rad, s_np, gs, tstep);
 
     // 4. store the rings (even n: pixel pairs as one 8-byte store when aligned)
     for (int g = 0; g < gn; ++g) {
-        const C *z = src + (size_t)g * gs;
+        const C *z = src + g * gs;
         R *out = map + (size_t)(b0 + g) * P.npix + P.ofs[r];
         if (even && (reinterpret_cast<uintptr_t>(out) & 7) == 0) {
             float2 *o2 = reinterpret_cast<float2 *>(out);
-            for (int j = tid; j < N; j += kThreads) o2[j] = z[j];
+#pragma unroll 4
+            for (int j = tid; j < N; j += NT) o2[j] = z[j];
         } else if (even) {
-            for (int j = tid; j < N; j += kThreads) {
+            for (int j = tid; j < N; j += NT) {
                 out[2 * j] = z[j].x;
                 out[2 * j + 1] = z[j].y;
             }
         } else {
-            for (int j = tid; j < N; j += kThreads) out[j] = z[j].x;
+            for (int j = tid; j < N; j += NT) out[j] = z[j].x;
         }
     }
 }
@@ -751,10 +828,11 @@ ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
 // Launch one ring kernel over the smooth ring list and one over the
 // Bluestein ring list (each with its own shared-memory size).
 template <typename K, typename... Args>
-cudaError_t launch_two(K smooth, K blue, const DevPlan &P, bool fp64, int nmaps, cudaStream_t st, Args... args)
+cudaError_t launch_two(K smooth, K blue, const DevPlan &P, bool fp64, int nmaps, int group, cudaStream_t st,
+                       Args... args)
 {
     if (nmaps <= 0) return cudaSuccess;
-    const int g = ring_group(nmaps);
+    const int g = group > 0 ? std::min(group, nmaps) : ring_group(nmaps);
     const int gy = (nmaps + g - 1) / g;
     if (P.n_smooth > 0) {
         const size_t smem = ring_smem_bytes_for_cap(P.fft_cap, fp64);
@@ -786,17 +864,17 @@ size_t ring_smem_bytes(const DevPlan &P, bool fp64)
     return ring_smem_bytes_for_cap(P.fft_cap, fp64);
 }
 
-cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps,
+cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps, int group,
                                    cudaStream_t st)
 {
-    return launch_two(ring_synth_kernel<double, false>, ring_synth_kernel<double, true>, P, true, nmaps, st, delta,
-                      map);
+    return launch_two(ring_synth_kernel<double, false>, ring_synth_kernel<double, true>, P, true, nmaps, group, st,
+                      delta, map);
 }
 
-size_t ring_mf_smem_bytes(int cap, int G) { return (size_t)(1 + 2 * G) * cap * sizeof(float2); }
+size_t ring_mf_smem_bytes(int cap, int G) { return (size_t)2 * G * cap * sizeof(float2); }
 
 cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int g_smooth,
-                                 int g_blue, cudaStream_t st)
+                                 int g_blue, int nt, cudaStream_t st)
 {
     if (nmaps <= 0) return cudaSuccess;
     for (int pass = 0; pass < 2; ++pass) {
@@ -809,16 +887,19 @@ cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float
         while (G > 1 && ring_mf_smem_bytes(cap, G) > (size_t)227 * 1024) G /= 2;
         const size_t smem = ring_mf_smem_bytes(cap, G);
         using K = void (*)(const DevPlan, const float2 *, float *, int);
-        K k = blue ? (G == 4 ? ring_synth_mf_kernel<true, 4>
-                             : G == 2 ? ring_synth_mf_kernel<true, 2> : ring_synth_mf_kernel<true, 1>)
-                   : (G == 4 ? ring_synth_mf_kernel<false, 4>
-                             : G == 2 ? ring_synth_mf_kernel<false, 2> : ring_synth_mf_kernel<false, 1>);
+        const bool big = nt >= 512;
+        K k = blue ? (G == 4   ? (big ? ring_synth_mf_kernel<true, 4, 512> : ring_synth_mf_kernel<true, 4, 256>)
+                      : G == 2 ? (big ? ring_synth_mf_kernel<true, 2, 512> : ring_synth_mf_kernel<true, 2, 256>)
+                               : (big ? ring_synth_mf_kernel<true, 1, 512> : ring_synth_mf_kernel<true, 1, 256>))
+                   : (G == 4   ? (big ? ring_synth_mf_kernel<false, 4, 512> : ring_synth_mf_kernel<false, 4, 256>)
+                      : G == 2 ? (big ? ring_synth_mf_kernel<false, 2, 512> : ring_synth_mf_kernel<false, 2, 256>)
+                               : (big ? ring_synth_mf_kernel<false, 1, 512> : ring_synth_mf_kernel<false, 1, 256>));
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
         const long long nblk = (long long)nl * ((nmaps + G - 1) / G);
-        k<<<(unsigned)nblk, kThreads, smem, st>>>(P, delta_rm, map, nmaps);
+        k<<<(unsigned)nblk, big ? 512 : 256, smem, st>>>(P, delta_rm, map, nmaps);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -857,14 +938,14 @@ cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smoot
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
                                       cudaStream_t st)
 {
-    return launch_two(ring_analysis_kernel<double, false>, ring_analysis_kernel<double, true>, P, true, nmaps, st,
+    return launch_two(ring_analysis_kernel<double, false>, ring_analysis_kernel<double, true>, P, true, nmaps, 0, st,
                       map, q);
 }
 
 cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
                                       cudaStream_t st)
 {
-    return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, st,
+    return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, 0, st,
                       map, q);
 }
 

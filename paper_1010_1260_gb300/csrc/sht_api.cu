@@ -38,7 +38,11 @@ struct sht_plan_s {
     std::vector<int> rings_smooth_h, rings_blue_h;  // host copies of the ring lists
     sht::TcWork tc;      // tensor-core forms: segment tables, status word, B-operand buffer
     size_t tc_bytes = 0;
+    // tile shapes (sht_autotune): results do not depend on them
     int ring_g[2] = {2, 1};  // maps per CTA of the FP32 ring step: smooth, Bluestein ring lists
+    int ring_nt = 256;       // threads per CTA of the FP32 ring step
+    int fp64_bc = 8;         // maps per CTA of the FP64 Legendre step
+    int fp64_ring_g = 8;     // maps per CTA of the FP64 ring step
     void *lcache[4] = {};  // plan-time Lambda operand per tensor-core form (sht_lambda_cache)
     size_t lcache_bytes[4] = {};
     std::mutex mu;
@@ -623,7 +627,8 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
         s1.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc launch");
         StageScope s2(p, SHT_STAGE_RING, st);
-        e = sht::launch_ring_synth_mf(p->dp, delta, map + (size_t)b0 * p->npix, nb, p->ring_g[0], p->ring_g[1], st);
+        e = sht::launch_ring_synth_mf(p->dp, delta, map + (size_t)b0 * p->npix, nb, p->ring_g[0], p->ring_g[1],
+                                      p->ring_nt, st);
         s2.done(e, sht::ring_launches(p->dp));
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_mf launch");
     }
@@ -758,6 +763,164 @@ int sht_lambda_cache(sht_plan_t p, int prec, int enable, void *stream)
     return SHT_OK;
 }
 
+int sht_autotune(sht_plan_t p, int prec, int nbatch, void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
+        return fail(SHT_EINVAL, "unknown precision %d", prec);
+    if (nbatch < 1) return fail(SHT_EINVAL, "nbatch < 1");
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool tc = prec != SHT_FP64;
+    // the launch group the transforms use: up to 64 maps (tensor-core forms), up to 8 for the
+    // FP64 Legendre candidates (each runs the full recurrence and contraction)
+    const int nb = std::min(nbatch, tc ? sht::kTcMaxMaps : 64);
+    const size_t esz = tc ? sizeof(float2) : sizeof(double2);
+    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * esz;
+    if ((rc = ensure_ws(p, per_map * nb))) return rc;
+    void *map = nullptr, *alm = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (map) cudaFree(map);
+        if (alm) cudaFree(alm);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&map, (size_t)nb * p->npix * (tc ? sizeof(float) : sizeof(double)));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ws, 0, per_map * nb, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SHT_ENOMEM : SHT_ECUDA, "autotune set-up: %s",
+                    cudaGetErrorString(e));
+    }
+    // one untimed launch, then `reps` timed ones; +inf on a launch error
+    auto time_it = [&](auto launch, int reps) -> float {
+        if (launch() != cudaSuccess) {
+            cudaGetLastError();
+            return 3.4e38f;
+        }
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < reps; ++i)
+            if (launch() != cudaSuccess) {
+                cudaGetLastError();
+                return 3.4e38f;
+            }
+        cudaEventRecord(e1, st);
+        float ms = 3.4e38f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            return 3.4e38f;
+        }
+        return ms;
+    };
+    if (tc) {
+        // FP32 ring step: maps per CTA for the two ring lists x threads per CTA
+        const float2 *d = static_cast<const float2 *>(p->ws);
+        float best = 3.4e38f;
+        int bs = p->ring_g[0], bb = p->ring_g[1], bt = p->ring_nt;
+        for (int nt : {256, 512})
+            for (int gsm : {1, 2, 4})
+                for (int gbl : {1, 2}) {
+                    const float ms = time_it(
+                        [&]() {
+                            return sht::launch_ring_synth_mf(p->dp, d, static_cast<float *>(map), nb, gsm, gbl, nt,
+                                                             st);
+                        },
+                        2);
+                    if (ms < best) {
+                        best = ms;
+                        bs = gsm;
+                        bb = gbl;
+                        bt = nt;
+                    }
+                }
+        p->ring_g[0] = bs;
+        p->ring_g[1] = bb;
+        p->ring_nt = bt;
+    } else {
+        const int nl = std::min(nb, 8);
+        e = cudaMalloc(&alm, (size_t)nl * p->nalm * sizeof(double2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(alm, 0, (size_t)nl * p->nalm * sizeof(double2), st);
+        if (e != cudaSuccess) {
+            cleanup();
+            cudaGetLastError();
+            return fail(SHT_ENOMEM, "autotune set-up: %s", cudaGetErrorString(e));
+        }
+        float best = 3.4e38f;
+        int bbc = p->fp64_bc;
+        for (int bc : {1, 2, 4, 8}) {
+            if (bc > nl) break;
+            const float ms = time_it(
+                [&]() {
+                    return sht::launch_legendre_fwd_fp64(p->dp, static_cast<const double2 *>(alm),
+                                                         static_cast<double2 *>(p->ws), nl, bc, st);
+                },
+                1);
+            if (ms < best) {
+                best = ms;
+                bbc = bc;
+            }
+        }
+        p->fp64_bc = bbc;
+        best = 3.4e38f;
+        int bg = p->fp64_ring_g;
+        for (int g : {2, 4, 8, 16}) {
+            if (g > nb && g > 2) break;
+            const float ms = time_it(
+                [&]() {
+                    return sht::launch_ring_synth_fp64(p->dp, static_cast<const double2 *>(p->ws),
+                                                       static_cast<double *>(map), nb, g, st);
+                },
+                2);
+            if (ms < best) {
+                best = ms;
+                bg = g;
+            }
+        }
+        p->fp64_ring_g = bg;
+    }
+    cleanup();
+    return SHT_OK;
+}
+
+int sht_tiles(sht_plan_t p, int *out, int n)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!out || n < 0) return fail(SHT_EINVAL, "null output or n < 0");
+    const int v[5] = {p->ring_g[0], p->ring_g[1], p->ring_nt, p->fp64_bc, p->fp64_ring_g};
+    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
+    return SHT_OK;
+}
+
+int sht_set_tiles(sht_plan_t p, const int *vals, int n)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!vals || n < 0 || n > 5) return fail(SHT_EINVAL, "need 0 <= n <= 5 values");
+    auto in = [](int v, std::initializer_list<int> ok) {
+        for (int o : ok)
+            if (v == o) return true;
+        return false;
+    };
+    const bool valid = (n < 1 || in(vals[0], {1, 2, 4})) && (n < 2 || in(vals[1], {1, 2})) &&
+                       (n < 3 || in(vals[2], {256, 512})) && (n < 4 || in(vals[3], {1, 2, 4, 8})) &&
+                       (n < 5 || in(vals[4], {1, 2, 4, 8, 16}));
+    if (!valid) return fail(SHT_EINVAL, "tile shape outside the candidate set");
+    std::lock_guard<std::mutex> lk(p->mu);
+    int *dst[5] = {&p->ring_g[0], &p->ring_g[1], &p->ring_nt, &p->fp64_bc, &p->fp64_ring_g};
+    for (int i = 0; i < n; ++i) *dst[i] = vals[i];
+    return SHT_OK;
+}
+
 int sht_plan_destroy(sht_plan_t plan)
 {
     free_plan(plan);
@@ -796,11 +959,11 @@ int sht_alm2map_batch(sht_plan_t p, int nbatch, const void *alm_dev, void *map_d
     for (int b0 = 0; b0 < nbatch; b0 += chunk) {
         const int nb = std::min(chunk, nbatch - b0);
         StageScope s1(p, SHT_STAGE_LEGENDRE, st);
-        cudaError_t e = sht::launch_legendre_fwd_fp64(p->dp, alm + (size_t)b0 * p->nalm, delta, nb, st);
+        cudaError_t e = sht::launch_legendre_fwd_fp64(p->dp, alm + (size_t)b0 * p->nalm, delta, nb, p->fp64_bc, st);
         s1.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_fwd_fp64 launch");
         StageScope s2(p, SHT_STAGE_RING, st);
-        e = sht::launch_ring_synth_fp64(p->dp, delta, map + (size_t)b0 * p->npix, nb, st);
+        e = sht::launch_ring_synth_fp64(p->dp, delta, map + (size_t)b0 * p->npix, nb, p->fp64_ring_g, st);
         s2.done(e, sht::ring_launches(p->dp));
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp64 launch");
     }

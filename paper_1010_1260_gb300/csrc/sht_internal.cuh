@@ -69,9 +69,10 @@ struct MultiPtrs {
 };
 
 // Legendre step, FP64 (recurrence and contraction in FP64).
-//   delta[b][ring][m] (complex) = Delta_m(theta_ring) for maps b in [0, nmaps).
+//   delta[b][ring][m] (complex) = Delta_m(theta_ring) for maps b in [0, nmaps);
+//   bc = maps per CTA (1, 2, 4, 8; 0 = 8), a tile shape only: results do not depend on it.
 cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, double2 *delta,
-                                     int nmaps, cudaStream_t st);
+                                     int nmaps, int bc, cudaStream_t st);
 
 // Legendre step of many one-map requests in one persistent launch over the
 // work list items[] = (request, m, ring block, -); counter must be 0 at launch.
@@ -86,12 +87,14 @@ cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smoot
 // Ring step: phase shift, fold of m onto the ring's bins, real inverse DFT of
 // each ring; delta is [map][ring][m].
 // FP32 ring step reading the tensor-core layout [ring][m][map] directly,
-// g_smooth / g_blue maps (1..4) per CTA for the two ring lists; the shared
-// memory per CTA is ring_mf_smem_bytes(cap, G).
+// g_smooth / g_blue maps (1, 2 or 4) per CTA for the two ring lists, nt
+// (256 or 512) threads per CTA; the shared memory per CTA is
+// ring_mf_smem_bytes(cap, G).
 cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int g_smooth,
-                                 int g_blue, cudaStream_t st);
+                                 int g_blue, int nt, cudaStream_t st);
 size_t ring_mf_smem_bytes(int cap, int G);
-cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps,
+// group = maps per CTA (0 = 8), a tile shape only.
+cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps, int group,
                                    cudaStream_t st);
 
 // Ring step of the transpose: q[b][ring][m] = sum_j y_j e^{-i m phi_j}.

@@ -83,12 +83,16 @@ def lib():
             L.sht_lambda_cache.argtypes = [P, I, I, V]
             L.sht_lambda_cache_bytes.argtypes = [P, I]
             L.sht_lambda_cache_bytes.restype = ctypes.c_longlong
+            L.sht_autotune.argtypes = [P, I, I, V]
+            L.sht_tiles.argtypes = [P, ctypes.POINTER(I), I]
+            L.sht_set_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_kernel_launches.argtypes = []
             L.sht_kernel_launches.restype = ctypes.c_ulonglong
             for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
                       "sht_alm2map_batch", "sht_map2alm_adjoint_batch", "sht_profile",
                       "sht_profile_read", "sht_sync", "sht_multi_create", "sht_multi_alm2map",
-                      "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache"):
+                      "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
+                      "sht_tiles", "sht_set_tiles"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -222,6 +226,32 @@ class Plan:
         later alm2map calls of that form stream it instead of running the
         recurrence, with identical results."""
         check(lib().sht_lambda_cache(self._h, PREC[prec], 1 if enable else 0, _stream_ptr(stream)))
+
+    # ------------------------------------------------------- tile shapes --
+    TILE_NAMES = ("ring_maps_smooth", "ring_maps_bluestein", "ring_threads", "fp64_legendre_maps",
+                  "fp64_ring_maps")
+
+    def autotune(self, prec: str, nbatch: int, stream=None) -> dict:
+        """Time the tile-shape candidates for form ``prec`` and batches of
+        ``nbatch`` maps on this plan and keep the fastest; returns tiles()."""
+        check(lib().sht_autotune(self._h, PREC[prec], int(nbatch), _stream_ptr(stream)))
+        return self.tiles()
+
+    def tiles(self) -> dict:
+        """The plan's current tile shapes."""
+        out = (ctypes.c_int * 5)()
+        check(lib().sht_tiles(self._h, out, 5))
+        return dict(zip(self.TILE_NAMES, list(out)))
+
+    def set_tiles(self, **kw):
+        """Set tile shapes by name (see TILE_NAMES); unnamed ones keep their value."""
+        cur = self.tiles()
+        for k, v in kw.items():
+            if k not in cur:
+                raise KeyError(k)
+            cur[k] = int(v)
+        vals = (ctypes.c_int * 5)(*[cur[k] for k in self.TILE_NAMES])
+        check(lib().sht_set_tiles(self._h, vals, 5))
 
     def sync(self):
         """Wait for the plan's device; raise ShtError(SHT_ETIMEOUT) if a kernel
