@@ -90,6 +90,24 @@ template <typename R> __device__ __forceinline__ const typename C2T<R>::type *w2
 template <> __device__ __forceinline__ const double2 *w2_table<double>(const DevPlan &P) { return P.w2_64; }
 template <> __device__ __forceinline__ const float2 *w2_table<float>(const DevPlan &P) { return P.w2_32; }
 
+// 8-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 // Factor N into radices: 8s first, then 4, 2, 3, 5, then remaining primes.
 __device__ int factorize(int N, int *rad)
 {
@@ -378,27 +396,36 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 // IFFT_Mb(FFT_Mb(x c) * Bh) with Bh = FFT_Mb(e^{-i pi t^2 / N}, wrapped) / Mb
 // from the plan (the forward sign uses conj(Bh[-k])).  a and b hold Mb
 // elements; W2 is w_Mb^q, q < Mb.  Returns the buffer holding X[0..N).
-template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads>
+// The chirp c_j = e^{sg i pi j^2 / N} (sg = + for INV) from the ring's table
+// T[q] = e^{i pi q / n}: c_j = T[(j^2 mod 2N) n / N]; j < Mb <= 4096, so j^2
+// does not overflow.
+template <bool INV, typename C>
+__device__ __forceinline__ C blue_chirp(const C *__restrict__ T, int n, int N, int j)
+{
+    C c = T[((j * j) % (2 * N)) * (n / N)];
+    if (!INV) c.y = -c.y;
+    return c;
+}
+
+// PRE_POST = false: the caller has already multiplied x by the chirp (and
+// zero-filled a[N..Mb)), and multiplies the result by the chirp itself.
+template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads, bool PRE_POST = true>
 __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const C *__restrict__ T, int n, int N,
                         int Mb, const int *rad2, int np2, const int gs = 0, const int wst = 1)
 {
     const int tid = threadIdx.x;
-    const int cstep = n / N;  // T index of e^{i pi / N}
-    auto chirp = [&](int j) {
-        const int q = (j * j) % (2 * N);  // j < Mb <= 4096: no overflow
-        C c = T[q * cstep];
-        if (!INV) c.y = -c.y;
-        return c;
-    };
-    for (int j = tid; j < Mb; j += NT) {
-        const C c = (j < N) ? chirp(j) : mk<R>(0, 0);
+    auto chirp = [&](int j) { return blue_chirp<INV>(T, n, N, j); };
+    if (PRE_POST) {
+        for (int j = tid; j < Mb; j += NT) {
+            const C c = (j < N) ? chirp(j) : mk<R>(0, 0);
 #pragma unroll
-        for (int gm = 0; gm < G; ++gm) {
-            C *ax = a + (size_t)gm * gs;
-            ax[j] = (j < N) ? cmul(ax[j], c) : c;
+            for (int gm = 0; gm < G; ++gm) {
+                C *ax = a + (size_t)gm * gs;
+                ax[j] = (j < N) ? cmul(ax[j], c) : c;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     C *f = stockham<false, R, C, G, WG, NT>(a, b, Mb, W2, rad2, np2, gs, wst);
     for (int k = tid; k < Mb; k += NT) {
         const C h = INV ? Bh[k] : cconj(Bh[k == 0 ? 0 : Mb - k]);
@@ -410,15 +437,17 @@ __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const
     }
     __syncthreads();
     C *y = stockham<true, R, C, G, WG, NT>(f, (f == a) ? b : a, Mb, W2, rad2, np2, gs, wst);
-    for (int k = tid; k < N; k += NT) {
-        const C c = chirp(k);
+    if (PRE_POST) {
+        for (int k = tid; k < N; k += NT) {
+            const C c = chirp(k);
 #pragma unroll
-        for (int gm = 0; gm < G; ++gm) {
-            C *yx = y + (size_t)gm * gs;
-            yx[k] = cmul(yx[k], c);
+            for (int gm = 0; gm < G; ++gm) {
+                C *yx = y + (size_t)gm * gs;
+                yx[k] = cmul(yx[k], c);
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     return y;
 }
 
@@ -550,9 +579,9 @@ ring_synth_kernel(const __grid_constant__ DevPlan P, const typename C2T<R>::type
 // two barriers.  Shared memory: two regions of G buffers of cap complex
 // elements (A: folded spectra, B: DFT inputs; the DFT ping-pongs between
 // them).  The ring's Delta block (M + 1 orders x G maps) is first copied into
-// region B with all loads in flight, so that the fold reads shared memory
-// instead of paying a global-memory latency per bin (when M + 1 > cap the
-// fold reads global memory directly).  CTAs of one ring are adjacent in the grid
+// region B by asynchronous copies, all in flight at once, so that the fold
+// reads shared memory instead of paying a global-memory latency per bin (when
+// M + 1 > cap the fold reads global memory directly).  CTAs of one ring are adjacent in the grid
 // (block = ring index x groups + group), so the maps of a sector are read at
 // about the same time.  The twiddles come from the plan's global tables
 // through the read-only cache, which leaves shared memory to the buffers.
@@ -594,49 +623,69 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
     const C *D = delta + (size_t)r * (M + 1) * nmaps + b0;  // D[m nmaps + g]
     const bool staged = M + 1 <= cap;
     const int n2 = 2 * n;
+    // Phase indices (m ps) mod 2n advance incrementally: bin k starts at k ps, the
+    // next bin of the thread at (k + NT) ps, the next alias m + n at m ps + n ps.
+    const int pstep = (ps >= 0) ? (n * ps) % n2 : 0;
+    const int dpk = (ps >= 0) ? (NT * ps) % n2 : 0;
     if (staged) {
-        // phase-shifted Delta_m e^{i m phi0} of map g at B0[m G + g]; (m ps) mod 2n
-        // in 32 bits (m <= M, ps < 2n)
-#pragma unroll 4
-        for (int m = tid; m <= M; m += NT) {
-            C ph;
-            if (ps >= 0) {
-                ph = T[(m * ps) % n2];
-            } else {
-                double sn, cs;
-                sincos((double)m * phi0, &sn, &cs);
-                ph = mk<R>((R)cs, (R)sn);
-            }
+        // Delta_m of map g -> B0[m G + g] by asynchronous copies, all in flight at
+        // once (16 bytes = two maps per copy when aligned)
+        const bool v16 = G >= 2 && gn == G && (nmaps & 1) == 0 && (b0 & 1) == 0;
+        const C *src = D + (size_t)tid * nmaps;
+        for (int m = tid; m <= M; m += NT, src += (size_t)NT * nmaps) {
+            if (v16) {
 #pragma unroll
-            for (int g = 0; g < G; ++g)
-                B0[m * G + g] = (g < gn) ? cmul(D[(size_t)m * nmaps + g], ph) : mk<R>(0, 0);
+                for (int h = 0; h < G; h += 2) cp_async16(&B0[m * G + h], src + h);
+            } else {
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (g < gn)
+                        cp_async8(&B0[m * G + g], src + g);
+                    else
+                        B0[m * G + g] = mk<R>(0, 0);
+                }
+            }
         }
+        cp_async_wait_all();
         __syncthreads();
+        int pk = (ps >= 0) ? (tid * ps) % n2 : 0;
         for (int k = tid; k < nb; k += NT) {
             C acc[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) acc[g] = mk<R>(0, 0);
-            // m = k + j n, then m = n - k + j n (m >= 1) conjugated
-            for (int m = k; m <= M; m += n) {
 #pragma unroll
-                for (int g = 0; g < G; ++g) acc[g] = cadd(acc[g], B0[m * G + g]);
-            }
-            for (int m = n - k; m <= M; m += n) {
-                if (m < 1) continue;
+            for (int pass = 0; pass < 2; ++pass) {
+                // pass 0: m = k + j n; pass 1: m = n - k + j n (>= 1), conjugated
+                const int m0 = pass == 0 ? k : n - k;
+                int pi = pass == 0 ? pk : pstep - pk + (pstep < pk ? n2 : 0);
+                for (int m = m0; m <= M; m += n) {
+                    C ph;
+                    if (ps >= 0) {
+                        ph = T[pi];
+                        pi += pstep;
+                        if (pi >= n2) pi -= n2;
+                    } else {
+                        double sn, cs;
+                        sincos((double)m * phi0, &sn, &cs);
+                        ph = mk<R>((R)cs, (R)sn);
+                    }
+                    if (pass == 1 && m < 1) continue;
 #pragma unroll
-                for (int g = 0; g < G; ++g) acc[g] = cadd(acc[g], cconj(B0[m * G + g]));
+                    for (int g = 0; g < G; ++g) {
+                        const C v = cmul(B0[m * G + g], ph);
+                        acc[g] = cadd(acc[g], pass == 0 ? v : cconj(v));
+                    }
+                }
             }
 #pragma unroll
             for (int g = 0; g < G; ++g)
                 if (g < gn) A0[g * cap + k] = acc[g];
+            pk += dpk;
+            if (pk >= n2) pk -= n2;
         }
     } else {
-        // Delta too long to stage: phases from the table, Delta from global memory.
-        // Phase indices advance incrementally: bin k starts at k ps, the next
-        // bin of the thread at (k + NT) ps, the next alias m + n at m ps + n ps.
-        const int pstep = (ps >= 0) ? (n * ps) % n2 : 0;
+        // Delta too long to stage: Delta from global memory
         int pk = (ps >= 0) ? (tid * ps) % n2 : 0;
-        const int dpk = (ps >= 0) ? (NT * ps) % n2 : 0;
         for (int k = tid; k < nb; k += NT) {
             C acc[G];
 #pragma unroll
@@ -676,46 +725,54 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
     __syncthreads();
 
     // 2. spectrum of the complex DFT, into B_g[0..N)
+    //    (Bluestein rings: times the chirp, and zero up to the convolution length Mb)
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const C *F = A0 + g * cap;
         C *Bg = B0 + g * cap;
 #pragma unroll 4
         for (int k = tid; k < N; k += NT) {
+            C z;
             if (even) {
                 const C f = F[k];
                 const C h = cconj(F[N - k]);
                 const C w = T[2 * k];  // e^{2 pi i k / n}
-                Bg[k] = cadd(cadd(f, h), cmuli(cmul(w, csub(f, h))));
+                z = cadd(cadd(f, h), cmuli(cmul(w, csub(f, h))));
             } else {
-                Bg[k] = (k < nb) ? F[k] : cconj(F[N - k]);
+                z = (k < nb) ? F[k] : cconj(F[N - k]);
             }
+            Bg[k] = BLUE ? cmul(z, blue_chirp<true>(T, n, N, k)) : z;
         }
+        if (BLUE)
+            for (int k = N + tid; k < Mb; k += NT) Bg[k] = mk<R>(0, 0);
     }
     __syncthreads();
 
     // 3. inverse complex DFT of length N of every map
     // (a CTA holding fewer than G maps transforms its spare buffers too,
     // harmlessly, and never stores them)
-    C *src = BLUE ? bluestein<true, R, C, G, true, NT>(B0, A0, w2_table<R>(P), bhat_table<R>(P) + P.blue_ofs[r], T, n,
+    C *src = BLUE ? bluestein<true, R, C, G, true, NT, false>(B0, A0, w2_table<R>(P), bhat_table<R>(P) + P.blue_ofs[r], T, n,
                                                        N, Mb, s_rad, s_np, gs, Mb > 0 ? kBlueMaxMb / Mb : 1)
                   : stockham<true, R, C, G, true, NT>(B0, A0, N, T, s_rad, s_np, gs, tstep);
 
-    // 4. store the rings (even n: pixel pairs as one 8-byte store when aligned)
+    // 4. store the rings (Bluestein rings: times the chirp; even n: pixel pairs
+    //    as one 8-byte store when aligned)
     for (int g = 0; g < gn; ++g) {
         const C *z = src + g * gs;
         R *out = map + (size_t)(b0 + g) * P.npix + P.ofs[r];
+        auto val = [&](int j) { return BLUE ? cmul(z[j], blue_chirp<true>(T, n, N, j)) : z[j]; };
         if (even && (reinterpret_cast<uintptr_t>(out) & 7) == 0) {
             float2 *o2 = reinterpret_cast<float2 *>(out);
 #pragma unroll 4
-            for (int j = tid; j < N; j += NT) o2[j] = z[j];
+            for (int j = tid; j < N; j += NT) o2[j] = val(j);
         } else if (even) {
             for (int j = tid; j < N; j += NT) {
-                out[2 * j] = z[j].x;
-                out[2 * j + 1] = z[j].y;
+                const C v = val(j);
+                out[2 * j] = v.x;
+                out[2 * j + 1] = v.y;
             }
         } else {
-            for (int j = tid; j < N; j += NT) out[j] = z[j].x;
+            for (int j = tid; j < N; j += NT) out[j] = val(j).x;
         }
     }
 }
