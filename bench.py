@@ -59,7 +59,9 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--lambda-cache", action="store_true",
-                    help="tensor-core forms: build the plan-time Lambda operand before timing")
+                    help="tensor-core forms: time the headline with the plan-time Lambda operand")
+    ap.add_argument("--no-cached-side", action="store_true",
+                    help="tensor-core forms: skip timing the cached-Lambda form beside the headline")
     ap.add_argument("--workload", choices=["batch", "requests"], default="batch",
                     help="batch: 64 maps at lmax 2048 (the headline); requests: 256 one-map requests, "
                          "lmax log-uniform in [64, 2048], nside = lmax // 2, in one multi-request call")
@@ -209,6 +211,54 @@ def legendre_flops(R: int, L: int, M: int, B: int, prec: str):
     return 3.0 * R * nlm + 4.0 * R * nlm * B
 
 
+def stage_roofline(stage: str, ms: float, args, R: int, lambda_bytes):
+    """Roofline of one step's kernel from its CUDA-event time per step."""
+    L, B = args.lmax, args.maps
+    nlm = (L + 1) * (L + 2) // 2
+    nrings = 4 * args.nside - 1
+    peaks = _peaks()
+    if stage == "ring":
+        npix = 12 * args.nside ** 2
+        esz = 8 if args.prec == "fp64" else 4
+        by = B * (nrings * (L + 1) * 2 * esz + npix * esz)
+        ach = by / (ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"kernel": "ring_synth (smooth and Bluestein ring lists, 2 launches)", "bound": "hbm",
+                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic_for("ring_synth_fp64" if args.prec == "fp64" else "ring_synth_mf"),
+                "bytes_per_step": by, "bytes": "Delta read (complex) + map written", "ms_per_step": ms,
+                "peak_source": "MEASURED_PEAKS hbm_gbs"}
+    if args.prec == "fp64":
+        fl = legendre_flops(R, L, L, B, args.prec)
+        ach = fl / (ms * 1e-3) / 1e12
+        return {"kernel": "legendre_fwd_fp64", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_fwd_fp64"),
+                "peak_source": "nominal FP64 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2070 MHz)",
+                "flops_per_launch": fl, "ms_per_launch": ms}
+    tpk = peaks.get("bf16_tflops_sustained", 1691.3) * TENSOR_PEAK_RATIO[args.prec]
+    fl_t = 4.0 * R * nlm * B
+    tensor = {"algorithmic_tflops": fl_t / (ms * 1e-3) / 1e12,
+              "executed_tflops": PRODUCTS[args.prec] * fl_t / (ms * 1e-3) / 1e12, "peak": tpk,
+              "peak_source": "MEASURED_PEAKS bf16 sustained x nominal dtype ratio",
+              "frac_executed": PRODUCTS[args.prec] * fl_t / (ms * 1e-3) / 1e12 / tpk}
+    if lambda_bytes:
+        # cached Lambda operand: streamed once per launch, with a_lm read and Delta written
+        by = lambda_bytes + B * (16 * nlm + nrings * (L + 1) * 8)
+        ach = by / (ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"kernel": "legendre_tc_stream (cached Lambda)", "bound": "hbm", "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "traffic": traffic_for("legendre_tc_stream"),
+                "bytes_per_launch": by, "ms_per_launch": ms, "peak_source": "MEASURED_PEAKS hbm_gbs",
+                "bytes": "Lambda operand + a_lm (complex128) + Delta (complex64)", "tensor": tensor}
+    # the FP64 recurrence (3 flops per (l, m, ring pair)) bounds the kernel
+    fl64 = 3.0 * R * nlm
+    ach = fl64 / (ms * 1e-3) / 1e12
+    return {"kernel": "legendre_tc", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_tc"),
+            "peak_source": "nominal FP64 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2070 MHz)",
+            "flops_per_launch": fl64, "ms_per_launch": ms, "tensor": tensor}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -344,68 +394,61 @@ def run_ours(args):
                "d2h_bytes_per_step": int(m_pin.numel() * m_pin.element_size()), "ms_per_step": dt * 1000}
         del a_pin, m_pin
 
+    # the same form with the plan-time Lambda operand (the recurrence moved to
+    # plan time), timed beside the headline
+    cached = None
+    if args.prec != "fp64" and not args.lambda_cache and not args.no_cached_side:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.lambda_cache(args.prec)
+        build_s = time.perf_counter() - t0
+        for _ in range(2):
+            plan.alm2map(alm, args.prec, out=out)
+        torch.cuda.synchronize()
+        plan.profile(True)
+        plan.profile_read()
+        clk2 = ClockSampler(local)
+        if not args.no_clocks:
+            clk2.start()
+            time.sleep(0.3)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            plan.alm2map(alm, args.prec, out=out)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cclocks = clk2.stop()
+        cst = plan.profile_read()
+        plan.profile(False)
+        cms = c0.elapsed_time(c1) / args.steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([cms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            cms = float(t.item())
+        cached = {"value": world * B / (cms * 1e-3), "unit": UNIT, "ms_per_step": cms, "steps": args.steps,
+                  "stages_ms_per_step": {k: v[0] / args.steps for k, v in cst.items() if v[1]},
+                  "lambda_bytes": plan.lambda_cache_bytes(args.prec), "build_s": build_s, "clocks": cclocks,
+                  "note": "Lambda computed by the FP64 recurrence once at plan time (sht_lambda_cache), "
+                          "streamed from HBM by every call; results bit-identical to the headline's"}
+        plan.lambda_cache(args.prec, False)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel
-    dom = max(stages, key=lambda s: stages[s][0])
-    # the step's time in its dominant stage (the tensor-core forms launch the
-    # operand prep and the Legendre kernel inside the same stage)
-    dom_ms = stages[dom][0] / args.steps
+    # roofline of the dominant kernel (and of the other step)
     R = (4 * args.nside - 1 + 1) // 2
-    roof = None
-    if dom == "legendre" and args.prec == "fp64":
-        fl = legendre_flops(R, L, L, B, args.prec)
-        ach = fl / (dom_ms * 1e-3) / 1e12
-        roof = {"kernel": "legendre_fwd_fp64", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_fwd_fp64"),
-                "peak_source": "nominal FP64 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2070 MHz); ncu fp64 pipe active is the cross-check",
-                "flops_per_launch": fl, "ms_per_launch": dom_ms}
-    elif dom == "legendre" and lcache is not None:
-        # cached Lambda operand: the kernel streams it once per launch (plus
-        # the B operand and the Delta writes); HBM bounds it
-        nlm = (L + 1) * (L + 2) // 2
-        by = lcache["bytes"] + B * (16 * nlm + (4 * args.nside - 1) * (L + 1) * 8)
-        ach = by / (dom_ms * 1e-3) / 1e9
-        peak = _peaks().get("hbm_gbs", 6800.0)
-        roof = {"kernel": "legendre_tc cached (+ operand prep)", "bound": "hbm", "achieved": ach, "peak": peak,
-                "unit": "GB/s", "frac": ach / peak, "traffic": traffic_for("legendre_tc_cached"),
-                "bytes_per_launch": by, "ms_per_launch": dom_ms,
-                "bytes": "Lambda operand + a_lm (complex128) + Delta (complex64)"}
-        tpk = _peaks().get("bf16_tflops_sustained", 1691.3) * TENSOR_PEAK_RATIO[args.prec]
-        fl_t = 4.0 * R * nlm * B
-        roof["tensor"] = {"algorithmic_tflops": fl_t / (dom_ms * 1e-3) / 1e12,
-                          "executed_tflops": PRODUCTS[args.prec] * fl_t / (dom_ms * 1e-3) / 1e12,
-                          "peak": tpk, "peak_source": "MEASURED_PEAKS bf16 sustained x nominal dtype ratio",
-                          "frac_executed": PRODUCTS[args.prec] * fl_t / (dom_ms * 1e-3) / 1e12 / tpk}
-    elif dom == "legendre":
-        # tensor-core forms: the FP64 recurrence bounds the kernel; the
-        # contraction's tensor-pipe figure is reported beside it
-        nlm = (L + 1) * (L + 2) // 2
-        fl64 = 3.0 * R * nlm
-        ach = fl64 / (dom_ms * 1e-3) / 1e12
-        roof = {"kernel": "legendre_tc (+ operand prep)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": traffic_for("legendre_tc"),
-                "peak_source": "nominal FP64 1.25 TFLOP/s; the recurrence (3 flops per (l, m, ring pair)) is the bound",
-                "flops_per_launch": fl64, "ms_per_launch": dom_ms}
-        tpk = _peaks().get("bf16_tflops_sustained", 1691.3) * TENSOR_PEAK_RATIO[args.prec]
-        fl_t = 4.0 * R * nlm * B
-        roof["tensor"] = {"algorithmic_tflops": fl_t / (dom_ms * 1e-3) / 1e12,
-                          "executed_tflops": PRODUCTS[args.prec] * fl_t / (dom_ms * 1e-3) / 1e12,
-                          "peak": tpk, "peak_source": "MEASURED_PEAKS bf16 sustained x nominal dtype ratio",
-                          "frac_executed": PRODUCTS[args.prec] * fl_t / (dom_ms * 1e-3) / 1e12 / tpk}
-    elif dom == "ring":
-        npix = 12 * args.nside ** 2
-        esz = 8 if args.prec == "fp64" else 4
-        by = B * ((4 * args.nside - 1) * (L + 1) * 2 * esz + npix * esz)
-        ach = by / (dom_ms * 1e-3) / 1e9
-        peak = _peaks().get("hbm_gbs", 6800.0)
-        roof = {"kernel": "ring_synth", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": traffic_for("ring_synth"), "bytes_per_launch": by,
-                "ms_per_launch": dom_ms}
+    rl = {k: stage_roofline(k, v[0] / args.steps, args, R, lcache["bytes"] if lcache else None)
+          for k, v in stages.items() if v[1] and k in ("legendre", "ring")}
+    dom = max(rl, key=lambda k: stages[k][0]) if rl else None
+    roof = rl.get(dom)
+    if cached is not None:
+        cst = cached["stages_ms_per_step"]
+        cached["roofline"] = {k: stage_roofline(k, cst[k], args, R, cached["lambda_bytes"])
+                              for k in ("legendre", "ring") if k in cst}
 
     maps_per_s = world * B / (ms * 1e-3)
     line = {"metric": METRIC, "value": maps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -413,8 +456,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": dict(workload(args), parallelism="replicas x%d" % world, precision=args.prec,
                            lambda_cache=lcache is not None),
-            "lambda_cache": lcache, "tiles": tiles,
-            "roofline": roof,
+            "lambda_cache": lcache, "tiles": tiles, "lambda_cached_form": cached,
+            "roofline": roof, "roofline_other_step": {k: v for k, v in rl.items() if k != dom},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
             "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy,
             "fp64_path": fp64_path}

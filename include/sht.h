@@ -213,7 +213,9 @@ const char *sht_last_error(void);
  * sec. 6; here CUDA events are recorded on the launch stream around every
  * kernel the plan launches while profiling is enabled).
  * Stages: SHT_STAGE_LEGENDRE (Legendre step), SHT_STAGE_RING (ring step),
- * SHT_STAGE_ADJ_RING, SHT_STAGE_ADJ_LEGENDRE (the transpose's two steps).
+ * SHT_STAGE_ADJ_RING, SHT_STAGE_ADJ_LEGENDRE (the transpose's two steps),
+ * SHT_STAGE_OPERAND_PREP (the tensor-core forms' conversion of a_lm into the
+ * split B operand, before each Legendre launch).
  * sht_profile_read synchronises the plan's device, writes the summed
  * milliseconds and the launch count of each of the first nstage stages into
  * ms[] and launches[] (either may be NULL) and resets the counters. */
@@ -221,7 +223,8 @@ const char *sht_last_error(void);
 #define SHT_STAGE_RING 1
 #define SHT_STAGE_ADJ_RING 2
 #define SHT_STAGE_ADJ_LEGENDRE 3
-#define SHT_NSTAGES 4
+#define SHT_STAGE_OPERAND_PREP 4
+#define SHT_NSTAGES 5
 int sht_profile(sht_plan_t plan, int enable);
 int sht_profile_read(sht_plan_t plan, int nstage, double *ms, long long *launches);
 

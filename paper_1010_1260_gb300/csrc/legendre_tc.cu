@@ -289,6 +289,9 @@ __device__ __forceinline__ void store_chunk(unsigned char *sbase, int t, int c, 
 // written as NPA pieces into the stage's A tiles ([parity][piece], 4 KB
 // each, K-major rows of 32 bytes with the 32-byte swizzle).  a_cur holds
 // A_{l+1} for the stage's degrees, one per lane.
+// The products A_{l+1} x are written as fma(A, x, +0.0), which equals A x up
+// to the sign of a zero and issues as a DFMA (the FP64 pipe takes a DMUL per
+// 76 cycles and a DFMA per 64 per warp).
 // SLOW = false (no ring of the warp still rescaled): software-pipelined for
 // one warp per SM sub-partition issuing in order -- each degree issues its
 // DFMA (the only dependent chain), the DMUL of the degree two ahead (which
@@ -308,8 +311,8 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
     if constexpr (!SLOW) {
         // A_{l+1} x two degrees ahead, A_{l+1} three degrees ahead: the DFMA of
         // a degree never waits for its DMUL, nor the DMUL for its shuffle.
-        double ax0 = __shfl_sync(0xffffffffu, a_cur, 0) * x;
-        double ax1 = __shfl_sync(0xffffffffu, a_cur, 1) * x;
+        double ax0 = fma(__shfl_sync(0xffffffffu, a_cur, 0), x, 0.0);
+        double ax1 = fma(__shfl_sync(0xffffffffu, a_cur, 1), x, 0.0);
         double an = __shfl_sync(0xffffffffu, a_cur, 2);
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
@@ -326,7 +329,7 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
                     val[u] = p1;
                     const double tt = fma(ax0, p1, -p0);
                     ax0 = ax1;
-                    if (q + 2 < STEPS) ax1 = an * x;
+                    if (q + 2 < STEPS) ax1 = fma(an, x, 0.0);
                     if (q + 3 < STEPS) an = __shfl_sync(0xffffffffu, a_cur, q + 3);
                     p0 = p1;
                     p1 = tt;
@@ -351,7 +354,7 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
     }
     double ax[STEPS], vv[STEPS];
 #pragma unroll
-    for (int q = 0; q < STEPS; ++q) ax[q] = __shfl_sync(0xffffffffu, a_cur, q) * x;
+    for (int q = 0; q < STEPS; ++q) ax[q] = fma(__shfl_sync(0xffffffffu, a_cur, q), x, 0.0);
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
         const bool live_k = (k == 0);
@@ -527,19 +530,63 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
                 ++gg;
             }
             if (!ok) break;
-            // Delta_m(north) = E + O, Delta_m(south) = E - O for this item's
-            // rows; Delta is [ring][m][map], so a row's maps are contiguous
-            if (pair < P.npairs) {
-                const int2 rr = P.pair_ring[pair];
+            // Delta_m(north) = E + O, Delta_m(south) = E - O for the warp's 32
+            // rows; Delta is [ring][m][map].  Per block of 16 maps (columns
+            // 32 k .. 32 k + 31 of E and of O) the warp reads its rows' totals,
+            // writes N and S back transposed into the same, now consumed,
+            // totals (row r's 32 floats as 16-byte granules, granule x at
+            // x ^ (r & 7): no bank conflicts) and sends each row's 128 bytes
+            // out as 16-byte stores, four rows per instruction.
+            {
+                const int quad = warp - 4;
+                int2 rr = make_int2(-1, -1);
+                if (pair < P.npairs) rr = P.pair_ring[pair];
                 const int M1 = P.mmax + 1;
-                float2 *dn = delta + ((size_t)rr.x * M1 + m) * nmaps;
-                float2 *ds = delta + ((size_t)max(rr.y, 0) * M1 + m) * nmaps;
-                for (int b = 0; b < nmaps; ++b) {
-                    const float er = tot[(2 * b) * kRows + row], ei = tot[(2 * b + 1) * kRows + row];
-                    const float orr = tot[(ncols + 2 * b) * kRows + row];
-                    const float oi = tot[(ncols + 2 * b + 1) * kRows + row];
-                    dn[b] = make_float2(er + orr, (m == 0) ? 0.f : ei + oi);
-                    if (rr.y >= 0) ds[b] = make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
+                const bool vec = (nmaps & 1) == 0;
+                // float x of row r of the transposed block at column col0
+                auto slot = [&](int col0, int r, int x) {
+                    return tot + (size_t)(col0 + r) * kRows + 32 * quad + ((((x >> 2) ^ (r & 7)) << 2) | (x & 3));
+                };
+                for (int k = 0; 32 * k < ncols; ++k) {
+                    float e[32], o[32];
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        e[c] = tot[(32 * k + c) * kRows + row];
+                        o[c] = tot[(ncols + 32 * k + c) * kRows + row];
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int x = 0; x < 32; x += 4) {
+                        const float4 nv = make_float4(e[x] + o[x], (m == 0) ? 0.f : e[x + 1] + o[x + 1],
+                                                      e[x + 2] + o[x + 2], (m == 0) ? 0.f : e[x + 3] + o[x + 3]);
+                        const float4 sv = make_float4(e[x] - o[x], (m == 0) ? 0.f : e[x + 1] - o[x + 1],
+                                                      e[x + 2] - o[x + 2], (m == 0) ? 0.f : e[x + 3] - o[x + 3]);
+                        *reinterpret_cast<float4 *>(slot(32 * k, lane, x)) = nv;
+                        *reinterpret_cast<float4 *>(slot(ncols + 32 * k, lane, x)) = sv;
+                    }
+                    __syncwarp();
+                    const int sg = lane & 7;  // granule sg: maps 16 k + 2 sg and + 1
+                    const int b = 16 * k + 2 * sg;
+#pragma unroll
+                    for (int side = 0; side < 2; ++side) {
+#pragma unroll
+                        for (int it = 0; it < 8; ++it) {
+                            const int rw = it * 4 + (lane >> 3);
+                            const int ring = __shfl_sync(0xffffffffu, side == 0 ? rr.x : rr.y, rw);
+                            const float4 v =
+                                *reinterpret_cast<const float4 *>(slot(side == 0 ? 32 * k : ncols + 32 * k, rw, 4 * sg));
+                            if (ring >= 0) {
+                                float2 *d = delta + ((size_t)ring * M1 + m) * nmaps + b;
+                                if (vec && b + 1 < nmaps) {
+                                    *reinterpret_cast<float4 *>(d) = v;
+                                } else {
+                                    if (b < nmaps) d[0] = make_float2(v.x, v.y);
+                                    if (b + 1 < nmaps) d[1] = make_float2(v.z, v.w);
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
                 }
             }
         }

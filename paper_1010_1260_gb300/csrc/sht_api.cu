@@ -618,7 +618,7 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
     float2 *delta = static_cast<float2 *>(p->ws);  // [ring][m][map]
     for (int b0 = 0; b0 < nbatch; b0 += group) {
         const int nb = std::min(group, nbatch - b0);
-        StageScope s0(p, SHT_STAGE_LEGENDRE, st);
+        StageScope s0(p, SHT_STAGE_OPERAND_PREP, st);
         cudaError_t e = sht::launch_tc_prep(p->dp, p->tc, prec, alm + (size_t)b0 * p->nalm, nb, st);
         s0.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");

@@ -103,7 +103,7 @@ def check(rc: int):
         raise ShtError(rc, lib().sht_last_error().decode())
 
 
-STAGES = ("legendre", "ring", "adj_ring", "adj_legendre")
+STAGES = ("legendre", "ring", "adj_ring", "adj_legendre", "operand_prep")
 
 
 def kernel_launches() -> int:
