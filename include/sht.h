@@ -234,6 +234,16 @@ int sht_profile_read(sht_plan_t plan, int nstage, double *ms, long long *launche
  * SHT_ECUDA for a CUDA error, else SHT_OK. */
 int sht_sync(sht_plan_t plan);
 
+/* Test hook for the bounded device-side waits: the next tensor-core Legendre
+ * launch of this plan (per-call or cached-Lambda form) skips, in its CTA 0,
+ * the operand copies of stage number `stage` (counted over that CTA's work
+ * items; -1 clears the hook).  The MMA warp's wait for that stage then runs
+ * out after its 2 s limit; the CTA stops, drains (bounded) what it issued,
+ * frees its tensor memory and sets the plan's status word, so sht_sync
+ * reports SHT_ETIMEOUT and that launch's output is invalid.  No fault, trap or
+ * endless wait is involved; the context stays usable.  Errors: SHT_EINVAL. */
+int sht_debug_withhold_stage(sht_plan_t plan, int stage);
+
 /* Number of kernels libsht has launched in this process (all plans). */
 unsigned long long sht_kernel_launches(void);
 

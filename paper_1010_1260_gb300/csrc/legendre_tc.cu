@@ -35,6 +35,9 @@
 // through mbarriers.  Every wait is bounded by a global-timer limit; on
 // timeout the CTA records an error in the plan's status word, drains its
 // copies and MMAs (again bounded), frees its tensor memory and returns.
+// withhold >= 0 (a test hook, sht_debug_withhold_stage) makes CTA 0 skip the
+// copies of its stage number `withhold`, so that the MMA warp's wait for that
+// stage runs out: nothing faults, the CTA takes the abort path above.
 #include "sht.h"
 #include "sht_internal.cuh"
 
@@ -398,7 +401,7 @@ constexpr int kPrefetch = 8;  // stages of B tiles prefetched into L2 ahead of t
 template <bool BF16, int NPA, int NPB>
 __global__ void __launch_bounds__(kWarps * 32, 1)
 legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, const int *__restrict__ seg_off,
-                   float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status)
+                   float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status, int withhold)
 {
     using C = Cfg<BF16, NPA, NPB>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -608,6 +611,10 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
                     const int s = (int)(gs % C::NS);
                     const uint32_t ph = (gs / C::NS) & 1u;
                     if (i + kPrefetch < nst) bulk_prefetch_l2(blk + (size_t)(i + kPrefetch) * SB, SB);
+                    if ((int)gs == withhold && blockIdx.x == 0) {
+                        ++gs;  // test hook: this stage's copy is never issued
+                        continue;
+                    }
                     if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
                         ok = false;
                         break;
@@ -713,7 +720,7 @@ template <bool BF16, int NPA, int NPB>
 __global__ void __launch_bounds__(kWarps * 32, 1)
 legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf,
                           const unsigned char *__restrict__ acache, const int *__restrict__ seg_off,
-                          float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status)
+                          float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status, int withhold)
 {
     using C = Cfg<BF16, NPA, NPB>;
     constexpr int NS = StreamCfg<BF16, NPA, NPB>::NS;
@@ -869,6 +876,10 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
                 for (int i = 0; i < nst; ++i) {
                     const int s = (int)(gs % NS);
                     const uint32_t ph = (gs / NS) & 1u;
+                    if ((int)gs == withhold && blockIdx.x == 0) {
+                        ++gs;  // test hook: this stage's copies are never issued
+                        continue;
+                    }
                     if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
                         ok = false;
                         break;
@@ -1062,9 +1073,9 @@ cudaError_t launch_persistent(K kern, int smem, const DevPlan &P, const TcWork &
     const int ncols = tc_ncols(nmaps);
     if constexpr (STREAM)
         kern<<<grid, kWarps * 32, smem, st>>>(P, b, static_cast<const unsigned char *>(acache), seg, delta, nmaps,
-                                              ncols, W.status);
+                                              ncols, W.status, W.withhold);
     else
-        kern<<<grid, kWarps * 32, smem, st>>>(P, b, seg, delta, nmaps, ncols, W.status);
+        kern<<<grid, kWarps * 32, smem, st>>>(P, b, seg, delta, nmaps, ncols, W.status, W.withhold);
     return cudaGetLastError();
 }
 

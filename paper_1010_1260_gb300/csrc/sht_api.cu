@@ -624,6 +624,7 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
         StageScope s1(p, SHT_STAGE_LEGENDRE, st);
         e = sht::launch_tc_main(p->dp, p->tc, prec, p->lcache[prec], delta, nb, st);
+        p->tc.withhold = -1;  // the test hook applies to one launch
         s1.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc launch");
         StageScope s2(p, SHT_STAGE_RING, st);
@@ -897,6 +898,17 @@ int sht_tiles(sht_plan_t p, int *out, int n)
     if (!out || n < 0) return fail(SHT_EINVAL, "null output or n < 0");
     const int v[5] = {p->ring_g[0], p->ring_g[1], p->ring_nt, p->fp64_bc, p->fp64_ring_g};
     for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
+    return SHT_OK;
+}
+
+int sht_debug_withhold_stage(sht_plan_t p, int stage)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (stage < -1) return fail(SHT_EINVAL, "stage < -1");
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->tc.withhold = stage;
     return SHT_OK;
 }
 

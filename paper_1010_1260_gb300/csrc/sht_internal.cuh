@@ -120,6 +120,7 @@ constexpr int kTcMaxMaps = 64;
 struct TcWork {
     const int *seg_tf32 = nullptr;
     const int *seg_bf16 = nullptr;
+    int withhold = -1;  // test hook: stage whose copies CTA 0 of the next launch skips (-1: none)
     long long kall_tf32 = 0, kall_bf16 = 0;
     void *bbuf = nullptr;
     int *status = nullptr;

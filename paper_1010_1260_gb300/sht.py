@@ -86,13 +86,14 @@ def lib():
             L.sht_autotune.argtypes = [P, I, I, V]
             L.sht_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_set_tiles.argtypes = [P, ctypes.POINTER(I), I]
+            L.sht_debug_withhold_stage.argtypes = [P, I]
             L.sht_kernel_launches.argtypes = []
             L.sht_kernel_launches.restype = ctypes.c_ulonglong
             for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
                       "sht_alm2map_batch", "sht_map2alm_adjoint_batch", "sht_profile",
                       "sht_profile_read", "sht_sync", "sht_multi_create", "sht_multi_alm2map",
                       "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
-                      "sht_tiles", "sht_set_tiles"):
+                      "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -252,6 +253,11 @@ class Plan:
             cur[k] = int(v)
         vals = (ctypes.c_int * 5)(*[cur[k] for k in self.TILE_NAMES])
         check(lib().sht_set_tiles(self._h, vals, 5))
+
+    def debug_withhold_stage(self, stage: int):
+        """Test hook: the next tensor-core Legendre launch skips one stage's
+        operand copies in its first CTA, so its bounded wait runs out."""
+        check(lib().sht_debug_withhold_stage(self._h, int(stage)))
 
     def sync(self):
         """Wait for the plan's device; raise ShtError(SHT_ETIMEOUT) if a kernel

@@ -62,5 +62,6 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.sht_autotune(None, sht.PREC["bf16x6_tc"], 4, None) == sht.SHT_EINVAL
     assert lib.sht_tiles(None, None, 0) == sht.SHT_EINVAL
     assert lib.sht_set_tiles(None, None, 0) == sht.SHT_EINVAL
+    assert lib.sht_debug_withhold_stage(None, 0) == sht.SHT_EINVAL
     assert lib.sht_nalm(None) == 0 and lib.sht_npix(None) == 0
     assert lib.sht_plan_destroy(None) == sht.SHT_OK
