@@ -109,6 +109,29 @@ int sht_alm2map(sht_plan_t plan, const void *alm_dev, void *map_dev, int prec, v
  * nalm complex128, fully overwritten. */
 int sht_map2alm_adjoint(sht_plan_t plan, const void *map_dev, void *alm_dev, int prec, void *stream);
 
+/* Quadrature-weighted analysis, map2alm (Eq. map2almDef with the integral's
+ * measure and the conjugate harmonic; the paper leaves this direction to
+ * future work, sec. 1):
+ *   a_lm = sum_p w_p y_p lambda_lm(theta_p) e^{-i m phi_p},  m >= 0,
+ * with w_p the plan's pixel weight of p's ring: Gauss-Legendre weight x 2 pi /
+ * nphi on a GL grid (exact for band-limited maps when nrings >= lmax + 1 and
+ * nphi >= 2 lmax + 1), 4 pi / npix on HEALPix (equal-area pixels; approximate),
+ * none on a RINGS grid until sht_set_ring_weights.  niter >= 0 Jacobi
+ * refinements a += map2alm(y - alm2map(a)) follow (the usual HEALPix
+ * iteration); they allocate two temporary buffers (nbatch maps, nbatch
+ * coefficient sets) and synchronise `stream` at the end.  FP64 only (prec =
+ * SHT_FP64, else SHT_EUNSUPPORTED).  map_dev: nbatch x npix float64;
+ * alm_dev: nbatch x nalm complex128, fully overwritten.  Errors: SHT_EINVAL,
+ * SHT_EUNSUPPORTED (no weights, or a precision form), SHT_ENOMEM, SHT_ECUDA. */
+int sht_map2alm(sht_plan_t plan, const void *map_dev, void *alm_dev, int prec, int niter, void *stream);
+int sht_map2alm_batch(sht_plan_t plan, int nbatch, const void *map_dev, void *alm_dev, int prec, int niter,
+                      void *stream);
+
+/* Pixel quadrature weight of every ring (host array of nrings doubles, each
+ * finite and >= 0): set (synchronises the plan's device) or read. */
+int sht_set_ring_weights(sht_plan_t plan, const double *w);
+int sht_ring_weights(sht_plan_t plan, double *w);
+
 /* Batched forms: nbatch >= 0 maps, strides nalm and npix.  nbatch == 0 is a no-op. */
 int sht_alm2map_batch(sht_plan_t plan, int nbatch, const void *alm_dev, void *map_dev,
                       int prec, void *stream);

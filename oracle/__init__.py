@@ -15,6 +15,11 @@ marshals numpy arrays.  Each function follows the paper (Hupca et al.,
                            (Algorithm 1), the ring sum as a literal DFT.
 * ``map2alm_adjoint``   -- the literal real-linear transpose of ``alm2map``
                            (Eq. map2almDef without quadrature weights).
+* ``map2alm``           -- the quadrature-weighted analysis sum
+                           a_lm = sum_p w_p y_p lambda_lm e^{-i m phi_p} (Eq.
+                           map2almDef with the integral's measure), written out
+                           as the literal transpose applied to w * y, divided
+                           by the transpose's factor 2 for m > 0.
 * ``gl_grid``, ``healpix_grid`` -- ring geometry (Gauss-Legendre by Newton
                            iteration; HEALPix RING from Gorski et al. 2005).
 
@@ -185,3 +190,25 @@ def map2alm_adjoint(grid: dict, lmax: int, mmax: int, maps: np.ndarray, ms=None,
     if nt < 0:
         raise RuntimeError("orc_map2alm_adjoint failed (%d)" % nt)
     return out
+
+
+def pixel_weights(grid: dict) -> np.ndarray:
+    """Quadrature weight of each ring's pixels: the Gauss weight x 2 pi / nphi on
+    a Gauss-Legendre grid, the equal pixel area 4 pi / npix on HEALPix."""
+    if grid["kind"] == "gl":
+        return grid["w"] * (2.0 * np.pi / grid["nphi"])
+    if grid["kind"] == "healpix":
+        return np.full(grid["nrings"], 4.0 * np.pi / grid["npix"])
+    raise ValueError("no quadrature weights for a generic ring grid")
+
+
+def map2alm(grid: dict, lmax: int, mmax: int, maps: np.ndarray, weights=None) -> np.ndarray:
+    """a_lm = sum_p w_p y_p lambda_lm(theta_p) e^{-i m phi_p}, m >= 0 (ring weights
+    ``weights`` or the grid's own)."""
+    w = pixel_weights(grid) if weights is None else np.asarray(weights, dtype=np.float64)
+    maps = np.atleast_2d(np.asarray(maps, dtype=np.float64))
+    wp = np.repeat(w, grid["nphi"].astype(np.int64))
+    g = map2alm_adjoint(grid, lmax, mmax, maps * wp[None, :])
+    m_of = np.concatenate([np.full(lmax + 1 - m, m) for m in range(mmax + 1)])
+    g[:, m_of > 0] *= 0.5
+    return g

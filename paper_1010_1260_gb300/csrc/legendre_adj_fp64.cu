@@ -1,5 +1,6 @@
 // Legendre step of the transpose (map2alm_adjoint) in FP64:
-//   g_lm = c_m sum_r lambda_lm(x_r) q_m(r),  c_0 = 1, c_m = 2 for m > 0,
+//   g_lm = c_m sum_r lambda_lm(x_r) q_m(r),  c_0 = 1, c_m = 2 for m > 0 (c_m = 1
+//   for the quadrature-weighted analysis sum, whose q carries the weights),
 // the real-linear transpose of Eq. DeltaDef (the paper's map2alm, Eq. map2almDef,
 // without quadrature weights).  With the ring pairs of the forward step and
 // lambda_lm(-x) = (-1)^(l-m) lambda_lm(x):
@@ -39,7 +40,7 @@ struct QPair {
 template <int BC>
 __global__ void __launch_bounds__(kThreads)
 legendre_adj_fp64_kernel(const DevPlan P, const double2 *__restrict__ q, double2 *__restrict__ g,
-                         int nmaps)
+                         int nmaps, double cfac)
 {
     constexpr int PS = 4 / BC;  // pair slices in phase 2
     const int m = blockIdx.x;
@@ -68,7 +69,7 @@ legendre_adj_fp64_kernel(const DevPlan P, const double2 *__restrict__ q, double2
     const int bsel = (tid / kCL) % BC;  // phase-2 map
     const int ph = tid / (kCL * BC);    // phase-2 pair slice
     const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
-    const double cm = (m == 0) ? 1.0 : 2.0;
+    const double cm = (m == 0) ? 1.0 : cfac;
 
     for (int l0 = m; l0 <= L; l0 += kCL) {
         const int cnt = min(kCL, L + 1 - l0);
@@ -166,7 +167,7 @@ size_t smem_bytes(int R)
 }
 
 template <int BC>
-cudaError_t launch_bc(const DevPlan &P, const double2 *q, double2 *g, int nmaps, cudaStream_t st)
+cudaError_t launch_bc(const DevPlan &P, const double2 *q, double2 *g, int nmaps, double cfac, cudaStream_t st)
 {
     const size_t smem = smem_bytes<BC>(P.npairs);
     auto kern = legendre_adj_fp64_kernel<BC>;
@@ -175,7 +176,7 @@ cudaError_t launch_bc(const DevPlan &P, const double2 *q, double2 *g, int nmaps,
         if (e != cudaSuccess) return e;
     }
     dim3 grid(P.mmax + 1, (nmaps + BC - 1) / BC);
-    kern<<<grid, kThreads, smem, st>>>(P, q, g, nmaps);
+    kern<<<grid, kThreads, smem, st>>>(P, q, g, nmaps, cfac);
     return cudaGetLastError();
 }
 
@@ -189,14 +190,14 @@ size_t legendre_adj_smem_bytes(const DevPlan &P, int bc)
     return s <= (size_t)(227 * 1024 - 1024) ? s : 0;
 }
 
-cudaError_t launch_legendre_adj_fp64(const DevPlan &P, const double2 *q, double2 *g, int nmaps,
+cudaError_t launch_legendre_adj_fp64(const DevPlan &P, const double2 *q, double2 *g, int nmaps, double cfac,
                                      cudaStream_t st)
 {
     if (nmaps <= 0) return cudaSuccess;
     const int bc = pick_bc(nmaps);
-    if (bc == 4) return launch_bc<4>(P, q, g, nmaps, st);
-    if (bc == 2) return launch_bc<2>(P, q, g, nmaps, st);
-    return launch_bc<1>(P, q, g, nmaps, st);
+    if (bc == 4) return launch_bc<4>(P, q, g, nmaps, cfac, st);
+    if (bc == 2) return launch_bc<2>(P, q, g, nmaps, cfac, st);
+    return launch_bc<1>(P, q, g, nmaps, cfac, st);
 }
 
 }  // namespace sht

@@ -586,7 +586,7 @@ ring_synth_kernel(const __grid_constant__ DevPlan P, const typename C2T<R>::type
 // about the same time.  The twiddles come from the plan's global tables
 // through the read-only cache, which leaves shared memory to the buffers.
 template <bool BLUE, int G, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, (NT == 256 && G <= 2) ? 3 : 1)
 ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict__ delta, float *__restrict__ map,
                      int nmaps)
 {
@@ -646,29 +646,59 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
                 }
             }
         }
+        // the phase of each of the thread's bins' first alias (m = k), loaded
+        // while the copies are in flight; bins k = tid + j NT, j < JB, cover
+        // nb <= cap <= 4097
+        constexpr int JB = 4352 / NT + 1;
+        C ph0[JB];
+        int pk0[JB];
+        {
+            int pk = (ps >= 0) ? (tid * ps) % n2 : 0;
+#pragma unroll
+            for (int j = 0; j < JB; ++j) {
+                const int k = tid + j * NT;
+                pk0[j] = pk;
+                if (k < nb && k <= M) {
+                    if (ps >= 0) {
+                        ph0[j] = T[pk];
+                    } else {
+                        double sn, cs;
+                        sincos((double)k * phi0, &sn, &cs);
+                        ph0[j] = mk<R>((R)cs, (R)sn);
+                    }
+                }
+                pk += dpk;
+                if (pk >= n2) pk -= n2;
+            }
+        }
         cp_async_wait_all();
         __syncthreads();
-        int pk = (ps >= 0) ? (tid * ps) % n2 : 0;
-        for (int k = tid; k < nb; k += NT) {
+#pragma unroll
+        for (int j = 0; j < JB; ++j) {
+            const int k = tid + j * NT;
+            if (k >= nb) break;
             C acc[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) acc[g] = mk<R>(0, 0);
 #pragma unroll
             for (int pass = 0; pass < 2; ++pass) {
                 // pass 0: m = k + j n; pass 1: m = n - k + j n (>= 1), conjugated
+                const int pk = pk0[j];
                 const int m0 = pass == 0 ? k : n - k;
                 int pi = pass == 0 ? pk : pstep - pk + (pstep < pk ? n2 : 0);
                 for (int m = m0; m <= M; m += n) {
                     C ph;
-                    if (ps >= 0) {
+                    if (pass == 0 && m == k) {
+                        ph = ph0[j];
+                    } else if (ps >= 0) {
                         ph = T[pi];
-                        pi += pstep;
-                        if (pi >= n2) pi -= n2;
                     } else {
                         double sn, cs;
                         sincos((double)m * phi0, &sn, &cs);
                         ph = mk<R>((R)cs, (R)sn);
                     }
+                    pi += pstep;
+                    if (pi >= n2) pi -= n2;
                     if (pass == 1 && m < 1) continue;
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
@@ -680,8 +710,6 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
 #pragma unroll
             for (int g = 0; g < G; ++g)
                 if (g < gn) A0[g * cap + k] = acc[g];
-            pk += dpk;
-            if (pk >= n2) pk -= n2;
         }
     } else {
         // Delta too long to stage: Delta from global memory
@@ -797,10 +825,11 @@ ring_synth_multi_kernel(const DevPlan *__restrict__ plans, const int2 *__restric
 // where Y is the forward real DFT of the ring (Y_{n-k} = conj Y_k).  For even
 // n the real DFT runs as one complex DFT of z_j = y_{2j} + i y_{2j+1}, length
 // h = n/2: Y_k = (Z_k + conj Z_{h-k})/2 - (i/2) w^{-k} (Z_k - conj Z_{h-k}).
+// wring (optional): q_m(r) is multiplied by the ring's pixel quadrature weight.
 template <typename R, bool BLUE>
 __global__ void __launch_bounds__(kThreads)
-ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
-                     typename C2T<R>::type *__restrict__ qout, int nmaps, int gmaps)
+ring_analysis_kernel(const DevPlan P, const R *__restrict__ map, typename C2T<R>::type *__restrict__ qout,
+                     const double *__restrict__ wring, int nmaps, int gmaps)
 {
     using C = typename C2T<R>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -876,7 +905,8 @@ ring_analysis_kernel(const DevPlan P, const R *__restrict__ map,
                 sincos((double)m * phi0, &sn, &cs);
                 ph = mk<R>((R)cs, (R)sn);
             }
-            q[m] = cmul(yk, cconj(ph));
+            const C v = cmul(yk, cconj(ph));
+            q[m] = wring ? mk<R>(rmul(v.x, (R)wring[r]), rmul(v.y, (R)wring[r])) : v;
         }
         __syncthreads();
     }
@@ -993,17 +1023,17 @@ cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smoot
 }
 
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
-                                      cudaStream_t st)
+                                      const double *wring, cudaStream_t st)
 {
     return launch_two(ring_analysis_kernel<double, false>, ring_analysis_kernel<double, true>, P, true, nmaps, 0, st,
-                      map, q);
+                      map, q, wring);
 }
 
 cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
-                                      cudaStream_t st)
+                                      const double *wring, cudaStream_t st)
 {
     return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, 0, st,
-                      map, q);
+                      map, q, wring);
 }
 
 }  // namespace sht

@@ -44,6 +44,8 @@ struct sht_plan_s {
     int fp64_bc = 8;         // maps per CTA of the FP64 Legendre step
     int fp64_ring_g = 8;     // maps per CTA of the FP64 ring step
     void *lcache[4] = {};  // plan-time Lambda operand per tensor-core form (sht_lambda_cache)
+    std::vector<double> wring_h;  // pixel quadrature weight per ring (host copy)
+    double *wring_d = nullptr;    // the same on the device (DevPlan::wring)
     size_t lcache_bytes[4] = {};
     std::mutex mu;
 };
@@ -93,6 +95,7 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 
 struct Rings {
     std::vector<double> x, s, phi0;
+    std::vector<double> w;  // quadrature weight of each pixel of the ring (empty: none)
     std::vector<int> nphi, ps;
 };
 
@@ -123,6 +126,20 @@ void gl_geometry(int n, int nphi, Rings &R)
     if (n % 2) R.x[n / 2] = 0.0;
     R.s.resize(n);
     for (int i = 0; i < n; ++i) R.s[i] = std::sqrt((1.0 - R.x[i]) * (1.0 + R.x[i]));
+    // Gauss weight 2 / ((1 - x^2) P_n'(x)^2), times 2 pi / nphi per pixel
+    R.w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double z = R.x[i];
+        double pa = 1.0, pb = z;
+        for (int j = 2; j <= n; ++j) {
+            const double pc = ((2.0 * j - 1.0) * z * pb - (j - 1.0) * pa) / j;
+            pa = pb;
+            pb = pc;
+        }
+        const double pn = (n == 1) ? z : pb, pn1 = (n == 1) ? 1.0 : pa;
+        const double dp = n * (z * pn - pn1) / (z * z - 1.0);
+        R.w[i] = 2.0 / ((1.0 - z * z) * dp * dp) * (2.0 * kPi / nphi);
+    }
     R.nphi.assign(n, nphi);
     R.phi0.assign(n, 0.0);
     R.ps.assign(n, 0);
@@ -175,6 +192,7 @@ void healpix_geometry(int nside, Rings &R)
     }
     R.x[2 * nside - 1] = 0.0;  // equator
     R.s[2 * nside - 1] = 1.0;
+    R.w.assign(nr, 4.0 * kPi / (12.0 * dn * dn));  // equal-area pixels
 }
 
 // ----------------------------------------------------------------- tables --
@@ -495,6 +513,18 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, ofs, &d.ofs))) return rc;
     if ((rc = upload(p, R.phi0, &d.phi0))) return rc;
     if ((rc = upload(p, R.ps, &d.ps))) return rc;
+    {
+        // pixel quadrature weights: mutable (sht_set_ring_weights), zero when the grid has none
+        p->wring_h = R.w.empty() ? std::vector<double>(nr, 0.0) : R.w;
+        void *w = nullptr;
+        cudaError_t e = cudaMalloc(&w, (size_t)nr * sizeof(double));
+        if (e != cudaSuccess) return fail(SHT_ENOMEM, "cudaMalloc(weights): %s", cudaGetErrorString(e));
+        p->allocs.push_back(w);
+        e = cudaMemcpy(w, p->wring_h.data(), (size_t)nr * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(weights)");
+        p->wring_d = static_cast<double *>(w);
+        d.wring = p->wring_d;
+    }
     if ((rc = upload(p, twofs, &d.twofs))) return rc;
     if ((rc = upload(p, tw64, &d.tw64))) return rc;
     if ((rc = upload(p, tw32, &d.tw32))) return rc;
@@ -634,6 +664,71 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_mf launch");
     }
     return SHT_OK;
+}
+
+// FP64 alm2map of nbatch maps (caller holds the plan lock and the device).
+int alm2map_fp64(sht_plan_s *p, int nbatch, const double2 *alm, double *map, cudaStream_t st)
+{
+    int rc;
+    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
+    size_t chunk_sz = std::max<size_t>(1, max_ws_bytes() / per_map);
+    int chunk = (int)std::min<size_t>(chunk_sz, 32768);  // grid.y limit of the ring kernel
+    chunk = std::min(chunk, nbatch);
+    if ((rc = ensure_ws(p, per_map * chunk))) return rc;
+    double2 *delta = static_cast<double2 *>(p->ws);
+    for (int b0 = 0; b0 < nbatch; b0 += chunk) {
+        const int nb = std::min(chunk, nbatch - b0);
+        StageScope s1(p, SHT_STAGE_LEGENDRE, st);
+        cudaError_t e = sht::launch_legendre_fwd_fp64(p->dp, alm + (size_t)b0 * p->nalm, delta, nb, p->fp64_bc, st);
+        s1.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_fwd_fp64 launch");
+        StageScope s2(p, SHT_STAGE_RING, st);
+        e = sht::launch_ring_synth_fp64(p->dp, delta, map + (size_t)b0 * p->npix, nb, p->fp64_ring_g, st);
+        s2.done(e, sht::ring_launches(p->dp));
+        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp64 launch");
+    }
+    return SHT_OK;
+}
+
+// Quadrature-weighted ring analysis + Legendre sum (weights from the plan) or
+// the plain transpose (weights nullptr, cfac 2) of nbatch FP64 maps (caller
+// holds the plan lock and the device).
+int analysis_fp64(sht_plan_s *p, int nbatch, const double *map, double2 *alm, const double *wring, double cfac,
+                  cudaStream_t st)
+{
+    int rc;
+    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
+    size_t chunk_sz = std::max<size_t>(1, max_ws_bytes() / per_map);
+    int chunk = (int)std::min<size_t>(chunk_sz, 32768);
+    chunk = std::min(chunk, nbatch);
+    if ((rc = ensure_ws(p, per_map * chunk))) return rc;
+    double2 *q = static_cast<double2 *>(p->ws);
+    for (int b0 = 0; b0 < nbatch; b0 += chunk) {
+        const int nb = std::min(chunk, nbatch - b0);
+        StageScope s1(p, SHT_STAGE_ADJ_RING, st);
+        cudaError_t e = sht::launch_ring_analysis_fp64(p->dp, map + (size_t)b0 * p->npix, q, nb, wring, st);
+        s1.done(e, sht::ring_launches(p->dp));
+        if (e != cudaSuccess) return cuda_fail(e, "ring_analysis_fp64 launch");
+        StageScope s2(p, SHT_STAGE_ADJ_LEGENDRE, st);
+        e = sht::launch_legendre_adj_fp64(p->dp, q, alm + (size_t)b0 * p->nalm, nb, cfac, st);
+        s2.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_adj_fp64 launch");
+    }
+    return SHT_OK;
+}
+
+// Jacobi refinement helpers: r = y - s (in place in s), a += d.
+__global__ void residual_kernel(const double *__restrict__ y, double *__restrict__ s, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s[i] = y[i] - s[i];
+}
+__global__ void accumulate_kernel(double2 *__restrict__ a, const double2 *__restrict__ d, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        a[i].x += d[i].x;
+        a[i].y += d[i].y;
+    }
 }
 
 }  // namespace
@@ -959,27 +1054,8 @@ int sht_alm2map_batch(sht_plan_t p, int nbatch, const void *alm_dev, void *map_d
     if (prec != SHT_FP64) return alm2map_tc(p, nbatch, alm_dev, map_dev, prec, stream);
     std::lock_guard<std::mutex> lk(p->mu);
     DeviceGuard dg(p->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
-    size_t chunk_sz = std::max<size_t>(1, max_ws_bytes() / per_map);
-    int chunk = (int)std::min<size_t>(chunk_sz, 32768);  // grid.y limit of the ring kernel
-    chunk = std::min(chunk, nbatch);
-    if ((rc = ensure_ws(p, per_map * chunk))) return rc;
-    const double2 *alm = static_cast<const double2 *>(alm_dev);
-    double *map = static_cast<double *>(map_dev);
-    double2 *delta = static_cast<double2 *>(p->ws);
-    for (int b0 = 0; b0 < nbatch; b0 += chunk) {
-        const int nb = std::min(chunk, nbatch - b0);
-        StageScope s1(p, SHT_STAGE_LEGENDRE, st);
-        cudaError_t e = sht::launch_legendre_fwd_fp64(p->dp, alm + (size_t)b0 * p->nalm, delta, nb, p->fp64_bc, st);
-        s1.done(e);
-        if (e != cudaSuccess) return cuda_fail(e, "legendre_fwd_fp64 launch");
-        StageScope s2(p, SHT_STAGE_RING, st);
-        e = sht::launch_ring_synth_fp64(p->dp, delta, map + (size_t)b0 * p->npix, nb, p->fp64_ring_g, st);
-        s2.done(e, sht::ring_launches(p->dp));
-        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp64 launch");
-    }
-    return SHT_OK;
+    return alm2map_fp64(p, nbatch, static_cast<const double2 *>(alm_dev), static_cast<double *>(map_dev),
+                        static_cast<cudaStream_t>(stream));
 }
 
 int sht_alm2map(sht_plan_t p, const void *alm_dev, void *map_dev, int prec, void *stream)
@@ -1003,26 +1079,102 @@ int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, voi
         return fail(SHT_EUNSUPPORTED, "adjoint: %d ring pairs exceed the shared-memory state", p->npairs);
     std::lock_guard<std::mutex> lk(p->mu);
     DeviceGuard dg(p->device);
+    return analysis_fp64(p, nbatch, static_cast<const double *>(map_dev), static_cast<double2 *>(alm_dev), nullptr,
+                         2.0, static_cast<cudaStream_t>(stream));
+}
+
+int sht_map2alm_batch(sht_plan_t p, int nbatch, const void *map_dev, void *alm_dev, int prec, int niter,
+                      void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (nbatch < 0 || niter < 0) return fail(SHT_EINVAL, "nbatch < 0 or niter < 0");
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
+        return fail(SHT_EINVAL, "unknown precision %d", prec);
+    if (nbatch == 0) return SHT_OK;
+    if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
+    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "precision %d not built for map2alm", prec);
+    if (sht::legendre_adj_smem_bytes(p->dp, 4) == 0)
+        return fail(SHT_EUNSUPPORTED, "map2alm: %d ring pairs exceed the shared-memory state", p->npairs);
+    std::lock_guard<std::mutex> lk(p->mu);
+    bool any = false;
+    for (double w : p->wring_h) any = any || w > 0.0;
+    if (!any) return fail(SHT_EUNSUPPORTED, "the grid has no quadrature weights (sht_set_ring_weights)");
+    DeviceGuard dg(p->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
-    size_t chunk_sz = std::max<size_t>(1, max_ws_bytes() / per_map);
-    int chunk = (int)std::min<size_t>(chunk_sz, 32768);
-    chunk = std::min(chunk, nbatch);
-    if ((rc = ensure_ws(p, per_map * chunk))) return rc;
     const double *map = static_cast<const double *>(map_dev);
     double2 *alm = static_cast<double2 *>(alm_dev);
-    double2 *q = static_cast<double2 *>(p->ws);
-    for (int b0 = 0; b0 < nbatch; b0 += chunk) {
-        const int nb = std::min(chunk, nbatch - b0);
-        StageScope s1(p, SHT_STAGE_ADJ_RING, st);
-        cudaError_t e = sht::launch_ring_analysis_fp64(p->dp, map + (size_t)b0 * p->npix, q, nb, st);
-        s1.done(e, sht::ring_launches(p->dp));
-        if (e != cudaSuccess) return cuda_fail(e, "ring_analysis_fp64 launch");
-        StageScope s2(p, SHT_STAGE_ADJ_LEGENDRE, st);
-        e = sht::launch_legendre_adj_fp64(p->dp, q, alm + (size_t)b0 * p->nalm, nb, st);
-        s2.done(e);
-        if (e != cudaSuccess) return cuda_fail(e, "legendre_adj_fp64 launch");
+    if ((rc = analysis_fp64(p, nbatch, map, alm, p->wring_d, 1.0, st))) return rc;
+    if (niter == 0) return SHT_OK;
+    // Jacobi refinement: a += map2alm(y - alm2map(a)), niter times
+    void *res = nullptr, *da = nullptr;
+    const long long npx = (long long)nbatch * p->npix, nal = (long long)nbatch * p->nalm;
+    cudaError_t e = cudaMalloc(&res, (size_t)npx * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&da, (size_t)nal * sizeof(double2));
+    if (e != cudaSuccess) {
+        if (res) cudaFree(res);
+        if (da) cudaFree(da);
+        cudaGetLastError();
+        return fail(SHT_ENOMEM, "map2alm iteration buffers: %s", cudaGetErrorString(e));
     }
+    for (int it = 0; it < niter && rc == SHT_OK; ++it) {
+        rc = alm2map_fp64(p, nbatch, alm, static_cast<double *>(res), st);
+        if (rc) break;
+        residual_kernel<<<1184, 256, 0, st>>>(map, static_cast<double *>(res), npx);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            rc = cuda_fail(e, "residual launch");
+            break;
+        }
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        rc = analysis_fp64(p, nbatch, static_cast<const double *>(res), static_cast<double2 *>(da), p->wring_d, 1.0,
+                           st);
+        if (rc) break;
+        accumulate_kernel<<<1184, 256, 0, st>>>(alm, static_cast<const double2 *>(da), nal);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            rc = cuda_fail(e, "accumulate launch");
+            break;
+        }
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    // the buffers may still be in use by the launches just queued on st
+    const cudaError_t se = cudaStreamSynchronize(st);
+    cudaFree(res);
+    cudaFree(da);
+    if (rc == SHT_OK && se != cudaSuccess) rc = cuda_fail(se, "cudaStreamSynchronize");
+    return rc;
+}
+
+int sht_map2alm(sht_plan_t p, const void *map_dev, void *alm_dev, int prec, int niter, void *stream)
+{
+    return sht_map2alm_batch(p, 1, map_dev, alm_dev, prec, niter, stream);
+}
+
+int sht_set_ring_weights(sht_plan_t p, const double *w)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!w) return fail(SHT_EINVAL, "null weights");
+    for (int r = 0; r < p->nrings; ++r)
+        if (!(std::isfinite(w[r]) && w[r] >= 0.0)) return fail(SHT_EINVAL, "weight %d not finite and >= 0", r);
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaDeviceSynchronize();  // no launch may still read the old weights
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    e = cudaMemcpy(p->wring_d, w, (size_t)p->nrings * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(weights)");
+    p->wring_h.assign(w, w + p->nrings);
+    return SHT_OK;
+}
+
+int sht_ring_weights(sht_plan_t p, double *w)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!w) return fail(SHT_EINVAL, "null output");
+    std::copy(p->wring_h.begin(), p->wring_h.end(), w);
     return SHT_OK;
 }
 

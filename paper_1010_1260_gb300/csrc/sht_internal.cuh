@@ -39,6 +39,7 @@ struct DevPlan {
     const long long *ofs;    // [nrings] first pixel
     const double *phi0;      // [nrings]
     const int *ps;           // [nrings] phi0 = pi * ps / nphi, or -1 (arbitrary phi0)
+    const double *wring;     // [nrings] quadrature weight of each pixel of the ring (0: none)
     const long long *twofs;  // [nrings] offset of the ring's table in tw64 / tw32
     const double2 *tw64;     // per distinct nphi = n: e^{i pi q / n}, q in [0, 2n)
     const float2 *tw32;
@@ -99,13 +100,14 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
 
 // Ring step of the transpose: q[b][ring][m] = sum_j y_j e^{-i m phi_j}.
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
-                                      cudaStream_t st);
+                                      const double *wring, cudaStream_t st);
 cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
-                                      cudaStream_t st);
+                                      const double *wring, cudaStream_t st);
 
 // Legendre step of the transpose, FP64:
-//   g[b][idx(l, m)] = c_m sum_r lambda_lm(x_r) q[b][r][m],  c_0 = 1, c_m = 2.
-cudaError_t launch_legendre_adj_fp64(const DevPlan &P, const double2 *q, double2 *g, int nmaps,
+//   g[b][idx(l, m)] = c_m sum_r lambda_lm(x_r) q[b][r][m],  c_0 = 1, c_m = cfac for m > 0
+//   (cfac = 2: the real-linear transpose of alm2map; cfac = 1: the analysis sum).
+cudaError_t launch_legendre_adj_fp64(const DevPlan &P, const double2 *q, double2 *g, int nmaps, double cfac,
                                      cudaStream_t st);
 // Shared memory the FP64 adjoint Legendre kernel needs (0 if the plan has too many ring pairs).
 size_t legendre_adj_smem_bytes(const DevPlan &P, int bc);

@@ -87,13 +87,18 @@ def lib():
             L.sht_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_set_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_debug_withhold_stage.argtypes = [P, I]
+            L.sht_map2alm.argtypes = [P, V, V, I, I, V]
+            L.sht_map2alm_batch.argtypes = [P, I, V, V, I, I, V]
+            L.sht_set_ring_weights.argtypes = [P, V]
+            L.sht_ring_weights.argtypes = [P, V]
             L.sht_kernel_launches.argtypes = []
             L.sht_kernel_launches.restype = ctypes.c_ulonglong
             for f in ("sht_plan", "sht_plan_destroy", "sht_alm2map", "sht_map2alm_adjoint",
                       "sht_alm2map_batch", "sht_map2alm_adjoint_batch", "sht_profile",
                       "sht_profile_read", "sht_sync", "sht_multi_create", "sht_multi_alm2map",
                       "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
-                      "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage"):
+                      "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage", "sht_map2alm",
+                      "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -258,6 +263,34 @@ class Plan:
         """Test hook: the next tensor-core Legendre launch skips one stage's
         operand copies in its first CTA, so its bounded wait runs out."""
         check(lib().sht_debug_withhold_stage(self._h, int(stage)))
+
+    # ---------------------------------------------------------- analysis --
+    def map2alm(self, maps: torch.Tensor, niter: int = 0, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        """Quadrature-weighted analysis of float64 CUDA maps ([B, npix] or
+        [npix]) with ``niter`` Jacobi refinements (complex128 result)."""
+        if not (maps.is_cuda and maps.dtype == torch.float64):
+            raise TypeError("maps must be a CUDA float64 tensor")
+        single = maps.dim() == 1
+        y = maps.reshape(-1, self.npix).contiguous()
+        B = y.shape[0]
+        if out is None:
+            out = torch.empty((B, self.nalm), dtype=torch.complex128, device=maps.device)
+        check(lib().sht_map2alm_batch(self._h, B, y.data_ptr(), out.data_ptr(), PREC["fp64"], int(niter),
+                                      _stream_ptr(stream)))
+        return out.reshape(self.nalm) if single else out.reshape(B, self.nalm)
+
+    def ring_weights(self) -> np.ndarray:
+        """Pixel quadrature weight of every ring."""
+        w = np.empty(self.nrings, dtype=np.float64)
+        check(lib().sht_ring_weights(self._h, w.ctypes.data))
+        return w
+
+    def set_ring_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (self.nrings,):
+            raise ValueError("need %d weights" % self.nrings)
+        check(lib().sht_set_ring_weights(self._h, w.ctypes.data))
 
     def sync(self):
         """Wait for the plan's device; raise ShtError(SHT_ETIMEOUT) if a kernel

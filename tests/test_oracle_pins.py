@@ -271,6 +271,39 @@ def test_gl_round_trip_identity(oracle_mod):
     assert np.max(np.abs(back - want)) < 1e-12 * np.max(np.abs(want))
 
 
+def test_map2alm_gl_exact(oracle_mod):
+    # the weighted analysis inverts alm2map exactly on a Gauss-Legendre grid with
+    # n_rings = lmax + 1 and n_phi > 2 lmax (orthonormality + exact quadrature);
+    # a missing weight, conjugate or factor 1/2 for m > 0 breaks it
+    lmax = 40
+    grid = oracle_mod.gl_grid(41, 82)
+    alm = inputs.gaussian_alm(lmax, lmax, 7, nmaps=2, spectrum="white")
+    s = oracle_mod.alm2map(grid, lmax, lmax, alm)
+    back = oracle_mod.map2alm(grid, lmax, lmax, s)
+    ls, ms = inputs.lm_arrays(lmax, lmax)
+    want = alm.copy()
+    want[:, ms == 0] = want[:, ms == 0].real
+    assert np.max(np.abs(back - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_map2alm_healpix_monopole_and_dipole(oracle_mod):
+    # y = 1: the equal HEALPix pixel areas sum to 4 pi, so a_00 = 4 pi Y_00 =
+    # sqrt(4 pi) exactly; a_10 = 0 by north/south symmetry; y = cos(theta):
+    # a_10 = sum_p w_p cos^2(theta_p) sqrt(3 / 4 pi) -> sqrt(4 pi / 3) as nside grows
+    grid = oracle_mod.healpix_grid(8)
+    ones = np.ones((1, grid["npix"]))
+    a = oracle_mod.map2alm(grid, 4, 4, ones)[0]
+    assert abs(a[0] - np.sqrt(4 * np.pi)) < 1e-13
+    assert abs(a[1]) < 1e-13
+    w = oracle_mod.pixel_weights(grid)
+    assert abs(np.sum(w * grid["nphi"]) - 4 * np.pi) < 1e-13
+    z = np.repeat(grid["x"], grid["nphi"].astype(np.int64))[None, :]
+    assert abs(oracle_mod.map2alm(grid, 2, 2, z)[0][0]) < 1e-13
+    g32 = oracle_mod.healpix_grid(32)
+    z32 = np.repeat(g32["x"], g32["nphi"].astype(np.int64))[None, :]
+    assert abs(oracle_mod.map2alm(g32, 2, 2, z32)[0][1] - np.sqrt(4 * np.pi / 3)) < 1e-3
+
+
 # ------------------------------------------------------------------ adjoint --
 
 @pytest.mark.parametrize("grid_args", [("hp", 4), ("gl", (10, 21)), ("hp", 2)])
