@@ -433,6 +433,8 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
         return stage0 + s * C::STAGE_BYTES + (C::A_TILES + par * NPB + piece) * kTileBytes;
     };
     auto nstages_of = [&](int m) { return (L - m + 1 + C::STEPS - 1) / C::STEPS; };
+    // first stage of a work item (evanescent skip: whole 64-degree groups)
+    auto first_stage = [&](int item) { return P.skip_g ? P.skip_g[item] * C::GROUP : 0; };
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -469,20 +471,28 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
             const int m = item / nrb;
             const int pair = (item % nrb) * kRows + t;
             const bool live = pair < P.npairs;
+            const int s0 = first_stage(item);
             double x = 0.0, p0 = 0.0, p1 = 0.0;
             int k = 0;
             if (live) {
+                const size_t o = (size_t)m * P.npairs + pair;
                 x = P.pair_x[pair];
-                p1 = P.start_v[(size_t)m * P.npairs + pair];
-                k = P.start_k[(size_t)m * P.npairs + pair];
+                if (s0 > 0) {
+                    p0 = P.warm_p0[o];
+                    p1 = P.warm_p1[o];
+                    k = P.warm_k[o];
+                } else {
+                    p1 = P.start_v[o];
+                    k = P.start_k[o];
+                }
             }
             const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
             const int nst = nstages_of(m);
+            int l = m + s0 * C::STEPS;
             // A_{l+1} for the stage's degrees, one per lane, prefetched a stage ahead
             auto coef = [&](int lq) { return (lane < C::STEPS && lq <= L) ? __ldg(&P.coefA[mofs + (lq - m)]) : 0.0; };
-            double a_cur = coef(m + 1 + lane);
-            int l = m;
-            for (int i = 0; i < nst; ++i) {
+            double a_cur = coef(l + 1 + lane);
+            for (int i = s0; i < nst; ++i) {
                 const int s = (int)(gs % C::NS);
                 const uint32_t ph = (gs / C::NS) & 1u;
                 const double a_next = coef(m + (i + 1) * C::STEPS + 1 + lane);
@@ -509,7 +519,7 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             const int m = item / nrb;
             const int pair = (item % nrb) * kRows + row;
-            const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP;
+            const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP - first_stage(item) / C::GROUP;
             for (int g = 0; g < ngroups; ++g) {
                 const int set = (int)(gg & 1u);
                 ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
@@ -606,8 +616,9 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
                 const int m = item / nrb;
                 const unsigned char *blk = bbuf + (size_t)(seg_off[2 * m] / C::STEPS) * SB;
                 const int nst = nstages_of(m);
-                for (int i = 0; i < kPrefetch && i < nst; ++i) bulk_prefetch_l2(blk + (size_t)i * SB, SB);
-                for (int i = 0; i < nst; ++i) {
+                const int s0 = first_stage(item);
+                for (int i = s0; i < s0 + kPrefetch && i < nst; ++i) bulk_prefetch_l2(blk + (size_t)i * SB, SB);
+                for (int i = s0; i < nst; ++i) {
                     const int s = (int)(gs % C::NS);
                     const uint32_t ph = (gs / C::NS) & 1u;
                     if (i + kPrefetch < nst) bulk_prefetch_l2(blk + (size_t)(i + kPrefetch) * SB, SB);
@@ -639,7 +650,7 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const int m = item / nrb;
                 const int nst = nstages_of(m);
-                for (int i0 = 0; i0 < nst && ok; i0 += C::GROUP) {
+                for (int i0 = first_stage(item); i0 < nst && ok; i0 += C::GROUP) {
                     const int set = (int)(gg & 1u);
                     if (!mbar_wait(bar_set_empty(set), ((gg >> 1) & 1u) ^ 1u, &s_abort)) {
                         ok = false;
@@ -754,6 +765,8 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
         return stage0 + s * C::STAGE_BYTES + (C::A_TILES + par * NPB + piece) * kTileBytes;
     };
     auto nstages_of = [&](int m) { return (L - m + 1 + C::STEPS - 1) / C::STEPS; };
+    // first stage of a work item (evanescent skip: whole 64-degree groups)
+    auto first_stage = [&](int item) { return P.skip_g ? P.skip_g[item] * C::GROUP : 0; };
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -790,7 +803,7 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             const int m = item / nrb;
             const int pair = (item % nrb) * kRows + row;
-            const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP;
+            const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP - first_stage(item) / C::GROUP;
             for (int g = 0; g < ngroups; ++g) {
                 const int set = (int)(gg & 1u);
                 ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
@@ -873,7 +886,7 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
                 const int nst = nstages_of(m);
                 const unsigned char *bblk = bbuf + st0 * SB;
                 const unsigned char *ablk = acache + (st0 * nrb + (size_t)(item % nrb) * nst) * SA;
-                for (int i = 0; i < nst; ++i) {
+                for (int i = first_stage(item); i < nst; ++i) {
                     const int s = (int)(gs % NS);
                     const uint32_t ph = (gs / NS) & 1u;
                     if ((int)gs == withhold && blockIdx.x == 0) {
@@ -904,7 +917,7 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const int m = item / nrb;
                 const int nst = nstages_of(m);
-                for (int i0 = 0; i0 < nst && ok; i0 += C::GROUP) {
+                for (int i0 = first_stage(item); i0 < nst && ok; i0 += C::GROUP) {
                     const int set = (int)(gg & 1u);
                     if (!mbar_wait(bar_set_empty(set), ((gg >> 1) & 1u) ^ 1u, &s_abort)) {
                         ok = false;
@@ -1016,6 +1029,79 @@ cudaError_t run_prep(const DevPlan &P, const TcWork &W, const double2 *alm, int 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ evanescent skip --
+// Per (m, ring block): the first 64-degree group containing a degree whose
+// recurrence value is representable in FP32 (exponent k = 0 and
+// |p_l| >= 2^-126) in any ring of the block, and each ring's recurrence state
+// at the start of that group.  The recurrence is the producers' (same fused
+// operations), rescaled as soon as |p| > 2^256 while k < 0; rescaling by 2^-512
+// is exact, so a producer that starts from this state computes the same values
+// as one that starts at degree m, and the values it skips would all have
+// rounded to zero.  At least one group is kept per item.  One CTA of 128
+// threads per (ring block, m).
+__global__ void __launch_bounds__(kRows)
+warm_start_kernel(const DevPlan P, int *__restrict__ skip_g, double *__restrict__ wp0, double *__restrict__ wp1,
+                  int *__restrict__ wk)
+{
+    __shared__ int s_first;
+    const int L = P.lmax;
+    const int nrb = (P.npairs + kRows - 1) / kRows;
+    const int rb = blockIdx.x;
+    const int m = blockIdx.y;
+    const int t = threadIdx.x;
+    const int pair = rb * kRows + t;
+    const bool live = pair < P.npairs;
+    const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
+    const double x = live ? P.pair_x[pair] : 0.0;
+    const double v0 = live ? P.start_v[(size_t)m * P.npairs + pair] : 0.0;
+    const int k0 = live ? P.start_k[(size_t)m * P.npairs + pair] : 0;
+    if (t == 0) s_first = L + 1;
+    __syncthreads();
+    // pass 1: first representable degree of this ring
+    {
+        double p0 = 0.0, p1 = v0;
+        int k = k0;
+        for (int l = m; l <= L && live; ++l) {
+            if (k == 0 && fabs(p1) >= 0x1p-126) {
+                atomicMin(&s_first, l);
+                break;
+            }
+            const double a = (l + 1 <= L) ? __ldg(&P.coefA[mofs + (l + 1 - m)]) : 0.0;
+            const double tt = fma(fma(a, x, 0.0), p1, -p0);
+            p0 = p1;
+            p1 = tt;
+            if (k < 0 && above_hi(p1)) {
+                p1 *= 0x1p-512;
+                p0 *= 0x1p-512;
+                k += 1;
+            }
+        }
+    }
+    __syncthreads();
+    const int ngroups = (L - m + 1 + 63) / 64;
+    const int g0 = min((s_first - m) / 64, ngroups - 1);
+    if (t == 0) skip_g[(size_t)m * nrb + rb] = g0;
+    // pass 2: the state at degree m + 64 g0
+    if (!live) return;
+    double p0 = 0.0, p1 = v0;
+    int k = k0;
+    for (int l = m; l < m + 64 * g0; ++l) {
+        const double a = __ldg(&P.coefA[mofs + (l + 1 - m)]);
+        const double tt = fma(fma(a, x, 0.0), p1, -p0);
+        p0 = p1;
+        p1 = tt;
+        if (k < 0 && above_hi(p1)) {
+            p1 *= 0x1p-512;
+            p0 *= 0x1p-512;
+            k += 1;
+        }
+    }
+    const size_t o = (size_t)m * P.npairs + pair;
+    wp0[o] = p0;
+    wp1[o] = p1;
+    wk[o] = k;
+}
+
 // ------------------------------------------------- plan-time Lambda operand --
 // The A tiles of every (m, ring block rb, stage i) exactly as the producers
 // write them into shared memory (same recurrence, same rounding, same pieces,
@@ -1036,19 +1122,28 @@ lambda_build_kernel(const DevPlan P, const int *__restrict__ seg_off, unsigned c
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int pair = rb * kRows + t;
+    // stages before the item's first (evanescent skip) are never read: not written
+    const int s0 = P.skip_g ? P.skip_g[m * nrb + rb] * (64 / STEPS) : 0;
     double x = 0.0, p0 = 0.0, p1 = 0.0;
     int k = 0;
     if (pair < P.npairs) {
+        const size_t o = (size_t)m * P.npairs + pair;
         x = P.pair_x[pair];
-        p1 = P.start_v[(size_t)m * P.npairs + pair];
-        k = P.start_k[(size_t)m * P.npairs + pair];
+        if (s0 > 0) {
+            p0 = P.warm_p0[o];
+            p1 = P.warm_p1[o];
+            k = P.warm_k[o];
+        } else {
+            p1 = P.start_v[o];
+            k = P.start_k[o];
+        }
     }
     const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
     const int nst = (L - m + 1 + STEPS - 1) / STEPS;
     unsigned char *blk = aout + ((size_t)(seg_off[2 * m] / STEPS) * nrb + (size_t)rb * nst) * SA;
     auto coef = [&](int lq) { return (lane < STEPS && lq <= L) ? __ldg(&P.coefA[mofs + (lq - m)]) : 0.0; };
-    int l = m;
-    for (int i = 0; i < nst; ++i) {
+    int l = m + s0 * STEPS;
+    for (int i = s0; i < nst; ++i) {
         const double a_cur = coef(l + 1 + lane);
         if (__any_sync(0xffffffffu, k < 0))
             produce_stage<BF16, NPA, true>(blk + (size_t)i * SA, t, x, a_cur, l, L, p0, p1, k);
@@ -1109,6 +1204,14 @@ size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec)
     if (prec == SHT_BF16X3_TC) return (size_t)(W.kall_bf16 / 32) * nrb * 2 * 2 * kTileBytes;
     if (prec == SHT_BF16X6_TC) return (size_t)(W.kall_bf16 / 32) * nrb * 2 * 3 * kTileBytes;
     return 0;
+}
+
+cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,
+                              cudaStream_t st)
+{
+    dim3 grid((P.npairs + kRows - 1) / kRows, P.mmax + 1);
+    warm_start_kernel<<<grid, kRows, 0, st>>>(P, skip_g, warm_p0, warm_p1, warm_k);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, void *out, cudaStream_t st)

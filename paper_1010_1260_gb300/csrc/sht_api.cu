@@ -44,6 +44,8 @@ struct sht_plan_s {
     int fp64_bc = 8;         // maps per CTA of the FP64 Legendre step
     int fp64_ring_g = 8;     // maps per CTA of the FP64 ring step
     void *lcache[4] = {};  // plan-time Lambda operand per tensor-core form (sht_lambda_cache)
+    bool skip_evanescent = true;  // tensor-core forms: start items after their all-zero degrees
+    void *warm = nullptr;         // the skip tables (one allocation), built on first use
     std::vector<double> wring_h;  // pixel quadrature weight per ring (host copy)
     double *wring_d = nullptr;    // the same on the device (DevPlan::wring)
     size_t lcache_bytes[4] = {};
@@ -224,6 +226,7 @@ void free_plan(sht_plan_s *p)
         if (p->tc.bbuf) cudaFree(p->tc.bbuf);
         for (void *c : p->lcache)
             if (c) cudaFree(c);
+        if (p->warm) cudaFree(p->warm);
         for (auto &e : p->prof_pending) {
             cudaEventDestroy(e.a);
             cudaEventDestroy(e.b);
@@ -630,6 +633,52 @@ int check_plan(sht_plan_t p)
     return SHT_OK;
 }
 
+// Evanescent-skip tables of the tensor-core forms: built on first use (one
+// FP64 pass over the recurrence, synchronous), or detached when disabled.
+int ensure_warm(sht_plan_s *p, cudaStream_t st)
+{
+    sht::DevPlan &d = p->dp;
+    if (!p->skip_evanescent) {
+        d.skip_g = nullptr;
+        d.warm_p0 = d.warm_p1 = nullptr;
+        d.warm_k = nullptr;
+        return SHT_OK;
+    }
+    const size_t nrb = (size_t)((p->npairs + 127) / 128), M1 = (size_t)p->mmax + 1;
+    const size_t nst = M1 * (size_t)p->npairs;
+    const size_t b_g = (M1 * nrb * sizeof(int) + 255) / 256 * 256;
+    const size_t b_p = nst * sizeof(double);
+    if (!p->warm) {
+        cudaError_t e = cudaMalloc(&p->warm, b_g + 2 * b_p + nst * sizeof(int));
+        if (e != cudaSuccess) {
+            p->warm = nullptr;
+            cudaGetLastError();
+            return fail(SHT_ENOMEM, "skip tables: %s", cudaGetErrorString(e));
+        }
+        char *b = static_cast<char *>(p->warm);
+        int *g = reinterpret_cast<int *>(b);
+        double *w0 = reinterpret_cast<double *>(b + b_g), *w1 = reinterpret_cast<double *>(b + b_g + b_p);
+        int *wk = reinterpret_cast<int *>(b + b_g + 2 * b_p);
+        d.skip_g = nullptr;  // the build itself starts every item at degree m
+        e = sht::launch_warm_start(d, g, w0, w1, wk, st);
+        if (e == cudaSuccess) {
+            g_launches.fetch_add(1, std::memory_order_relaxed);
+            e = cudaStreamSynchronize(st);
+        }
+        if (e != cudaSuccess) {
+            cudaFree(p->warm);
+            p->warm = nullptr;
+            return cuda_fail(e, "warm_start");
+        }
+    }
+    char *b = static_cast<char *>(p->warm);
+    d.skip_g = reinterpret_cast<const int *>(b);
+    d.warm_p0 = reinterpret_cast<const double *>(b + b_g);
+    d.warm_p1 = reinterpret_cast<const double *>(b + b_g + b_p);
+    d.warm_k = reinterpret_cast<const int *>(b + b_g + 2 * b_p);
+    return SHT_OK;
+}
+
 // Precision forms: FP64 recurrence (or the plan-time Lambda operand, when
 // cached) + tensor-core contraction (groups of at most 64 maps), FP32 Delta,
 // FP32 ring step, float32 maps.
@@ -643,6 +692,7 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
     const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(float2);
     if ((rc = ensure_ws(p, per_map * group))) return rc;
     if ((rc = ensure_tc(p, prec))) return rc;
+    if ((rc = ensure_warm(p, st))) return rc;
     const double2 *alm = static_cast<const double2 *>(alm_dev);
     float *map = static_cast<float *>(map_dev);
     float2 *delta = static_cast<float2 *>(p->ws);  // [ring][m][map]
@@ -838,6 +888,7 @@ int sht_lambda_cache(sht_plan_t p, int prec, int enable, void *stream)
         return SHT_OK;
     }
     if (p->lcache[prec]) return SHT_OK;
+    if ((rc = ensure_warm(p, st))) return rc;
     const size_t need = sht::tc_lambda_bytes(p->dp, p->tc, prec);
     void *buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, need);
@@ -845,7 +896,10 @@ int sht_lambda_cache(sht_plan_t p, int prec, int enable, void *stream)
         cudaGetLastError();
         return fail(SHT_ENOMEM, "Lambda operand cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
     }
-    e = sht::launch_lambda_build(p->dp, p->tc, prec, buf, st);
+    // zero first: the stages the evanescent skip leaves unwritten hold exact
+    // zeros, so the operand is valid with the skip on or off
+    e = cudaMemsetAsync(buf, 0, need, st);
+    if (e == cudaSuccess) e = sht::launch_lambda_build(p->dp, p->tc, prec, buf, st);
     if (e == cudaSuccess) {
         g_launches.fetch_add(1, std::memory_order_relaxed);
         e = cudaStreamSynchronize(st);
@@ -993,6 +1047,16 @@ int sht_tiles(sht_plan_t p, int *out, int n)
     if (!out || n < 0) return fail(SHT_EINVAL, "null output or n < 0");
     const int v[5] = {p->ring_g[0], p->ring_g[1], p->ring_nt, p->fp64_bc, p->fp64_ring_g};
     for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
+    return SHT_OK;
+}
+
+int sht_skip_evanescent(sht_plan_t p, int enable)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->skip_evanescent = enable != 0;
     return SHT_OK;
 }
 

@@ -40,6 +40,14 @@ struct DevPlan {
     const double *phi0;      // [nrings]
     const int *ps;           // [nrings] phi0 = pi * ps / nphi, or -1 (arbitrary phi0)
     const double *wring;     // [nrings] quadrature weight of each pixel of the ring (0: none)
+    // Evanescent skip of the tensor-core forms (nullptr: none): work item
+    // (m, ring block rb) starts at degree m + 64 skip_g[m nrb + rb], where the
+    // recurrence state of pair r is (warm_p0, warm_p1, warm_k)[m npairs + r]
+    // (p_{l-1}, p_l, exponent); every value below that degree, in every ring of
+    // the block, rounds to zero in FP32.
+    const int *skip_g;
+    const double *warm_p0, *warm_p1;
+    const int *warm_k;
     const long long *twofs;  // [nrings] offset of the ring's table in tw64 / tw32
     const double2 *tw64;     // per distinct nphi = n: e^{i pi q / n}, q in [0, 2n)
     const float2 *tw32;
@@ -138,6 +146,9 @@ cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const do
 cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, const void *acache, float2 *delta,
                            int nmaps, cudaStream_t st);
 size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
+// Fill the evanescent-skip tables (skip_g: [mmax+1][nrb]; warm_*: [mmax+1][npairs]).
+cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,
+                              cudaStream_t st);
 cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, void *out, cudaStream_t st);
 
 // Kernels one ring-step launch issues (one per non-empty ring list).

@@ -87,6 +87,7 @@ def lib():
             L.sht_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_set_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_debug_withhold_stage.argtypes = [P, I]
+            L.sht_skip_evanescent.argtypes = [P, I]
             L.sht_map2alm.argtypes = [P, V, V, I, I, V]
             L.sht_map2alm_batch.argtypes = [P, I, V, V, I, I, V]
             L.sht_set_ring_weights.argtypes = [P, V]
@@ -98,7 +99,7 @@ def lib():
                       "sht_profile_read", "sht_sync", "sht_multi_create", "sht_multi_alm2map",
                       "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
                       "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage", "sht_map2alm",
-                      "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights"):
+                      "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -258,6 +259,10 @@ class Plan:
             cur[k] = int(v)
         vals = (ctypes.c_int * 5)(*[cur[k] for k in self.TILE_NAMES])
         check(lib().sht_set_tiles(self._h, vals, 5))
+
+    def skip_evanescent(self, enable: bool = True):
+        """Tensor-core forms: start work items after their all-zero degrees."""
+        check(lib().sht_skip_evanescent(self._h, 1 if enable else 0))
 
     def debug_withhold_stage(self, stage: int):
         """Test hook: the next tensor-core Legendre launch skips one stage's
