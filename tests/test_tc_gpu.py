@@ -81,3 +81,38 @@ def test_tc_batch_equals_singles(sht):
         single = plan.alm2map(alm[b], "fp32_tc")
         assert torch.allclose(single, batch[b], rtol=0, atol=1e-6 * float(batch[b].abs().max()))
     plan.sync()
+
+
+def _rings_case():
+    # generic rings: odd and even lengths, a prime length 61 (Bluestein, N = 61),
+    # 2 x 31 (Bluestein, N = 31), arbitrary first azimuths (no table phases)
+    theta = np.array([0.21, 0.47, 0.8, 1.1, 1.4, 1.7, 2.05, 2.5, 2.9])
+    nphi = np.array([7, 61, 62, 90, 125, 124, 64, 33, 12], dtype=np.int32)
+    phi0 = np.array([0.013, 0.4, 1.7, 0.0, 2.2, 0.31, 0.05, 3.0, 0.77])
+    return theta, nphi, phi0
+
+
+@pytest.mark.parametrize("prec", ["fp32_tc", "bf16x6_tc"])
+@pytest.mark.parametrize("gl_odd", [False, True])
+def test_tc_odd_lengths_and_generic_rings(oracle_mod, sht, prec, gl_odd):
+    if gl_odd:
+        lmax, nmaps = 30, 3
+        og, sg = oracle_mod.gl_grid(31, 61), sht.gl(31, 61)       # odd n: full-length complex DFT
+    else:
+        lmax, nmaps = 40, 5
+        theta, nphi, phi0 = _rings_case()
+        og, sg = oracle_mod.rings_grid(theta, nphi, phi0), sht.rings(theta, nphi, phi0)
+    alm = inputs.batch_alm(lmax, lmax, 400 + lmax, nmaps)
+    plan = sht.Plan(sg, lmax)
+    got = plan.alm2map(torch.from_numpy(alm).cuda(), prec)
+    plan.sync()
+    want = oracle_mod.alm2map(og, lmax, lmax, alm)
+    g = got.double().cpu().numpy()
+    errs = [_rl2(g[b], want[b]) for b in range(nmaps)]
+    assert max(errs) < TOL[prec], errs
+    # every tile shape gives the same maps on these rings too
+    for gs, gb, nt in ((1, 1, 256), (4, 2, 512)):
+        plan.set_tiles(ring_maps_smooth=gs, ring_maps_bluestein=gb, ring_threads=nt)
+        again = plan.alm2map(torch.from_numpy(alm).cuda(), prec)
+        plan.sync()
+        assert torch.equal(again, got)
