@@ -132,10 +132,14 @@ __device__ int factorize(int N, int *rad)
 //   Y[(j/Ns) Ns R + j%Ns + q Ns] = sum_r X[j + r N/R] w_{Ns R}^{r (j%Ns)} w_R^{r q}.
 // WG: W is a global table read through the read-only cache with element
 // stride wst (w_N^q = W[q wst]) instead of a shared-memory table.
-template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads>
+// PAD: the buffers hold element i at i + i / 16 (one unused slot per 16
+// elements), which makes the strided stores of the first passes free of
+// shared-memory bank conflicts.
+template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads, bool PAD = false>
 __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, const int npass, const int gs = 0,
                       const int wst = 1)
 {
+    auto PI = [](int i) { return PAD ? i + (i >> 4) : i; };
     const int tid = threadIdx.x;
     const R sg = INV ? (R)1 : (R)-1;
     auto tw = [&](int q) {
@@ -178,7 +182,7 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 #pragma unroll
                 for (int gm = 0; gm < G; ++gm)
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                    for (int r = 0; r < 8; ++r) v[gm][r] = src[gm * gs + PI(j + r * NR)];
                 if (kk) {
                     const int e = kk * tscale;
 #pragma unroll
@@ -201,22 +205,22 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
                     b[1] = mk<R>(rmul(c8, b[1].x - sg * b[1].y), rmul(c8, b[1].y + sg * b[1].x));
                     b[2] = muli(b[2]);
                     b[3] = mk<R>(rmul(c8, -b[3].x - sg * b[3].y), rmul(c8, sg * b[3].x - b[3].y));
-                    C *d = dst + gm * gs + o;
+                    C *d = dst + gm * gs;
                     {
                         const C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
                         const C s13 = cadd(a[1], a[3]), d13 = muli(csub(a[1], a[3]));
-                        d[0] = cadd(s02, s13);
-                        d[2 * Ns] = cadd(d02, d13);
-                        d[4 * Ns] = csub(s02, s13);
-                        d[6 * Ns] = csub(d02, d13);
+                        d[PI(o)] = cadd(s02, s13);
+                        d[PI(o + 2 * Ns)] = cadd(d02, d13);
+                        d[PI(o + 4 * Ns)] = csub(s02, s13);
+                        d[PI(o + 6 * Ns)] = csub(d02, d13);
                     }
                     {
                         const C s02 = cadd(b[0], b[2]), d02 = csub(b[0], b[2]);
                         const C s13 = cadd(b[1], b[3]), d13 = muli(csub(b[1], b[3]));
-                        d[Ns] = cadd(s02, s13);
-                        d[3 * Ns] = cadd(d02, d13);
-                        d[5 * Ns] = csub(s02, s13);
-                        d[7 * Ns] = csub(d02, d13);
+                        d[PI(o + Ns)] = cadd(s02, s13);
+                        d[PI(o + 3 * Ns)] = cadd(d02, d13);
+                        d[PI(o + 5 * Ns)] = csub(s02, s13);
+                        d[PI(o + 7 * Ns)] = csub(d02, d13);
                     }
                 }
             }
@@ -230,17 +234,17 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
                 C v[G][2];
 #pragma unroll
                 for (int gm = 0; gm < G; ++gm) {
-                    v[gm][0] = src[gm * gs + j];
-                    v[gm][1] = src[gm * gs + j + NR];
+                    v[gm][0] = src[gm * gs + PI(j)];
+                    v[gm][1] = src[gm * gs + PI(j + NR)];
                 }
                 const C w1 = kk ? tw(kk * tscale) : mk<R>(1, 0);
                 const int o = g * Ns * 2 + kk;
 #pragma unroll
                 for (int gm = 0; gm < G; ++gm) {
                     const C v1 = kk ? cmul(v[gm][1], w1) : v[gm][1];
-                    C *d = dst + gm * gs + o;
-                    d[0] = cadd(v[gm][0], v1);
-                    d[Ns] = csub(v[gm][0], v1);
+                    C *d = dst + gm * gs;
+                    d[PI(o)] = cadd(v[gm][0], v1);
+                    d[PI(o + Ns)] = csub(v[gm][0], v1);
                 }
             }
         } else if (Rr == 4) {
@@ -254,7 +258,7 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 #pragma unroll
                 for (int gm = 0; gm < G; ++gm)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                    for (int r = 0; r < 4; ++r) v[gm][r] = src[gm * gs + PI(j + r * NR)];
                 if (kk) {
                     const int e = kk * tscale;
 #pragma unroll
@@ -270,11 +274,11 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
                     // radix 4 with w_4 = sg * i
                     const C a0 = cadd(v[gm][0], v[gm][2]), a1 = csub(v[gm][0], v[gm][2]);
                     const C a2 = cadd(v[gm][1], v[gm][3]), a3 = muli(csub(v[gm][1], v[gm][3]));
-                    C *d = dst + gm * gs + o;
-                    d[0] = cadd(a0, a2);
-                    d[Ns] = cadd(a1, a3);
-                    d[2 * Ns] = csub(a0, a2);
-                    d[3 * Ns] = csub(a1, a3);
+                    C *d = dst + gm * gs;
+                    d[PI(o)] = cadd(a0, a2);
+                    d[PI(o + Ns)] = cadd(a1, a3);
+                    d[PI(o + 2 * Ns)] = csub(a0, a2);
+                    d[PI(o + 3 * Ns)] = csub(a1, a3);
                 }
             }
         } else if (Rr == 3) {
@@ -290,7 +294,7 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 #pragma unroll
                 for (int gm = 0; gm < G; ++gm)
 #pragma unroll
-                    for (int r = 0; r < 3; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                    for (int r = 0; r < 3; ++r) v[gm][r] = src[gm * gs + PI(j + r * NR)];
                 if (kk) {
                     const int e = kk * tscale;
                     w[1] = tw(e);
@@ -307,10 +311,10 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
                     const C t2 = csub(v[gm][1], v[gm][2]);
                     const C m1 = mk<R>(rfma(c3, t1.x, v[gm][0].x), rfma(c3, t1.y, v[gm][0].y));
                     const C m2 = mk<R>(-rmul(s3, t2.y), rmul(s3, t2.x));  // i s3 (v1 - v2)
-                    C *d = dst + gm * gs + o;
-                    d[0] = cadd(v[gm][0], t1);
-                    d[Ns] = cadd(m1, m2);
-                    d[2 * Ns] = csub(m1, m2);
+                    C *d = dst + gm * gs;
+                    d[PI(o)] = cadd(v[gm][0], t1);
+                    d[PI(o + Ns)] = cadd(m1, m2);
+                    d[PI(o + 2 * Ns)] = csub(m1, m2);
                 }
             }
         } else if (Rr == 5) {
@@ -328,7 +332,7 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 #pragma unroll
                 for (int gm = 0; gm < G; ++gm)
 #pragma unroll
-                    for (int r = 0; r < 5; ++r) v[gm][r] = src[gm * gs + j + r * NR];
+                    for (int r = 0; r < 5; ++r) v[gm][r] = src[gm * gs + PI(j + r * NR)];
                 if (kk) {
                     const int e = kk * tscale;
 #pragma unroll
@@ -349,12 +353,12 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
                     // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
                     const C n1 = mk<R>(-rfma(s1, b1.y, rmul(s2, b2.y)), rfma(s1, b1.x, rmul(s2, b2.x)));
                     const C n2 = mk<R>(-rfma(s2, b1.y, -rmul(s1, b2.y)), rfma(s2, b1.x, -rmul(s1, b2.x)));
-                    C *d = dst + gm * gs + o;
-                    d[0] = cadd(v0, cadd(a1, a2));
-                    d[Ns] = cadd(m1, n1);
-                    d[2 * Ns] = cadd(m2, n2);
-                    d[3 * Ns] = csub(m2, n2);
-                    d[4 * Ns] = csub(m1, n1);
+                    C *d = dst + gm * gs;
+                    d[PI(o)] = cadd(v0, cadd(a1, a2));
+                    d[PI(o + Ns)] = cadd(m1, n1);
+                    d[PI(o + 2 * Ns)] = cadd(m2, n2);
+                    d[PI(o + 3 * Ns)] = csub(m2, n2);
+                    d[PI(o + 4 * Ns)] = csub(m1, n1);
                 }
             }
         } else {
@@ -369,14 +373,14 @@ __device__ C *stockham(C *src, C *dst, const int N, const C *W, const int *rad, 
 #pragma unroll
                 for (int gm = 0; gm < G; ++gm) {
                     const C *sx = src + gm * gs;
-                    C acc = sx[j];
+                    C acc = sx[PI(j)];
                     int idx = e;
                     for (int rr = 1; rr < Rr; ++rr) {
-                        acc = cadd(acc, cmul(sx[j + rr * NR], tw(idx)));
+                        acc = cadd(acc, cmul(sx[PI(j + rr * NR)], tw(idx)));
                         idx += e;
                         if (idx >= N) idx -= N;
                     }
-                    dst[gm * gs + g * Ns * Rr + kk + q * Ns] = acc;
+                    dst[gm * gs + PI(g * Ns * Rr + kk + q * Ns)] = acc;
                 }
             }
         }
@@ -409,41 +413,43 @@ __device__ __forceinline__ C blue_chirp(const C *__restrict__ T, int n, int N, i
 
 // PRE_POST = false: the caller has already multiplied x by the chirp (and
 // zero-filled a[N..Mb)), and multiplies the result by the chirp itself.
-template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads, bool PRE_POST = true>
+template <bool INV, typename R, typename C, int G = 1, bool WG = false, int NT = kThreads, bool PRE_POST = true,
+          bool PAD = false>
 __device__ C *bluestein(C *a, C *b, const C *W2, const C *__restrict__ Bh, const C *__restrict__ T, int n, int N,
                         int Mb, const int *rad2, int np2, const int gs = 0, const int wst = 1)
 {
     const int tid = threadIdx.x;
     auto chirp = [&](int j) { return blue_chirp<INV>(T, n, N, j); };
+    auto PI = [](int i) { return PAD ? i + (i >> 4) : i; };
     if (PRE_POST) {
         for (int j = tid; j < Mb; j += NT) {
             const C c = (j < N) ? chirp(j) : mk<R>(0, 0);
 #pragma unroll
             for (int gm = 0; gm < G; ++gm) {
                 C *ax = a + (size_t)gm * gs;
-                ax[j] = (j < N) ? cmul(ax[j], c) : c;
+                ax[PI(j)] = (j < N) ? cmul(ax[PI(j)], c) : c;
             }
         }
         __syncthreads();
     }
-    C *f = stockham<false, R, C, G, WG, NT>(a, b, Mb, W2, rad2, np2, gs, wst);
+    C *f = stockham<false, R, C, G, WG, NT, PAD>(a, b, Mb, W2, rad2, np2, gs, wst);
     for (int k = tid; k < Mb; k += NT) {
         const C h = INV ? Bh[k] : cconj(Bh[k == 0 ? 0 : Mb - k]);
 #pragma unroll
         for (int gm = 0; gm < G; ++gm) {
             C *fx = f + (size_t)gm * gs;
-            fx[k] = cmul(fx[k], h);
+            fx[PI(k)] = cmul(fx[PI(k)], h);
         }
     }
     __syncthreads();
-    C *y = stockham<true, R, C, G, WG, NT>(f, (f == a) ? b : a, Mb, W2, rad2, np2, gs, wst);
+    C *y = stockham<true, R, C, G, WG, NT, PAD>(f, (f == a) ? b : a, Mb, W2, rad2, np2, gs, wst);
     if (PRE_POST) {
         for (int k = tid; k < N; k += NT) {
             const C c = chirp(k);
 #pragma unroll
             for (int gm = 0; gm < G; ++gm) {
                 C *yx = y + (size_t)gm * gs;
-                yx[k] = cmul(yx[k], c);
+                yx[PI(k)] = cmul(yx[PI(k)], c);
             }
         }
         __syncthreads();
@@ -601,9 +607,11 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
     const int gn = min(G, nmaps - b0);  // maps in this CTA
     const int r = BLUE ? P.rings_blue[li] : P.rings_smooth[li];
     const int cap = BLUE ? P.blue_cap : P.fft_cap;
-    C *A0 = reinterpret_cast<C *>(smem_raw);  // map g: A at A0 + g cap, B at A0 + (G + g) cap
-    C *B0 = A0 + G * cap;
-    const int gs = cap;
+    const int capP = cap + (cap >> 4) + 1;      // padded buffer (element i at i + i / 16)
+    auto PI = [](int i) { return i + (i >> 4); };
+    C *A0 = reinterpret_cast<C *>(smem_raw);  // map g: A at A0 + g capP, B at A0 + (G + g) capP
+    C *B0 = A0 + G * capP;
+    const int gs = capP;
     const int tid = threadIdx.x;
     const int n = P.nphi[r];
     const int M = P.mmax;
@@ -709,7 +717,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
             }
 #pragma unroll
             for (int g = 0; g < G; ++g)
-                if (g < gn) A0[g * cap + k] = acc[g];
+                if (g < gn) A0[g * capP + PI(k)] = acc[g];
         }
     } else {
         // Delta too long to stage: Delta from global memory
@@ -745,7 +753,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
             }
 #pragma unroll
             for (int g = 0; g < G; ++g)
-                if (g < gn) A0[g * cap + k] = acc[g];
+                if (g < gn) A0[g * capP + PI(k)] = acc[g];
             pk += dpk;
             if (pk >= n2) pk -= n2;
         }
@@ -756,39 +764,39 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict
     //    (Bluestein rings: times the chirp, and zero up to the convolution length Mb)
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const C *F = A0 + g * cap;
-        C *Bg = B0 + g * cap;
+        const C *F = A0 + g * capP;
+        C *Bg = B0 + g * capP;
 #pragma unroll 4
         for (int k = tid; k < N; k += NT) {
             C z;
             if (even) {
-                const C f = F[k];
-                const C h = cconj(F[N - k]);
+                const C f = F[PI(k)];
+                const C h = cconj(F[PI(N - k)]);
                 const C w = T[2 * k];  // e^{2 pi i k / n}
                 z = cadd(cadd(f, h), cmuli(cmul(w, csub(f, h))));
             } else {
-                z = (k < nb) ? F[k] : cconj(F[N - k]);
+                z = (k < nb) ? F[PI(k)] : cconj(F[PI(N - k)]);
             }
-            Bg[k] = BLUE ? cmul(z, blue_chirp<true>(T, n, N, k)) : z;
+            Bg[PI(k)] = BLUE ? cmul(z, blue_chirp<true>(T, n, N, k)) : z;
         }
         if (BLUE)
-            for (int k = N + tid; k < Mb; k += NT) Bg[k] = mk<R>(0, 0);
+            for (int k = N + tid; k < Mb; k += NT) Bg[PI(k)] = mk<R>(0, 0);
     }
     __syncthreads();
 
     // 3. inverse complex DFT of length N of every map
     // (a CTA holding fewer than G maps transforms its spare buffers too,
     // harmlessly, and never stores them)
-    C *src = BLUE ? bluestein<true, R, C, G, true, NT, false>(B0, A0, w2_table<R>(P), bhat_table<R>(P) + P.blue_ofs[r], T, n,
+    C *src = BLUE ? bluestein<true, R, C, G, true, NT, false, true>(B0, A0, w2_table<R>(P), bhat_table<R>(P) + P.blue_ofs[r], T, n,
                                                        N, Mb, s_rad, s_np, gs, Mb > 0 ? kBlueMaxMb / Mb : 1)
-                  : stockham<true, R, C, G, true, NT>(B0, A0, N, T, s_rad, s_np, gs, tstep);
+                  : stockham<true, R, C, G, true, NT, true>(B0, A0, N, T, s_rad, s_np, gs, tstep);
 
     // 4. store the rings (Bluestein rings: times the chirp; even n: pixel pairs
     //    as one 8-byte store when aligned)
     for (int g = 0; g < gn; ++g) {
         const C *z = src + g * gs;
         R *out = map + (size_t)(b0 + g) * P.npix + P.ofs[r];
-        auto val = [&](int j) { return BLUE ? cmul(z[j], blue_chirp<true>(T, n, N, j)) : z[j]; };
+        auto val = [&](int j) { return BLUE ? cmul(z[PI(j)], blue_chirp<true>(T, n, N, j)) : z[PI(j)]; };
         if (even && (reinterpret_cast<uintptr_t>(out) & 7) == 0) {
             float2 *o2 = reinterpret_cast<float2 *>(out);
 #pragma unroll 4
@@ -958,7 +966,7 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
                       delta, map);
 }
 
-size_t ring_mf_smem_bytes(int cap, int G) { return (size_t)2 * G * cap * sizeof(float2); }
+size_t ring_mf_smem_bytes(int cap, int G) { return (size_t)2 * G * (cap + (cap >> 4) + 1) * sizeof(float2); }
 
 cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int g_smooth,
                                  int g_blue, int nt, cudaStream_t st)
