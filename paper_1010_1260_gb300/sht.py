@@ -339,6 +339,63 @@ class Plan:
         return out
 
 
+    def alm2map_host_stream(self, alms, prec: str = "fp64", outs=None) -> list:
+        """alm2map of a sequence of host batches (complex128, ideally pinned)
+        into host maps, pipelined: batch k+1's coefficients go up on one copy
+        stream and batch k-1's maps come down on another while batch k is
+        transformed on the current stream (two device buffer sets).  Every
+        batch's copies and transform happen; returns the host maps after
+        waiting for all of them."""
+        alms = [a.reshape(-1, self.nalm) for a in alms]
+        if not alms:
+            return []
+        B = alms[0].shape[0]
+        for a in alms:
+            if a.is_cuda or a.dtype != torch.complex128 or a.shape[0] != B:
+                raise TypeError("host complex128 batches of equal size expected")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        key = (B, prec)
+        if getattr(self, "_stream_bufs", None) is None or self._stream_bufs[0] != key:
+            self._stream_bufs = (key, [torch.empty((B, self.nalm), dtype=torch.complex128, device=dev) for _ in range(2)],
+                                 [torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], device=dev) for _ in range(2)])
+        _, d_alm, d_map = self._stream_bufs
+        if outs is None:
+            outs = [torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], pin_memory=True) for _ in alms]
+        comp = torch.cuda.current_stream()
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
+        uploaded = [torch.cuda.Event() for _ in alms]
+        done = [torch.cuda.Event() for _ in alms]
+        consumed = [torch.cuda.Event() for _ in alms]   # input buffer free again
+        downloaded = [torch.cuda.Event() for _ in alms]  # output buffer free again
+        n = len(alms)
+
+        def upload(k):
+            with torch.cuda.stream(up):
+                if k >= 2:
+                    up.wait_event(consumed[k - 2])
+                d_alm[k % 2].copy_(alms[k], non_blocking=True)
+                uploaded[k].record(up)
+
+        upload(0)
+        for k in range(n):
+            if k + 1 < n:
+                upload(k + 1)
+            comp.wait_event(uploaded[k])
+            if k >= 2:
+                comp.wait_event(downloaded[k - 2])
+            self.alm2map(d_alm[k % 2], prec, out=d_map[k % 2])
+            consumed[k].record(comp)
+            done[k].record(comp)
+            with torch.cuda.stream(down):
+                down.wait_event(done[k])
+                outs[k].copy_(d_map[k % 2], non_blocking=True)
+                downloaded[k].record(down)
+        down.synchronize()
+        up.synchronize()
+        comp.synchronize()
+        return outs
+
+
 class Multi:
     """Many one-map requests of different plans in one call (the batching form)."""
 

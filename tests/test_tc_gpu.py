@@ -116,3 +116,17 @@ def test_tc_odd_lengths_and_generic_rings(oracle_mod, sht, prec, gl_odd):
         again = plan.alm2map(torch.from_numpy(alm).cuda(), prec)
         plan.sync()
         assert torch.equal(again, got)
+
+
+def test_host_stream_matches_device_calls(sht):
+    """The pipelined host-buffer API gives the maps of one alm2map per batch."""
+    plan = sht.Plan(sht.healpix(16), 40)
+    batches = [torch.from_numpy(inputs.batch_alm(40, 40, 600 + k, 3)).pin_memory() for k in range(5)]
+    outs = plan.alm2map_host_stream(batches, "bf16x6_tc")
+    for k, a in enumerate(batches):
+        want = plan.alm2map(a.cuda(), "bf16x6_tc").cpu()
+        assert torch.equal(outs[k], want)
+    # output buffers reused two apart, as the benchmark does
+    pins = [torch.empty((3, plan.npix), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    outs = plan.alm2map_host_stream(batches[:4], "bf16x6_tc", outs=[pins[k % 2] for k in range(4)])
+    assert torch.equal(pins[1], plan.alm2map(batches[3].cuda(), "bf16x6_tc").cpu())
