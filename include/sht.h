@@ -232,9 +232,16 @@ int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *
  * an atomic counter, then one launch per ring list does all rings; the
  * context is capturable in a CUDA graph (no allocation or host sync inside
  * sht_multi_alm2map; pointers are kernel parameters, so a captured graph
- * replays with the pointers it was captured with).  Tensor-core forms run
- * each request through its plan in turn.  1 <= nreq <= 256; all plans on one
- * device; the plans must outlive the context.
+ * replays with the pointers it was captured with).  Tensor-core forms: the
+ * operand prep of each request (one small launch each), then one persistent
+ * tensor-core Legendre launch over all requests' (request, m, ring block)
+ * items (one CTA per SM, items by decreasing cost, round robin), then one
+ * FP32 ring launch per ring list; equally capturable.  Creating a tensor-core
+ * context builds each plan's operand buffer and skip tables (synchronous);
+ * while the context runs, the plans' own transforms must not run concurrently
+ * (they share those buffers); a bounded device wait that runs out is reported
+ * by sht_sync(plans[0]).  1 <= nreq <= 256; all plans on one device; the
+ * plans must outlive the context.
  * sht_alm2map_multi = create + run + stream synchronize + destroy. */
 typedef struct sht_multi_s *sht_multi_t;
 int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht_multi_t *out);

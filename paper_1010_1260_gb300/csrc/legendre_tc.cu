@@ -398,10 +398,16 @@ constexpr int kPrefetch = 8;  // stages of B tiles prefetched into L2 ahead of t
 
 // Persistent kernel: CTA c handles work items c, c + gridDim.x, ... where
 // item j = (m = j / nrb, ring block rb = j % nrb): heavy (small m) items first.
-template <bool BF16, int NPA, int NPB>
+// MULTI: the items come from the list `items` (request, m, ring block), one
+// map per request, each with its own plan (plans[request]) and its own B
+// operand, segment table and Delta (mp): many requests of different grids and
+// band limits in one launch.
+template <bool BF16, int NPA, int NPB, bool MULTI = false>
 __global__ void __launch_bounds__(kWarps * 32, 1)
-legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, const int *__restrict__ seg_off,
-                   float2 *__restrict__ delta, int nmaps, int ncols, int *__restrict__ status, int withhold)
+legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__restrict__ bbuf,
+                   const int *__restrict__ seg_off, float2 *__restrict__ delta, int nmaps, int ncols,
+                   int *__restrict__ status, int withhold, const DevPlan *__restrict__ plans,
+                   const int4 *__restrict__ items, int nitems_multi, const __grid_constant__ MultiTcPtrs mp)
 {
     using C = Cfg<BF16, NPA, NPB>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -414,9 +420,8 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
 
-    const int L = P.lmax;
     const int nrb = (P.npairs + kRows - 1) / kRows;
-    const int nitems = nrb * (P.mmax + 1);
+    const int nitems = MULTI ? nitems_multi : nrb * (P.mmax + 1);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
@@ -432,9 +437,39 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
     auto b_tile = [&](int s, int par, int piece) {
         return stage0 + s * C::STAGE_BYTES + (C::A_TILES + par * NPB + piece) * kTileBytes;
     };
-    auto nstages_of = [&](int m) { return (L - m + 1 + C::STEPS - 1) / C::STEPS; };
+    // work item -> plan, order m, ring block, B operand, segment table, Delta
+    struct Work {
+        const DevPlan *Q;
+        int m, rb;
+        const unsigned char *bb;
+        const int *seg;
+        float2 *dl;
+    };
+    auto work_of = [&](int it) {
+        Work w;
+        if constexpr (MULTI) {
+            const int4 v = items[it];
+            w.Q = plans + v.x;
+            w.m = v.y;
+            w.rb = v.z;
+            w.bb = static_cast<const unsigned char *>(mp.bbuf[v.x]);
+            w.seg = mp.seg[v.x];
+            w.dl = static_cast<float2 *>(mp.delta[v.x]);
+        } else {
+            w.Q = &P;
+            w.m = it / nrb;
+            w.rb = it - w.m * nrb;
+            w.bb = bbuf;
+            w.seg = seg_off;
+            w.dl = delta;
+        }
+        return w;
+    };
+    auto nstages_of = [&](const DevPlan &Q, int m) { return (Q.lmax - m + 1 + C::STEPS - 1) / C::STEPS; };
     // first stage of a work item (evanescent skip: whole 64-degree groups)
-    auto first_stage = [&](int item) { return P.skip_g ? P.skip_g[item] * C::GROUP : 0; };
+    auto first_stage = [&](const DevPlan &Q, int m, int rb) {
+        return Q.skip_g ? Q.skip_g[(size_t)m * ((Q.npairs + kRows - 1) / kRows) + rb] * C::GROUP : 0;
+    };
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -468,29 +503,32 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
         uint32_t gs = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int m = item / nrb;
-            const int pair = (item % nrb) * kRows + t;
-            const bool live = pair < P.npairs;
-            const int s0 = first_stage(item);
+            const Work w = work_of(item);
+            const DevPlan &Q = *w.Q;
+            const int m = w.m;
+            const int L = Q.lmax;
+            const int pair = w.rb * kRows + t;
+            const bool live = pair < Q.npairs;
+            const int s0 = first_stage(Q, m, w.rb);
             double x = 0.0, p0 = 0.0, p1 = 0.0;
             int k = 0;
             if (live) {
-                const size_t o = (size_t)m * P.npairs + pair;
-                x = P.pair_x[pair];
+                const size_t o = (size_t)m * Q.npairs + pair;
+                x = Q.pair_x[pair];
                 if (s0 > 0) {
-                    p0 = P.warm_p0[o];
-                    p1 = P.warm_p1[o];
-                    k = P.warm_k[o];
+                    p0 = Q.warm_p0[o];
+                    p1 = Q.warm_p1[o];
+                    k = Q.warm_k[o];
                 } else {
-                    p1 = P.start_v[o];
-                    k = P.start_k[o];
+                    p1 = Q.start_v[o];
+                    k = Q.start_k[o];
                 }
             }
             const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
-            const int nst = nstages_of(m);
+            const int nst = nstages_of(Q, m);
             int l = m + s0 * C::STEPS;
             // A_{l+1} for the stage's degrees, one per lane, prefetched a stage ahead
-            auto coef = [&](int lq) { return (lane < C::STEPS && lq <= L) ? __ldg(&P.coefA[mofs + (lq - m)]) : 0.0; };
+            auto coef = [&](int lq) { return (lane < C::STEPS && lq <= L) ? __ldg(&Q.coefA[mofs + (lq - m)]) : 0.0; };
             double a_cur = coef(l + 1 + lane);
             for (int i = s0; i < nst; ++i) {
                 const int s = (int)(gs % C::NS);
@@ -517,9 +555,12 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
         uint32_t gg = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int m = item / nrb;
-            const int pair = (item % nrb) * kRows + row;
-            const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP - first_stage(item) / C::GROUP;
+            const Work w = work_of(item);
+            const DevPlan &Q = *w.Q;
+            const int m = w.m;
+            const int L = Q.lmax;
+            const int pair = w.rb * kRows + row;
+            const int ngroups = (nstages_of(Q, m) + C::GROUP - 1) / C::GROUP - first_stage(Q, m, w.rb) / C::GROUP;
             for (int g = 0; g < ngroups; ++g) {
                 const int set = (int)(gg & 1u);
                 ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
@@ -553,8 +594,8 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
             {
                 const int quad = warp - 4;
                 int2 rr = make_int2(-1, -1);
-                if (pair < P.npairs) rr = P.pair_ring[pair];
-                const int M1 = P.mmax + 1;
+                if (pair < Q.npairs) rr = Q.pair_ring[pair];
+                const int M1 = Q.mmax + 1;
                 const bool vec = (nmaps & 1) == 0;
                 // float x of row r of the transposed block at column col0
                 auto slot = [&](int col0, int r, int x) {
@@ -589,7 +630,7 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
                             const float4 v =
                                 *reinterpret_cast<const float4 *>(slot(side == 0 ? 32 * k : ncols + 32 * k, rw, 4 * sg));
                             if (ring >= 0) {
-                                float2 *d = delta + ((size_t)ring * M1 + m) * nmaps + b;
+                                float2 *d = w.dl + ((size_t)ring * M1 + m) * nmaps + b;
                                 if (vec && b + 1 < nmaps) {
                                     *reinterpret_cast<float4 *>(d) = v;
                                 } else {
@@ -613,10 +654,13 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
             uint32_t gs = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                const int m = item / nrb;
-                const unsigned char *blk = bbuf + (size_t)(seg_off[2 * m] / C::STEPS) * SB;
-                const int nst = nstages_of(m);
-                const int s0 = first_stage(item);
+                const Work w = work_of(item);
+            const DevPlan &Q = *w.Q;
+            const int m = w.m;
+            const int L = Q.lmax;
+                const unsigned char *blk = w.bb + (size_t)(w.seg[2 * m] / C::STEPS) * SB;
+                const int nst = nstages_of(Q, m);
+                const int s0 = first_stage(Q, m, w.rb);
                 for (int i = s0; i < s0 + kPrefetch && i < nst; ++i) bulk_prefetch_l2(blk + (size_t)i * SB, SB);
                 for (int i = s0; i < nst; ++i) {
                     const int s = (int)(gs % C::NS);
@@ -648,9 +692,12 @@ legendre_tc_kernel(const DevPlan P, const unsigned char *__restrict__ bbuf, cons
             uint32_t gs = 0, gg = 0;
             bool ok = true, issued = false;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                const int m = item / nrb;
-                const int nst = nstages_of(m);
-                for (int i0 = first_stage(item); i0 < nst && ok; i0 += C::GROUP) {
+                const Work w = work_of(item);
+            const DevPlan &Q = *w.Q;
+            const int m = w.m;
+            const int L = Q.lmax;
+                const int nst = nstages_of(Q, m);
+                for (int i0 = first_stage(Q, m, w.rb); i0 < nst && ok; i0 += C::GROUP) {
                     const int set = (int)(gg & 1u);
                     if (!mbar_wait(bar_set_empty(set), ((gg >> 1) & 1u) ^ 1u, &s_abort)) {
                         ok = false;
@@ -1166,11 +1213,31 @@ cudaError_t launch_persistent(K kern, int smem, const DevPlan &P, const TcWork &
     const int grid = (int)std::min<long long>(nitems, nsm);  // persistent: one CTA per SM
     const unsigned char *b = static_cast<const unsigned char *>(W.bbuf);
     const int ncols = tc_ncols(nmaps);
-    if constexpr (STREAM)
+    if constexpr (STREAM) {
         kern<<<grid, kWarps * 32, smem, st>>>(P, b, static_cast<const unsigned char *>(acache), seg, delta, nmaps,
                                               ncols, W.status, W.withhold);
-    else
-        kern<<<grid, kWarps * 32, smem, st>>>(P, b, seg, delta, nmaps, ncols, W.status, W.withhold);
+    } else {
+        static const MultiTcPtrs none{};
+        kern<<<grid, kWarps * 32, smem, st>>>(P, b, seg, delta, nmaps, ncols, W.status, W.withhold, nullptr, nullptr,
+                                              0, none);
+    }
+    return cudaGetLastError();
+}
+
+template <bool BF16, int NPA, int NPB>
+cudaError_t run_main_multi(const DevPlan &P, const DevPlan *plans_dev, const int4 *items, int nitems,
+                           const MultiTcPtrs &mp, int *status, cudaStream_t st)
+{
+    using C = Cfg<BF16, NPA, NPB>;
+    auto kern = legendre_tc_kernel<BF16, NPA, NPB, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int grid = std::min(nitems, nsm);  // persistent: one CTA per SM
+    kern<<<grid, kWarps * 32, C::SMEM, st>>>(P, nullptr, nullptr, nullptr, 1, tc_ncols(1), status, -1, plans_dev,
+                                             items, nitems, mp);
     return cudaGetLastError();
 }
 
@@ -1187,6 +1254,15 @@ cudaError_t run_main(const DevPlan &P, const TcWork &W, const void *acache, floa
 }
 
 }  // namespace
+
+cudaError_t launch_tc_main_multi(const DevPlan &P, const DevPlan *plans_dev, const int4 *items, int nitems,
+                                 const MultiTcPtrs &mp, int prec, int *status, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (prec == SHT_FP32_TC) return run_main_multi<false, 2, 2>(P, plans_dev, items, nitems, mp, status, st);
+    if (prec == SHT_BF16X3_TC) return run_main_multi<true, 2, 2>(P, plans_dev, items, nitems, mp, status, st);
+    return run_main_multi<true, 3, 3>(P, plans_dev, items, nitems, mp, status, st);
+}
 
 size_t tc_bbuf_bytes(const TcWork &W, int prec)
 {

@@ -591,22 +591,38 @@ ring_synth_kernel(const __grid_constant__ DevPlan P, const typename C2T<R>::type
 // (block = ring index x groups + group), so the maps of a sector are read at
 // about the same time.  The twiddles come from the plan's global tables
 // through the read-only cache, which leaves shared memory to the buffers.
-template <bool BLUE, int G, int NT>
+// MULTI: block i synthesises ring mitems[i].y of request mitems[i].x (one map,
+// G = 1) with that request's plan, Delta and map; capm is the buffer size the
+// launch's shared memory was sized for.
+template <bool BLUE, int G, int NT, bool MULTI = false>
 __global__ void __launch_bounds__(NT, (NT == 256 && G <= 2) ? 3 : 1)
-ring_synth_mf_kernel(const __grid_constant__ DevPlan P, const float2 *__restrict__ delta, float *__restrict__ map,
-                     int nmaps)
+ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restrict__ delta0, float *__restrict__ map0,
+                     int nmaps0, const DevPlan *__restrict__ plans, const int2 *__restrict__ mitems,
+                     const __grid_constant__ MultiTcPtrs mp, int capm)
 {
     using R = float;
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_rad[32];
     __shared__ int s_np;
-    const int ngroups = (nmaps + G - 1) / G;
-    const int li = blockIdx.x / ngroups;
-    const int b0 = (blockIdx.x - li * ngroups) * G;
+    int li, b0, req = 0;
+    if constexpr (MULTI) {
+        const int2 w = mitems[blockIdx.x];
+        req = w.x;
+        li = w.y;
+        b0 = 0;
+    } else {
+        const int ngroups = (nmaps0 + G - 1) / G;
+        li = blockIdx.x / ngroups;
+        b0 = (blockIdx.x - li * ngroups) * G;
+    }
+    const DevPlan &P = MULTI ? plans[req] : P0;
+    const float2 *__restrict__ delta = MULTI ? static_cast<const float2 *>(mp.delta[req]) : delta0;
+    float *__restrict__ map = MULTI ? static_cast<float *>(mp.map[req]) : map0;
+    const int nmaps = MULTI ? 1 : nmaps0;
     const int gn = min(G, nmaps - b0);  // maps in this CTA
-    const int r = BLUE ? P.rings_blue[li] : P.rings_smooth[li];
-    const int cap = BLUE ? P.blue_cap : P.fft_cap;
+    const int r = MULTI ? li : (BLUE ? P.rings_blue[li] : P.rings_smooth[li]);
+    const int cap = MULTI ? capm : (BLUE ? P.blue_cap : P.fft_cap);
     const int capP = cap + (cap >> 4) + 1;      // padded buffer (element i at i + i / 16)
     auto PI = [](int i) { return i + (i >> 4); };
     C *A0 = reinterpret_cast<C *>(smem_raw);  // map g: A at A0 + g capP, B at A0 + (G + g) capP
@@ -966,6 +982,28 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
                       delta, map);
 }
 
+cudaError_t launch_ring_synth_mf_multi(const DevPlan *plans_dev, const int2 *smooth_items, int n_smooth,
+                                       int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
+                                       const MultiTcPtrs &mp, cudaStream_t st)
+{
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool blue = pass == 1;
+        const int n = blue ? n_blue : n_smooth;
+        if (n <= 0) continue;
+        const int cap = blue ? blue_cap : smooth_cap;
+        const size_t smem = ring_mf_smem_bytes(cap, 1);
+        auto k = blue ? ring_synth_mf_kernel<true, 1, 256, true> : ring_synth_mf_kernel<false, 1, 256, true>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k<<<n, 256, smem, st>>>(DevPlan{}, nullptr, nullptr, 1, plans_dev, blue ? blue_items : smooth_items, mp, cap);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 size_t ring_mf_smem_bytes(int cap, int G) { return (size_t)2 * G * (cap + (cap >> 4) + 1) * sizeof(float2); }
 
 cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int g_smooth,
@@ -981,7 +1019,8 @@ cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float
         if (G == 3) G = 2;
         while (G > 1 && ring_mf_smem_bytes(cap, G) > (size_t)227 * 1024) G /= 2;
         const size_t smem = ring_mf_smem_bytes(cap, G);
-        using K = void (*)(const DevPlan, const float2 *, float *, int);
+        using K = void (*)(const DevPlan, const float2 *, float *, int, const DevPlan *, const int2 *,
+                           const MultiTcPtrs, int);
         const bool big = nt >= 512;
         K k = blue ? (G == 4   ? (big ? ring_synth_mf_kernel<true, 4, 512> : ring_synth_mf_kernel<true, 4, 256>)
                       : G == 2 ? (big ? ring_synth_mf_kernel<true, 2, 512> : ring_synth_mf_kernel<true, 2, 256>)
@@ -994,7 +1033,8 @@ cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float
             if (e != cudaSuccess) return e;
         }
         const long long nblk = (long long)nl * ((nmaps + G - 1) / G);
-        k<<<(unsigned)nblk, big ? 512 : 256, smem, st>>>(P, delta_rm, map, nmaps);
+        static const MultiTcPtrs none{};
+        k<<<(unsigned)nblk, big ? 512 : 256, smem, st>>>(P, delta_rm, map, nmaps, nullptr, nullptr, none, 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -1430,6 +1430,62 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, q->device);
         q->nctas = std::max(1, nsm) * 8;  // persistent CTAs: several per SM hide the FP64 latency
+    } else {
+        // tensor-core forms: each plan's B operand buffer and skip tables, then
+        // one work list (request, m, ring block) by decreasing cost for one
+        // persistent Legendre launch, merged ring lists, Delta [ring][m] per request
+        struct Item {
+            long long cost;
+            int4 w;
+        };
+        std::vector<Item> items;
+        std::vector<int2> smooth, blue;
+        std::vector<sht::DevPlan> dp(nreq);
+        size_t dofs = 0;
+        for (int i = 0; i < nreq; ++i) {
+            sht_plan_s *p = plans[i];
+            std::lock_guard<std::mutex> lk(p->mu);
+            if ((rc = ensure_tc(p, prec)) || (rc = ensure_warm(p, nullptr))) break;
+            dp[i] = p->dp;
+            const int nrb = (p->npairs + 127) / 128;
+            for (int m = 0; m <= p->mmax; ++m)
+                for (int rb = 0; rb < nrb; ++rb) {
+                    const long long rows = std::min(128, p->npairs - rb * 128);
+                    items.push_back({(long long)(p->lmax - m + 1) * rows, make_int4(i, m, rb, 0)});
+                }
+            for (int r : p->rings_smooth_h) smooth.push_back(make_int2(i, r));
+            for (int r : p->rings_blue_h) blue.push_back(make_int2(i, r));
+            q->smooth_cap = std::max(q->smooth_cap, p->dp.fft_cap);
+            q->blue_cap = std::max(q->blue_cap, p->dp.blue_cap);
+            q->delta_ofs.push_back(dofs);
+            dofs += (size_t)p->nrings * (p->mmax + 1) * sizeof(float2);
+            dofs = (dofs + 255) & ~(size_t)255;
+        }
+        if (rc) {
+            std::string keep = g_err;
+            free_multi(q);
+            g_err = keep;
+            return rc;
+        }
+        std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+        std::vector<int4> w(items.size());
+        for (size_t j = 0; j < items.size(); ++j) w[j] = items[j].w;
+        q->nitems = (int)w.size();
+        q->n_smooth = (int)smooth.size();
+        q->n_blue = (int)blue.size();
+        if ((rc = multi_upload(q, dp, &q->d_plans)) || (rc = multi_upload(q, w, &q->d_items)) ||
+            (rc = multi_upload(q, smooth, &q->d_smooth)) || (rc = multi_upload(q, blue, &q->d_blue))) {
+            std::string keep = g_err;
+            free_multi(q);
+            g_err = keep;
+            return rc;
+        }
+        cudaError_t e = cudaMalloc(&q->d_delta, dofs);
+        if (e != cudaSuccess) {
+            free_multi(q);
+            return fail(SHT_ENOMEM, "multi workspace: %s", cudaGetErrorString(e));
+        }
+        q->allocs.push_back(q->d_delta);
     }
     *out = q;
     return SHT_OK;
@@ -1449,11 +1505,30 @@ extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void
     for (int i = 0; i < q->nreq; ++i)
         if (!alm_dev[i] || !map_dev[i]) return fail(SHT_EINVAL, "null device pointer for request %d", i);
     if (q->prec != SHT_FP64) {
-        // tensor-core forms: each request through its own plan (groups of one map)
+        // tensor-core forms: the operand prep of every request, one persistent
+        // Legendre launch over all requests' work items, one ring launch per list
+        DeviceGuard dg(q->device);
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const bool bf16 = q->prec != SHT_FP32_TC;
+        sht::MultiTcPtrs mp{};
         for (int i = 0; i < q->nreq; ++i) {
-            const int rc = sht_alm2map_batch(q->plans[i], 1, alm_dev[i], map_dev[i], q->prec, stream);
-            if (rc) return rc;
+            const sht_plan_s *p = q->plans[i];
+            mp.bbuf[i] = p->tc.bbuf;
+            mp.seg[i] = bf16 ? p->tc.seg_bf16 : p->tc.seg_tf32;
+            mp.delta[i] = static_cast<char *>(q->d_delta) + q->delta_ofs[i];
+            mp.map[i] = map_dev[i];
+            cudaError_t e = sht::launch_tc_prep(p->dp, p->tc, q->prec, static_cast<const double2 *>(alm_dev[i]), 1, st);
+            if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
+            g_launches.fetch_add(1, std::memory_order_relaxed);
         }
+        cudaError_t e = sht::launch_tc_main_multi(q->plans[0]->dp, q->d_plans, q->d_items, q->nitems, mp, q->prec,
+                                                  q->plans[0]->tc.status, st);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_tc multi launch");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        e = sht::launch_ring_synth_mf_multi(q->d_plans, q->d_smooth, q->n_smooth, q->smooth_cap, q->d_blue, q->n_blue,
+                                            q->blue_cap, mp, st);
+        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_mf multi launch");
+        g_launches.fetch_add((q->n_smooth > 0) + (q->n_blue > 0), std::memory_order_relaxed);
         return SHT_OK;
     }
     DeviceGuard dg(q->device);

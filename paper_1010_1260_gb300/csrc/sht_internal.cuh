@@ -136,6 +136,14 @@ struct TcWork {
     int *status = nullptr;
 };
 inline int tc_ncols(int nmaps) { return ((2 * nmaps + 31) / 32) * 32; }
+
+// Per-request operands of a many-request tensor-core launch (one map each).
+struct MultiTcPtrs {
+    const void *bbuf[kMaxReq];  // B operand image of the request's plan
+    const int *seg[kMaxReq];    // its (m, parity) segment table for the form
+    void *delta[kMaxReq];       // its Delta, complex64 [ring][m]
+    void *map[kMaxReq];         // its map, float32
+};
 size_t tc_bbuf_bytes(const TcWork &W, int prec);
 cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const double2 *alm, int nmaps,
                            cudaStream_t st);
@@ -145,6 +153,17 @@ cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const do
 // the launch.
 cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, const void *acache, float2 *delta,
                            int nmaps, cudaStream_t st);
+// Many requests (one map each) in one persistent launch: items (request, m,
+// ring block) sorted by decreasing cost; plans_dev[request] are the requests'
+// plans (with their skip tables), P any one of them (launch shape only).
+cudaError_t launch_tc_main_multi(const DevPlan &P, const DevPlan *plans_dev, const int4 *items, int nitems,
+                                 const MultiTcPtrs &mp, int prec, int *status, cudaStream_t st);
+// FP32 ring step of many requests (one map each, Delta [ring][m]): items
+// (request, ring) of the smooth and Bluestein lists; caps are the largest
+// buffers over the requests.
+cudaError_t launch_ring_synth_mf_multi(const DevPlan *plans_dev, const int2 *smooth_items, int n_smooth,
+                                       int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
+                                       const MultiTcPtrs &mp, cudaStream_t st);
 size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
 // Fill the evanescent-skip tables (skip_g: [mmax+1][nrb]; warm_*: [mmax+1][npairs]).
 cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,

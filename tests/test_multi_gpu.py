@@ -70,14 +70,58 @@ def test_multi_graph_replay_equals_eager(sht):
             assert torch.equal(o, e)
 
 
-def test_multi_tensor_core_form(sht):
-    lmaxs = [64, 100, 48]
+@pytest.mark.parametrize("prec", ["fp32_tc", "bf16x6_tc"])
+def test_multi_tensor_core_form(sht, prec):
+    """One persistent tensor-core launch over all requests: bit for bit the
+    per-plan tensor-core path (same items, same arithmetic), and close to FP64."""
+    lmaxs = [64, 100, 48, 130, 33, 200]
+    plans, alms = _requests(sht, lmaxs)
+    multi = sht.Multi(plans, prec)
+    outs = multi.alm2map(alms)
+    torch.cuda.synchronize()
+    for p, a, o in zip(plans, alms, outs):
+        assert torch.equal(o, p.alm2map(a, prec))
+        ref = p.alm2map(a).float()
+        assert float(torch.linalg.norm(o - ref) / torch.linalg.norm(ref)) < (1e-5 if prec == "fp32_tc" else 1e-6)
+
+
+def test_multi_tensor_core_graph_replay(sht):
+    lmaxs = [64, 128, 90, 256]
+    plans, alms = _requests(sht, lmaxs)
+    multi = sht.Multi(plans, "bf16x6_tc")
+    eager = [o.clone() for o in multi.alm2map(alms)]
+    outs = multi.outputs()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        multi.alm2map(alms, outs)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        multi.alm2map(alms, outs)
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for o, e in zip(outs, eager):
+            assert torch.equal(o, e)
+
+
+def test_multi_tensor_core_log_uniform(oracle_mod, sht):
+    lmaxs = inputs.request_lmax(256, 4)
     plans, alms = _requests(sht, lmaxs)
     outs = sht.Multi(plans, "fp32_tc").alm2map(alms)
     torch.cuda.synchronize()
-    for p, a, o in zip(plans, alms, outs):
-        ref = p.alm2map(a).float()
-        assert float(torch.linalg.norm(o - ref) / torch.linalg.norm(ref)) < 1e-5
+    rng = np.random.default_rng(8)
+    for i in sorted(set(rng.choice(256, 5, replace=False).tolist()) | {int(np.argmin(lmaxs))}):
+        assert torch.equal(outs[i], plans[i].alm2map(alms[i], "fp32_tc"))
+    i = int(np.argmin(lmaxs))
+    L = int(lmaxs[i])
+    g = oracle_mod.healpix_grid(L // 2)
+    want = oracle_mod.alm2map(g, L, L, alms[i].cpu().numpy()[None])[0]
+    got = outs[i].double().cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5
 
 
 def test_multi_log_uniform_requests(oracle_mod, sht):
