@@ -639,6 +639,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restric
     const int nb = even ? n / 2 + 1 : (n - 1) / 2 + 1;
     const int tstep = even ? 4 : 2;
     const int Mb = BLUE ? P.blue_mb[r] : 0;
+    const C *Cp = BLUE ? P.chirp32 + P.chirp_ofs[r] : nullptr;  // e^{i pi t^2 / N}, t < N
 
     if (tid == 0) s_np = factorize(BLUE ? Mb : N, s_rad);
 
@@ -793,7 +794,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restric
             } else {
                 z = (k < nb) ? F[PI(k)] : cconj(F[PI(N - k)]);
             }
-            Bg[PI(k)] = BLUE ? cmul(z, blue_chirp<true>(T, n, N, k)) : z;
+            Bg[PI(k)] = BLUE ? cmul(z, Cp[k]) : z;
         }
         if (BLUE)
             for (int k = N + tid; k < Mb; k += NT) Bg[PI(k)] = mk<R>(0, 0);
@@ -812,7 +813,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restric
     for (int g = 0; g < gn; ++g) {
         const C *z = src + g * gs;
         R *out = map + (size_t)(b0 + g) * P.npix + P.ofs[r];
-        auto val = [&](int j) { return BLUE ? cmul(z[PI(j)], blue_chirp<true>(T, n, N, j)) : z[PI(j)]; };
+        auto val = [&](int j) { return BLUE ? cmul(z[PI(j)], Cp[j]) : z[PI(j)]; };
         if (even && (reinterpret_cast<uintptr_t>(out) & 7) == 0) {
             float2 *o2 = reinterpret_cast<float2 *>(out);
 #pragma unroll 4
@@ -970,10 +971,6 @@ cudaError_t launch_two(K smooth, K blue, const DevPlan &P, bool fp64, int nmaps,
 
 }  // namespace
 
-size_t ring_smem_bytes(const DevPlan &P, bool fp64)
-{
-    return ring_smem_bytes_for_cap(P.fft_cap, fp64);
-}
 
 cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, double *map, int nmaps, int group,
                                    cudaStream_t st)
@@ -1077,11 +1074,5 @@ cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, doubl
                       map, q, wring);
 }
 
-cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
-                                      const double *wring, cudaStream_t st)
-{
-    return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, 0, st,
-                      map, q, wring);
-}
 
 }  // namespace sht

@@ -450,6 +450,9 @@ int build_tables(sht_plan_s *p, const Rings &R)
     std::vector<float2> bh32;
     std::map<int, long long> bwhere;
     int bcap = 0;
+    std::vector<long long> cofs(nr, 0);
+    std::vector<float2> ch32;
+    std::map<int, long long> cofs_of;
     for (int r = 0; r < nr; ++r) {
         const int n = R.nphi[r];
         const int N = (n % 2 == 0) ? n / 2 : n;
@@ -465,11 +468,20 @@ int build_tables(sht_plan_s *p, const Rings &R)
         auto it = bwhere.find(N);
         if (it != bwhere.end()) {
             bofs[r] = it->second;
+            cofs[r] = cofs_of[N];
             continue;
         }
         const long long o = (long long)bh64.size();
         bwhere[N] = o;
         bofs[r] = o;
+        cofs_of[N] = (long long)ch32.size();
+        cofs[r] = cofs_of[N];
+        for (int t = 0; t < N; ++t) {
+            // c_t = e^{i pi t^2 / N}: the angle of the ring table's entry T_n[(t^2 mod 2N) n / N]
+            const long long qn = (((long long)t * t) % (2LL * N)) * (n / N);
+            const double a = kPi * (double)qn / (double)n;
+            ch32.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
         std::vector<double> re(Mb, 0.0), im(Mb, 0.0);
         for (int t = 0; t < N; ++t) {
             // b_t = e^{-i pi t^2 / N}, with t^2 reduced mod 2N for an exact angle
@@ -540,6 +552,8 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, rblue, &d.rings_blue))) return rc;
     if ((rc = upload(p, bmb, &d.blue_mb))) return rc;
     if ((rc = upload(p, bofs, &d.blue_ofs))) return rc;
+    if ((rc = upload(p, cofs, &d.chirp_ofs))) return rc;
+    if ((rc = upload(p, ch32, &d.chirp32))) return rc;
     if ((rc = upload(p, bh64, &d.bhat64))) return rc;
     if ((rc = upload(p, bh32, &d.bhat32))) return rc;
     if ((rc = upload(p, w2d, &d.w2_64))) return rc;

@@ -60,6 +60,8 @@ struct DevPlan {
     const int *rings_blue;     // [n_blue]
     const int *blue_mb;        // [nrings] Mb (0 for smooth rings)
     const long long *blue_ofs; // [nrings] offset of the ring's chirp spectrum in bhat64 / bhat32
+    const long long *chirp_ofs;  // [nrings] offset of the ring's chirp e^{i pi t^2 / N}, t < N, in chirp32
+    const float2 *chirp32;
     const double2 *bhat64;     // per distinct Bluestein N: FFT_Mb(e^{-i pi t^2 / N}, wrapped) / Mb
     const float2 *bhat32;
     const double2 *w2_64;      // e^{2 pi i q / kBlueMaxMb}, q < kBlueMaxMb
@@ -109,9 +111,6 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
 // Ring step of the transpose: q[b][ring][m] = sum_j y_j e^{-i m phi_j}.
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
                                       const double *wring, cudaStream_t st);
-cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
-                                      const double *wring, cudaStream_t st);
-
 // Legendre step of the transpose, FP64:
 //   g[b][idx(l, m)] = c_m sum_r lambda_lm(x_r) q[b][r][m],  c_0 = 1, c_m = cfac for m > 0
 //   (cfac = 2: the real-linear transpose of alm2map; cfac = 1: the analysis sum).
@@ -174,7 +173,6 @@ cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, voi
 inline int ring_launches(const DevPlan &P) { return (P.n_smooth > 0) + (P.n_blue > 0); }
 
 // Shared-memory bytes the ring kernels need for this plan.
-size_t ring_smem_bytes(const DevPlan &P, bool fp64);
 inline size_t ring_smem_bytes_for_cap(int cap, bool fp64)
 {
     return (size_t)3 * cap * (fp64 ? 16 : 8);  // two FFT buffers + twiddle table
