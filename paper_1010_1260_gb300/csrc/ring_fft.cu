@@ -948,7 +948,7 @@ cudaError_t launch_two(K smooth, K blue, const DevPlan &P, bool fp64, int nmaps,
     const int gy = (nmaps + g - 1) / g;
     if (P.n_smooth > 0) {
         const size_t smem = ring_smem_bytes_for_cap(P.fft_cap, fp64);
-        if (smem > 48 * 1024) {
+        if (smem > 40 * 1024) {  // dynamic + static above the 48 KB default needs the opt-in
             cudaError_t e = cudaFuncSetAttribute(smooth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
@@ -958,7 +958,7 @@ cudaError_t launch_two(K smooth, K blue, const DevPlan &P, bool fp64, int nmaps,
     }
     if (P.n_blue > 0) {
         const size_t smem = ring_smem_bytes_for_cap(P.blue_cap, fp64);
-        if (smem > 48 * 1024) {
+        if (smem > 40 * 1024) {  // dynamic + static above the 48 KB default needs the opt-in
             cudaError_t e = cudaFuncSetAttribute(blue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
@@ -990,7 +990,7 @@ cudaError_t launch_ring_synth_mf_multi(const DevPlan *plans_dev, const int2 *smo
         const int cap = blue ? blue_cap : smooth_cap;
         const size_t smem = ring_mf_smem_bytes(cap, 1);
         auto k = blue ? ring_synth_mf_kernel<true, 1, 256, true> : ring_synth_mf_kernel<false, 1, 256, true>;
-        if (smem > 48 * 1024) {
+        if (smem > 40 * 1024) {  // dynamic + static above the 48 KB default needs the opt-in
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
@@ -1025,7 +1025,7 @@ cudaError_t launch_ring_synth_mf(const DevPlan &P, const float2 *delta_rm, float
                    : (G == 4   ? (big ? ring_synth_mf_kernel<false, 4, 512> : ring_synth_mf_kernel<false, 4, 256>)
                       : G == 2 ? (big ? ring_synth_mf_kernel<false, 2, 512> : ring_synth_mf_kernel<false, 2, 256>)
                                : (big ? ring_synth_mf_kernel<false, 1, 512> : ring_synth_mf_kernel<false, 1, 256>));
-        if (smem > 48 * 1024) {
+        if (smem > 40 * 1024) {  // dynamic + static above the 48 KB default needs the opt-in
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
@@ -1045,7 +1045,7 @@ cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smoot
     if (n_smooth > 0) {
         auto k = ring_synth_multi_kernel<double, false>;
         const size_t smem = ring_smem_bytes_for_cap(smooth_cap, true);
-        if (smem > 48 * 1024) {
+        if (smem > 40 * 1024) {  // dynamic + static above the 48 KB default needs the opt-in
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
@@ -1056,7 +1056,7 @@ cudaError_t launch_ring_synth_multi_fp64(const DevPlan *plans, const int2 *smoot
     if (n_blue > 0) {
         auto k = ring_synth_multi_kernel<double, true>;
         const size_t smem = ring_smem_bytes_for_cap(blue_cap, true);
-        if (smem > 48 * 1024) {
+        if (smem > 40 * 1024) {  // dynamic + static above the 48 KB default needs the opt-in
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
