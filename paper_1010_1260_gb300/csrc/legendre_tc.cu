@@ -222,6 +222,77 @@ __device__ __forceinline__ void split_pieces(float v, uint32_t (&out)[NP])
     }
 }
 
+// The coefficient product A_l x of the recurrence, correctly rounded like a
+// DMUL but computed on the integer pipes: the FP64 pipe of this part issues two
+// instructions per clock per SM, and a recurrence step otherwise spends two of
+// them (the product and the FMA).  x is fixed per ring: XInt holds its
+// significand shifted to the top of 64 bits (0 for x = 0) and the additive
+// exponent/sign term; A is >= 0, normal or zero, and the product is normal.
+struct XInt {
+    unsigned long long m;    // (1.f_x) 2^63, or 0 when x == 0
+    unsigned long long add;  // ((e_x - 1024) << 52) + sign(x) 2^63, modulo 2^64
+};
+__device__ __forceinline__ XInt xint_of(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    XInt r;
+    r.m = ((b << 1) == 0) ? 0ull : ((b << 11) | 0x8000000000000000ull);
+    r.add = ((unsigned long long)((long long)((int)((b >> 52) & 0x7ff) - 1024)) << 52) + (b & 0x8000000000000000ull);
+    return r;
+}
+__device__ __forceinline__ double mul_coef(double a, const XInt &X)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long ma = (b << 11) | 0x8000000000000000ull;
+    const unsigned long long hi = __umul64hi(ma, X.m);  // (1.f_a)(1.f_x) 2^62, in [2^62, 2^64)
+    const unsigned top = (unsigned)(hi >> 63);
+    const unsigned sh = 10u + top;                       // 53 significant bits above bit sh
+    // round to nearest even: the low product only decides exact halves, so it
+    // is folded into bit 0 (strictly below the rounding bit) as a sticky bit
+    unsigned long long hs = hi | (unsigned long long)((ma * X.m) != 0ull);
+    hs += (unsigned long long)((512u << top) - 1u) + ((hs >> sh) & 1ull);
+    const unsigned long long m53 = hs >> sh;  // hidden bit at 2^52 (2^53 after a carry)
+    const unsigned long long r = (b & 0x7ff0000000000000ull) + X.add + ((unsigned long long)top << 52) + m53;
+    return (b == 0ull || X.m == 0ull) ? 0.0 : __longlong_as_double((long long)r);
+}
+// degrees (by position in the stage) whose coefficient product runs on the
+// integer pipes; the rest are DMULs (as an FMA with +0): both give the same bits
+#ifndef SHT_INT_PRODUCT_MASK
+#define SHT_INT_PRODUCT_MASK 1
+#endif
+__host__ __device__ constexpr bool int_product(int q) { return (q & SHT_INT_PRODUCT_MASK) == SHT_INT_PRODUCT_MASK; }
+template <int Q>
+__device__ __forceinline__ double coef_x(double a, double x, const XInt &X)
+{
+    if constexpr (int_product(Q)) return mul_coef(a, X);
+    else return fma(a, x, 0.0);
+}
+
+// BF16 pieces of two values at once, as the packed words the A tiles hold (a
+// in the low half, b in the high half): cvt.rn.bf16x2.f32 rounds and packs
+// both in one instruction off the integer pipes; the residuals are exact.
+#ifndef SHT_F2FP_SPLIT
+#define SHT_F2FP_SPLIT 1
+#endif
+template <int NP>
+__device__ __forceinline__ void split_pair_bf16(float a, float b, uint32_t (&w)[NP])
+{
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+#if SHT_F2FP_SPLIT
+        uint32_t p;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(b), "f"(a));
+#else
+        const uint32_t p = (rn_bf16_bits(a) >> 16) | rn_bf16_bits(b);
+#endif
+        w[i] = p;
+        if (i + 1 < NP) {
+            a -= __uint_as_float(p << 16);
+            b -= __uint_as_float(p & 0xFFFF0000u);
+        }
+    }
+}
+
 __device__ __forceinline__ bool above_hi(double v)
 {
     const int e = (__double2hiint(v) >> 20) & 0x7ff;
@@ -254,15 +325,18 @@ __device__ __forceinline__ void product_pieces(int i, int &ia, int &ib)
     ib = b[i];
 }
 
-// One producer stage: 2 KC consecutive degrees of one ring pair (row t),
-// written as NPA pieces into the stage's A tiles ([parity][piece], 4 KB
-// each, K-major rows of 32 bytes with the 32-byte swizzle).  a_cur holds
-// A_{l+1} for the stage's degrees, one per lane.  With SLOW = false (no ring
-// of the warp still rescaled) the stage is one branch-free block: the FP64
-// chain of DFMAs, then the conversions, which the compiler interleaves with
-// the chain's latency.  With SLOW = true rescaled rings contribute zeros and
-// the rescale test runs once per chunk of 2 VEC degrees (the values grow by
-// far less than 2^512 over a chunk).
+template <int NPA>
+__device__ __forceinline__ void store_words(unsigned char *sbase, int t, int c, const uint32_t (&we)[NPA][4],
+                                            const uint32_t (&wo)[NPA][4])
+{
+    const int off = t * kRowBytes + ((c ^ ((t >> 2) & 1)) << 4);
+#pragma unroll
+    for (int i = 0; i < NPA; ++i) {
+        *reinterpret_cast<uint4 *>(sbase + (0 * NPA + i) * kTileBytes + off) = make_uint4(we[i][0], we[i][1], we[i][2], we[i][3]);
+        *reinterpret_cast<uint4 *>(sbase + (1 * NPA + i) * kTileBytes + off) = make_uint4(wo[i][0], wo[i][1], wo[i][2], wo[i][3]);
+    }
+}
+
 // Store the packed pieces of one 16-byte chunk (VEC values per parity).
 template <bool BF16, int NPA, int VEC>
 __device__ __forceinline__ void store_chunk(unsigned char *sbase, int t, int c, const uint32_t (&pe)[NPA][VEC],
@@ -292,20 +366,21 @@ __device__ __forceinline__ void store_chunk(unsigned char *sbase, int t, int c, 
 // written as NPA pieces into the stage's A tiles ([parity][piece], 4 KB
 // each, K-major rows of 32 bytes with the 32-byte swizzle).  a_cur holds
 // A_{l+1} for the stage's degrees, one per lane.
-// The products A_{l+1} x are written as fma(A, x, +0.0), which equals A x up
-// to the sign of a zero and issues as a DFMA (the FP64 pipe takes a DMUL per
-// 76 cycles and a DFMA per 64 per warp).
+// The products A_{l+1} x are correctly rounded either way: degrees selected by
+// int_product() take them on the integer pipes (mul_coef), the others as
+// fma(A, x, +0.0), a DFMA (the FP64 pipe takes a DMUL per 76 cycles and a DFMA
+// per 64 per warp), so the FP64 pipe carries 1.5 instead of 2 instructions per
+// degree.  BF16 pieces are rounded and packed in pairs (split_pair_bf16).
 // SLOW = false (no ring of the warp still rescaled): software-pipelined for
 // one warp per SM sub-partition issuing in order -- each degree issues its
-// DFMA (the only dependent chain), the DMUL of the degree two ahead (which
-// keeps the FP64 pipe busy during the DFMA latency), the shuffle of the
+// DFMA (the only dependent chain), the product of the degree two ahead, the shuffle of the
 // coefficient three ahead, then the integer / FP32 conversion of the current
 // value, so the conversions hide under the FP64 work instead of following it.
 // SLOW = true: rescaled rings contribute zeros and the rescale test runs once
 // per chunk of 2 VEC degrees (the values grow by far less than 2^512 over a chunk).
 template <bool BF16, int NPA, bool SLOW>
-__device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, double x, double a_cur, int l, int L,
-                                              double &p0, double &p1, int &k)
+__device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, double x, const XInt &X, double a_cur, int l,
+                                              int L, double &p0, double &p1, int &k)
 {
     constexpr int KC = BF16 ? 16 : 8;
     constexpr int VEC = BF16 ? 8 : 4;
@@ -314,12 +389,13 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
     if constexpr (!SLOW) {
         // A_{l+1} x two degrees ahead, A_{l+1} three degrees ahead: the DFMA of
         // a degree never waits for its DMUL, nor the DMUL for its shuffle.
-        double ax0 = fma(__shfl_sync(0xffffffffu, a_cur, 0), x, 0.0);
-        double ax1 = fma(__shfl_sync(0xffffffffu, a_cur, 1), x, 0.0);
+        double ax0 = coef_x<0>(__shfl_sync(0xffffffffu, a_cur, 0), x, X);
+        double ax1 = coef_x<1>(__shfl_sync(0xffffffffu, a_cur, 1), x, X);
         double an = __shfl_sync(0xffffffffu, a_cur, 2);
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             uint32_t pe[NPA][VEC], po[NPA][VEC];
+            uint32_t we[NPA][4], wo[NPA][4];  // BF16: packed pairs
 #pragma unroll
             for (int vv = 0; vv < VEC; vv += 2) {
                 // four degrees (two even, two odd l - m), then the four
@@ -332,32 +408,50 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
                     val[u] = p1;
                     const double tt = fma(ax0, p1, -p0);
                     ax0 = ax1;
-                    if (q + 2 < STEPS) ax1 = fma(an, x, 0.0);
+                    if (q + 2 < STEPS) ax1 = int_product(q + 2) ? mul_coef(an, X) : fma(an, x, 0.0);
                     if (q + 3 < STEPS) an = __shfl_sync(0xffffffffu, a_cur, q + 3);
                     p0 = p1;
                     p1 = tt;
                 }
-                uint32_t cv[4][NPA];
+                float f[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int q = c * 2 * VEC + 2 * vv + u;
-                    split_pieces<BF16, NPA>(rn_f32(l + q <= L ? val[u] : 0.0), cv[u]);
+                    f[u] = rn_f32(l + q <= L ? val[u] : 0.0);
                 }
+                if constexpr (BF16) {
+                    uint32_t e2[NPA], o2[NPA];
+                    split_pair_bf16<NPA>(f[0], f[2], e2);
+                    split_pair_bf16<NPA>(f[1], f[3], o2);
 #pragma unroll
-                for (int i = 0; i < NPA; ++i) {
-                    pe[i][vv] = cv[0][i];
-                    po[i][vv] = cv[1][i];
-                    pe[i][vv + 1] = cv[2][i];
-                    po[i][vv + 1] = cv[3][i];
+                    for (int i = 0; i < NPA; ++i) {
+                        we[i][vv / 2] = e2[i];
+                        wo[i][vv / 2] = o2[i];
+                    }
+                } else {
+                    uint32_t cv[4][NPA];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) split_pieces<BF16, NPA>(f[u], cv[u]);
+#pragma unroll
+                    for (int i = 0; i < NPA; ++i) {
+                        pe[i][vv] = cv[0][i];
+                        po[i][vv] = cv[1][i];
+                        pe[i][vv + 1] = cv[2][i];
+                        po[i][vv + 1] = cv[3][i];
+                    }
                 }
             }
-            store_chunk<BF16, NPA, VEC>(sbase, t, c, pe, po);
+            if constexpr (BF16) store_words<NPA>(sbase, t, c, we, wo);
+            else store_chunk<BF16, NPA, VEC>(sbase, t, c, pe, po);
         }
         return;
     }
     double ax[STEPS], vv[STEPS];
 #pragma unroll
-    for (int q = 0; q < STEPS; ++q) ax[q] = fma(__shfl_sync(0xffffffffu, a_cur, q), x, 0.0);
+    for (int q = 0; q < STEPS; ++q) {
+        const double a = __shfl_sync(0xffffffffu, a_cur, q);
+        ax[q] = int_product(q) ? mul_coef(a, X) : fma(a, x, 0.0);
+    }
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
         const bool live_k = (k == 0);
@@ -376,6 +470,24 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
     }
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
+        if constexpr (BF16) {
+            uint32_t we[NPA][4], wo[NPA][4];
+#pragma unroll
+            for (int v = 0; v < VEC; v += 2) {
+                const int q = c * 2 * VEC + 2 * v;
+                uint32_t e2[NPA], o2[NPA];
+                split_pair_bf16<NPA>(rn_f32(l + q <= L ? vv[q] : 0.0), rn_f32(l + q + 2 <= L ? vv[q + 2] : 0.0), e2);
+                split_pair_bf16<NPA>(rn_f32(l + q + 1 <= L ? vv[q + 1] : 0.0), rn_f32(l + q + 3 <= L ? vv[q + 3] : 0.0),
+                                     o2);
+#pragma unroll
+                for (int i = 0; i < NPA; ++i) {
+                    we[i][v / 2] = e2[i];
+                    wo[i][v / 2] = o2[i];
+                }
+            }
+            store_words<NPA>(sbase, t, c, we, wo);
+            continue;
+        }
         uint32_t pe[NPA][VEC], po[NPA][VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
@@ -496,13 +608,20 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    // the CTA's work items: its list of the balanced schedule, else round robin
+    const bool listed = !MULTI && P.sched_ctas == (int)gridDim.x;
+    const int i0 = listed ? P.sched_off[blockIdx.x] : (int)blockIdx.x;
+    const int i1 = listed ? P.sched_off[blockIdx.x + 1] : nitems;
+    const int istep = listed ? 1 : (int)gridDim.x;
+    auto item_at = [&](int j) { return listed ? P.sched_items[j] : j; };
 
     if (warp < 4) {
         // ------------------------------------------------------ producers --
         const int t = threadIdx.x;
         uint32_t gs = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (int jt = i0; jt < i1 && ok; jt += istep) {
+            const int item = item_at(jt);
             const Work w = work_of(item);
             const DevPlan &Q = *w.Q;
             const int m = w.m;
@@ -524,6 +643,7 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                     k = Q.start_k[o];
                 }
             }
+            const XInt X = xint_of(x);
             const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
             const int nst = nstages_of(Q, m);
             int l = m + s0 * C::STEPS;
@@ -537,9 +657,9 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                 ok = __all_sync(0xffffffffu, mbar_wait(bar_empty(s), ph ^ 1u, &s_abort));
                 if (!ok) break;
                 if (__any_sync(0xffffffffu, k < 0))
-                    produce_stage<BF16, NPA, true>(a_tile(s, 0, 0), t, x, a_cur, l, L, p0, p1, k);
+                    produce_stage<BF16, NPA, true>(a_tile(s, 0, 0), t, x, X, a_cur, l, L, p0, p1, k);
                 else
-                    produce_stage<BF16, NPA, false>(a_tile(s, 0, 0), t, x, a_cur, l, L, p0, p1, k);
+                    produce_stage<BF16, NPA, false>(a_tile(s, 0, 0), t, x, X, a_cur, l, L, p0, p1, k);
                 l += C::STEPS;
                 fence_proxy_async();
                 __syncwarp();
@@ -554,7 +674,8 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
         const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
         uint32_t gg = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (int jt = i0; jt < i1 && ok; jt += istep) {
+            const int item = item_at(jt);
             const Work w = work_of(item);
             const DevPlan &Q = *w.Q;
             const int m = w.m;
@@ -653,7 +774,8 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
             constexpr uint32_t SB = (uint32_t)C::B_TILES * kTileBytes;
             uint32_t gs = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int jt = i0; jt < i1 && ok; jt += istep) {
+                const int item = item_at(jt);
                 const Work w = work_of(item);
             const DevPlan &Q = *w.Q;
             const int m = w.m;
@@ -691,7 +813,8 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
             const uint32_t id = idesc<BF16>(ncols);
             uint32_t gs = 0, gg = 0;
             bool ok = true, issued = false;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int jt = i0; jt < i1 && ok; jt += istep) {
+                const int item = item_at(jt);
                 const Work w = work_of(item);
             const DevPlan &Q = *w.Q;
             const int m = w.m;
@@ -837,6 +960,11 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    const bool listed = P.sched_ctas == (int)gridDim.x;
+    const int i0 = listed ? P.sched_off[blockIdx.x] : (int)blockIdx.x;
+    const int i1 = listed ? P.sched_off[blockIdx.x + 1] : nitems;
+    const int istep = listed ? 1 : (int)gridDim.x;
+    auto item_at = [&](int j) { return listed ? P.sched_items[j] : j; };
 
     if (warp < 8) {
         // ----------------------------------------------------------- drain --
@@ -847,7 +975,8 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
         float te[2][32], to[2][32];  // totals of chunks q = 2 j + half of E and O
         uint32_t gg = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (int jt = i0; jt < i1 && ok; jt += istep) {
+            const int item = item_at(jt);
             const int m = item / nrb;
             const int pair = (item % nrb) * kRows + row;
             const int ngroups = (nstages_of(m) + C::GROUP - 1) / C::GROUP - first_stage(item) / C::GROUP;
@@ -927,7 +1056,8 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
         if (lane == 0) {
             uint32_t gs = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int jt = i0; jt < i1 && ok; jt += istep) {
+                const int item = item_at(jt);
                 const int m = item / nrb;
                 const size_t st0 = (size_t)(seg_off[2 * m] / C::STEPS);  // stages of the orders below m
                 const int nst = nstages_of(m);
@@ -961,7 +1091,8 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
             const uint32_t id = idesc<BF16>(ncols);
             uint32_t gs = 0, gg = 0;
             bool ok = true, issued = false;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int jt = i0; jt < i1 && ok; jt += istep) {
+                const int item = item_at(jt);
                 const int m = item / nrb;
                 const int nst = nstages_of(m);
                 for (int i0 = first_stage(item); i0 < nst && ok; i0 += C::GROUP) {
@@ -1185,6 +1316,7 @@ lambda_build_kernel(const DevPlan P, const int *__restrict__ seg_off, unsigned c
             k = P.start_k[o];
         }
     }
+    const XInt X = xint_of(x);
     const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
     const int nst = (L - m + 1 + STEPS - 1) / STEPS;
     unsigned char *blk = aout + ((size_t)(seg_off[2 * m] / STEPS) * nrb + (size_t)rb * nst) * SA;
@@ -1193,9 +1325,9 @@ lambda_build_kernel(const DevPlan P, const int *__restrict__ seg_off, unsigned c
     for (int i = s0; i < nst; ++i) {
         const double a_cur = coef(l + 1 + lane);
         if (__any_sync(0xffffffffu, k < 0))
-            produce_stage<BF16, NPA, true>(blk + (size_t)i * SA, t, x, a_cur, l, L, p0, p1, k);
+            produce_stage<BF16, NPA, true>(blk + (size_t)i * SA, t, x, X, a_cur, l, L, p0, p1, k);
         else
-            produce_stage<BF16, NPA, false>(blk + (size_t)i * SA, t, x, a_cur, l, L, p0, p1, k);
+            produce_stage<BF16, NPA, false>(blk + (size_t)i * SA, t, x, X, a_cur, l, L, p0, p1, k);
         l += STEPS;
     }
 }

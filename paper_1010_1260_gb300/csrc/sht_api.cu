@@ -11,6 +11,7 @@
 #include <atomic>
 #include <algorithm>
 #include <map>
+#include <queue>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -46,6 +47,8 @@ struct sht_plan_s {
     void *lcache[4] = {};  // plan-time Lambda operand per tensor-core form (sht_lambda_cache)
     bool skip_evanescent = true;  // tensor-core forms: start items after their all-zero degrees
     void *warm = nullptr;         // the skip tables (one allocation), built on first use
+    int *sched = nullptr;         // the tensor-core work lists (DevPlan::sched_off, sched_items)
+    int sched_skip = -1;          // skip setting the lists were built for (-1: none yet)
     std::vector<double> wring_h;  // pixel quadrature weight per ring (host copy)
     double *wring_d = nullptr;    // the same on the device (DevPlan::wring)
     size_t lcache_bytes[4] = {};
@@ -227,6 +230,7 @@ void free_plan(sht_plan_s *p)
         for (void *c : p->lcache)
             if (c) cudaFree(c);
         if (p->warm) cudaFree(p->warm);
+        if (p->sched) cudaFree(p->sched);
         for (auto &e : p->prof_pending) {
             cudaEventDestroy(e.a);
             cudaEventDestroy(e.b);
@@ -649,6 +653,67 @@ int check_plan(sht_plan_t p)
 
 // Evanescent-skip tables of the tensor-core forms: built on first use (one
 // FP64 pass over the recurrence, synchronous), or detached when disabled.
+// The work lists of the persistent tensor-core launches for the plan's current
+// skip tables: a work queue served in m order (ring block minor) to the CTA
+// with the least work so far, replayed on the host.  The cost of an item is
+// the degrees its recurrence runs plus a fixed share for its setup and Delta
+// epilogue.
+int ensure_sched(sht_plan_s *p, cudaStream_t st)
+{
+    sht::DevPlan &d = p->dp;
+    const int want = d.skip_g ? 1 : 0;
+    const int nrb = (p->npairs + 127) / 128;
+    const int nitems = nrb * (p->mmax + 1);
+    if (p->sched && p->sched_skip == want) {
+        d.sched_off = p->sched;
+        d.sched_items = p->sched + d.sched_ctas + 1;
+        return SHT_OK;
+    }
+    d.sched_ctas = 0;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "work lists");
+    const int G = std::min(nitems, nsm);
+    std::vector<int> g0((size_t)nitems, 0);
+    if (d.skip_g) {
+        e = cudaMemcpyAsync(g0.data(), d.skip_g, (size_t)nitems * sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "work lists");
+    }
+    constexpr long long kItemOverhead = 48;
+    using Slot = std::pair<long long, int>;  // (work so far, CTA)
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> q;
+    for (int b = 0; b < G; ++b) q.push({0, b});
+    std::vector<int> owner((size_t)nitems), host((size_t)G + 1 + nitems, 0);
+    for (int j = 0; j < nitems; ++j) {
+        const Slot t = q.top();
+        q.pop();
+        owner[j] = t.second;
+        ++host[t.second + 1];
+        q.push({t.first + (p->lmax - j / nrb + 1 - 64LL * g0[j]) + kItemOverhead, t.second});
+    }
+    for (int b = 0; b < G; ++b) host[b + 1] += host[b];
+    std::vector<int> fill(host.begin(), host.begin() + G);
+    for (int j = 0; j < nitems; ++j) host[G + 1 + fill[owner[j]]++] = j;
+    if (!p->sched) {
+        e = cudaMalloc(&p->sched, host.size() * sizeof(int));
+        if (e != cudaSuccess) {
+            p->sched = nullptr;
+            cudaGetLastError();
+            return fail(SHT_ENOMEM, "work lists: %s", cudaGetErrorString(e));
+        }
+    }
+    e = cudaMemcpyAsync(p->sched, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "work lists");
+    p->sched_skip = want;
+    d.sched_ctas = G;
+    d.sched_off = p->sched;
+    d.sched_items = p->sched + G + 1;
+    return SHT_OK;
+}
+
 int ensure_warm(sht_plan_s *p, cudaStream_t st)
 {
     sht::DevPlan &d = p->dp;
@@ -656,7 +721,7 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
         d.skip_g = nullptr;
         d.warm_p0 = d.warm_p1 = nullptr;
         d.warm_k = nullptr;
-        return SHT_OK;
+        return ensure_sched(p, st);
     }
     const size_t nrb = (size_t)((p->npairs + 127) / 128), M1 = (size_t)p->mmax + 1;
     const size_t nst = M1 * (size_t)p->npairs;
@@ -690,7 +755,7 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
     d.warm_p0 = reinterpret_cast<const double *>(b + b_g);
     d.warm_p1 = reinterpret_cast<const double *>(b + b_g + b_p);
     d.warm_k = reinterpret_cast<const int *>(b + b_g + 2 * b_p);
-    return SHT_OK;
+    return ensure_sched(p, st);
 }
 
 // Precision forms: FP64 recurrence (or the plan-time Lambda operand, when

@@ -48,6 +48,16 @@ struct DevPlan {
     const int *skip_g;
     const double *warm_p0, *warm_p1;
     const int *warm_k;
+    // Work lists of the persistent tensor-core launches (sched_ctas == 0:
+    // round robin): CTA b of sched_ctas runs items sched_items[sched_off[b] ..
+    // sched_off[b + 1]), item = m nrb + rb.  The lists replay a work queue
+    // served in m order to the CTA with the least work so far, so every CTA
+    // gets the same work to within one item (whatever the skip leaves of each)
+    // and the ring blocks of one order still run at about the same time,
+    // sharing its B operand in L2.
+    const int *sched_off;
+    const int *sched_items;
+    int sched_ctas;
     const long long *twofs;  // [nrings] offset of the ring's table in tw64 / tw32
     const double2 *tw64;     // per distinct nphi = n: e^{i pi q / n}, q in [0, 2n)
     const float2 *tw32;
