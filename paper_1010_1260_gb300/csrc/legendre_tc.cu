@@ -608,12 +608,14 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    // the CTA's work items: its list of the balanced schedule, else round robin
-    const bool listed = !MULTI && P.sched_ctas == (int)gridDim.x;
-    const int i0 = listed ? P.sched_off[blockIdx.x] : (int)blockIdx.x;
-    const int i1 = listed ? P.sched_off[blockIdx.x + 1] : nitems;
+    // the CTA's work items: its list of the balanced schedule (the plan's, or
+    // the CTA-major item order of a many-request launch), else round robin
+    const int *off = MULTI ? mp.cta_off : P.sched_off;
+    const bool listed = (MULTI ? mp.ctas : P.sched_ctas) == (int)gridDim.x;
+    const int i0 = listed ? off[blockIdx.x] : (int)blockIdx.x;
+    const int i1 = listed ? off[blockIdx.x + 1] : nitems;
     const int istep = listed ? 1 : (int)gridDim.x;
-    auto item_at = [&](int j) { return listed ? P.sched_items[j] : j; };
+    auto item_at = [&](int j) { return (listed && !MULTI) ? P.sched_items[j] : j; };
 
     if (warp < 4) {
         // ------------------------------------------------------ producers --

@@ -1398,7 +1398,8 @@ struct sht_multi_s {
     std::vector<void *> allocs;
     sht::DevPlan *d_plans = nullptr;
     int4 *d_items = nullptr;
-    int nitems = 0;
+    int *d_cta_off = nullptr;  // tensor-core forms: CTA ranges of d_items
+    int nitems = 0, ctas = 0;
     int2 *d_smooth = nullptr, *d_blue = nullptr;
     int n_smooth = 0, n_blue = 0, smooth_cap = 0, blue_cap = 0;
     int *d_counter = nullptr;
@@ -1470,11 +1471,20 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
             const sht_plan_s *p = plans[i];
             dp[i] = p->dp;
             const int nrb = (p->npairs + 127) / 128;
-            for (int m = 0; m <= p->mmax; ++m)
-                for (int rb = 0; rb < nrb; ++rb) {
-                    const long long rows = std::min(128, p->npairs - rb * 128);
-                    items.push_back({(long long)(p->lmax - m + 1) * rows, make_int4(i, m, rb, 0)});
+            std::vector<int> g0((size_t)nrb * (p->mmax + 1), 0);
+            if (p->dp.skip_g) {
+                cudaError_t e = cudaMemcpy(g0.data(), p->dp.skip_g, g0.size() * sizeof(int), cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "skip tables");
+                    break;
                 }
+            }
+            // cost: the degrees the item's recurrence runs plus a fixed share
+            // for its setup and Delta epilogue
+            for (int m = 0; m <= p->mmax; ++m)
+                for (int rb = 0; rb < nrb; ++rb)
+                    items.push_back({(long long)(p->lmax - m + 1) - 64LL * g0[(size_t)m * nrb + rb] + 48,
+                                     make_int4(i, m, rb, 0)});
             for (int r : p->rings_smooth_h) smooth.push_back(make_int2(i, r));
             for (int r : p->rings_blue_h) blue.push_back(make_int2(i, r));
             q->smooth_cap = std::max(q->smooth_cap, p->dp.fft_cap);
@@ -1483,13 +1493,32 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
             dofs += (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
             dofs = (dofs + 255) & ~(size_t)255;
         }
+        // longest first to the CTA with the least work so far, stored CTA-major
         std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+        int nsm_tc = 0;
+        cudaDeviceGetAttribute(&nsm_tc, cudaDevAttrMultiProcessorCount, q->device);
+        const int G = std::max(1, std::min((int)items.size(), nsm_tc));
+        using Slot = std::pair<long long, int>;
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int b = 0; b < G; ++b) heap.push({0, b});
+        std::vector<int> owner(items.size()), coff((size_t)G + 1, 0);
+        for (size_t j = 0; j < items.size(); ++j) {
+            const Slot t = heap.top();
+            heap.pop();
+            owner[j] = t.second;
+            ++coff[t.second + 1];
+            heap.push({t.first + items[j].cost, t.second});
+        }
+        for (int b = 0; b < G; ++b) coff[b + 1] += coff[b];
+        std::vector<int> fill(coff.begin(), coff.begin() + G);
         std::vector<int4> w(items.size());
-        for (size_t j = 0; j < items.size(); ++j) w[j] = items[j].w;
+        for (size_t j = 0; j < items.size(); ++j) w[fill[owner[j]]++] = items[j].w;
+        q->ctas = G;
         q->nitems = (int)w.size();
         q->n_smooth = (int)smooth.size();
         q->n_blue = (int)blue.size();
         if ((rc = multi_upload(q, dp, &q->d_plans)) || (rc = multi_upload(q, w, &q->d_items)) ||
+            (rc = multi_upload(q, coff, &q->d_cta_off)) ||
             (rc = multi_upload(q, smooth, &q->d_smooth)) || (rc = multi_upload(q, blue, &q->d_blue))) {
             std::string keep = g_err;
             free_multi(q);
@@ -1596,6 +1625,8 @@ extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void
             mp.seg[i] = bf16 ? p->tc.seg_bf16 : p->tc.seg_tf32;
             mp.delta[i] = static_cast<char *>(q->d_delta) + q->delta_ofs[i];
             mp.map[i] = map_dev[i];
+            mp.cta_off = q->d_cta_off;
+            mp.ctas = q->ctas;
             cudaError_t e = sht::launch_tc_prep(p->dp, p->tc, q->prec, static_cast<const double2 *>(alm_dev[i]), 1, st);
             if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
             g_launches.fetch_add(1, std::memory_order_relaxed);

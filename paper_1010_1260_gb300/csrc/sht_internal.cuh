@@ -152,6 +152,10 @@ struct MultiTcPtrs {
     const int *seg[kMaxReq];    // its (m, parity) segment table for the form
     void *delta[kMaxReq];       // its Delta, complex64 [ring][m]
     void *map[kMaxReq];         // its map, float32
+    // work lists: the items are stored CTA-major, CTA b of ctas running items
+    // [cta_off[b], cta_off[b + 1]) (ctas == 0: round robin)
+    const int *cta_off;
+    int ctas;
 };
 size_t tc_bbuf_bytes(const TcWork &W, int prec);
 cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const double2 *alm, int nmaps,
