@@ -188,17 +188,17 @@ __host__ __device__ constexpr uint32_t idesc(int n)
 
 // FP64 -> FP32 rounded to nearest (ties away from zero) on the integer pipe,
 // so the conversion costs no FP64 issue slot.  Values below the FP32 normal
-// range become 0; |p| is bounded far below the FP32 maximum.
+// range become 0; |p| is bounded far below the FP32 maximum.  Bits 29..60 of
+// the double are its 9 low exponent bits and the 23 kept mantissa bits: adding
+// 2^30 rebiases the exponent by -896 modulo 2^9, which is exact for every FP32
+// normal exponent, and the first dropped bit rounds (a carry into the exponent
+// is the correct result).
 __device__ __forceinline__ float rn_f32(double d)
 {
-    const int hi = __double2hiint(d);
+    const unsigned hi = (unsigned)__double2hiint(d);
     const unsigned lo = (unsigned)__double2loint(d);
-    const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
-    const unsigned sign = (unsigned)hi & 0x80000000u;
-    const unsigned man = (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned rbit = (lo >> 28) & 1u;  // first dropped mantissa bit
-    const unsigned bits = (e <= 0) ? sign : (sign | ((((unsigned)e << 23) | man) + rbit));
-    return __uint_as_float(bits);
+    const unsigned bits = (__funnelshift_r(lo, hi, 29) + 0x40000000u + ((lo >> 28) & 1u)) | (hi & 0x80000000u);
+    return __uint_as_float((hi & 0x7ff00000u) <= 0x38000000u ? (hi & 0x80000000u) : bits);
 }
 __device__ __forceinline__ uint32_t rn_tf32_bits(float f)
 {
@@ -257,10 +257,11 @@ __device__ __forceinline__ double mul_coef(double a, const XInt &X)
 }
 // degrees (by position in the stage) whose coefficient product runs on the
 // integer pipes; the rest are DMULs (as an FMA with +0): both give the same bits
-#ifndef SHT_INT_PRODUCT_MASK
-#define SHT_INT_PRODUCT_MASK 1
+// (bit q of the pattern, q = position of the degree in the stage)
+#ifndef SHT_INT_PRODUCT_BITS
+#define SHT_INT_PRODUCT_BITS 0xAAAAAAAAu
 #endif
-__host__ __device__ constexpr bool int_product(int q) { return (q & SHT_INT_PRODUCT_MASK) == SHT_INT_PRODUCT_MASK; }
+__host__ __device__ constexpr bool int_product(int q) { return ((SHT_INT_PRODUCT_BITS >> (q & 31)) & 1u) != 0u; }
 template <int Q>
 __device__ __forceinline__ double coef_x(double a, double x, const XInt &X)
 {
@@ -413,12 +414,11 @@ __device__ __forceinline__ void produce_stage(unsigned char *sbase, int t, doubl
                     p0 = p1;
                     p1 = tt;
                 }
+                // degrees past L keep their (finite) values: the B operand's
+                // rows there are zero
                 float f[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = c * 2 * VEC + 2 * vv + u;
-                    f[u] = rn_f32(l + q <= L ? val[u] : 0.0);
-                }
+                for (int u = 0; u < 4; ++u) f[u] = rn_f32(val[u]);
                 if constexpr (BF16) {
                     uint32_t e2[NPA], o2[NPA];
                     split_pair_bf16<NPA>(f[0], f[2], e2);
