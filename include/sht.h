@@ -169,7 +169,10 @@ long long sht_lambda_cache_bytes(sht_plan_t plan, int prec);
  * recurrence (synchronous) that finds, for every (m, block of 128 ring pairs),
  * the first 64-degree group holding a value representable in FP32 and stores
  * every ring's recurrence state there (about 20 bytes per (m, ring pair));
- * later launches start each work item at that group.  The maps are
+ * later launches start each work item at that group.  Either way the first
+ * tensor-core launch after a change of this setting also builds the plan's
+ * per-CTA work lists for it on the host (synchronous), balancing the
+ * degrees left in each item.  The maps are
  * bit-identical with the skip on or off (rescaling by powers of two is exact
  * and the skipped values are zeros); the work saved is about 22 % at lmax
  * 2048 on a HEALPix Nside 1024 grid.  enable = 0 turns it off. */
@@ -235,7 +238,8 @@ int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *
  * replays with the pointers it was captured with).  Tensor-core forms: the
  * operand prep of each request (one small launch each), then one persistent
  * tensor-core Legendre launch over all requests' (request, m, ring block)
- * items (one CTA per SM, items by decreasing cost, round robin), then one
+ * items (one CTA per SM; each CTA runs a fixed list: the items, longest
+ * first, each given to the CTA with the least work so far), then one
  * FP32 ring launch per ring list; equally capturable.  Creating a tensor-core
  * context builds each plan's operand buffer and skip tables (synchronous);
  * while the context runs, the plans' own transforms must not run concurrently
