@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--cpu-rings", type=int, default=384,
                     help="rings of one map in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--lambda-cache", action="store_true",
