@@ -161,6 +161,19 @@ int sht_lambda_cache(sht_plan_t plan, int prec, int enable, void *stream);
  * or a form without one. */
 long long sht_lambda_cache_bytes(sht_plan_t plan, int prec);
 
+/* The work lists the persistent tensor-core launches run, computed on the
+ * host (no device access): items 0 .. nitems-1, taken in that order, go one
+ * by one to the list with the least total cost so far (ties: the lowest list
+ * index) -- the replay of a work queue served in item order.  List b is
+ * items[off[b] .. off[b + 1] - 1], in item order; off has nlists + 1 entries,
+ * items nitems.  Every list's total stays within the largest single cost of
+ * the mean.  The library orders a plan's (m, ring block) items by m and a
+ * many-request launch's by decreasing cost, with the cost of an item the
+ * degrees its recurrence runs after the evanescent skip plus a fixed share for
+ * its setup.  Returns SHT_EINVAL for nitems < 0, nlists < 1, a NULL array or
+ * a negative cost. */
+int sht_work_lists(int nitems, const long long *cost, int nlists, int *off, int *items);
+
 /* Evanescent skip of the tensor-core forms (on by default).  For large m
  * near the poles lambda_lm is far below the FP32 range for many degrees (the
  * region below the turning point, where Algorithm 2's rescaling keeps the

@@ -651,13 +651,37 @@ int check_plan(sht_plan_t p)
     return SHT_OK;
 }
 
-// Evanescent-skip tables of the tensor-core forms: built on first use (one
-// FP64 pass over the recurrence, synchronous), or detached when disabled.
+// Cost share of a tensor-core work item's setup and Delta epilogue, in degrees
+// of its recurrence (fitted to per-CTA clock counts: about 1.5 stages).
+constexpr long long kItemOverhead = 48;
+
+// Work lists of a persistent launch: the items, in the order given, go one by
+// one to the list with the least cost so far (ties: the lowest list index),
+// which replays a work queue served in that order.  List b is items[off[b] ..
+// off[b + 1]), in serving order; off has nlists + 1 entries.
+void build_work_lists(int nitems, const long long *cost, int nlists, int *off, int *items)
+{
+    using Slot = std::pair<long long, int>;  // (cost so far, list)
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> q;
+    for (int b = 0; b < nlists; ++b) q.push({0, b});
+    std::vector<int> owner((size_t)nitems);
+    std::fill(off, off + nlists + 1, 0);
+    for (int j = 0; j < nitems; ++j) {
+        const Slot t = q.top();
+        q.pop();
+        owner[j] = t.second;
+        ++off[t.second + 1];
+        q.push({t.first + cost[j], t.second});
+    }
+    for (int b = 0; b < nlists; ++b) off[b + 1] += off[b];
+    std::vector<int> fill(off, off + nlists);
+    for (int j = 0; j < nitems; ++j) items[fill[owner[j]]++] = j;
+}
+
 // The work lists of the persistent tensor-core launches for the plan's current
-// skip tables: a work queue served in m order (ring block minor) to the CTA
-// with the least work so far, replayed on the host.  The cost of an item is
-// the degrees its recurrence runs plus a fixed share for its setup and Delta
-// epilogue.
+// skip tables: items served in m order (ring block minor).  The cost of an
+// item is the degrees its recurrence runs plus a fixed share for its setup and
+// Delta epilogue.
 int ensure_sched(sht_plan_s *p, cudaStream_t st)
 {
     sht::DevPlan &d = p->dp;
@@ -681,21 +705,10 @@ int ensure_sched(sht_plan_s *p, cudaStream_t st)
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "work lists");
     }
-    constexpr long long kItemOverhead = 48;
-    using Slot = std::pair<long long, int>;  // (work so far, CTA)
-    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> q;
-    for (int b = 0; b < G; ++b) q.push({0, b});
-    std::vector<int> owner((size_t)nitems), host((size_t)G + 1 + nitems, 0);
-    for (int j = 0; j < nitems; ++j) {
-        const Slot t = q.top();
-        q.pop();
-        owner[j] = t.second;
-        ++host[t.second + 1];
-        q.push({t.first + (p->lmax - j / nrb + 1 - 64LL * g0[j]) + kItemOverhead, t.second});
-    }
-    for (int b = 0; b < G; ++b) host[b + 1] += host[b];
-    std::vector<int> fill(host.begin(), host.begin() + G);
-    for (int j = 0; j < nitems; ++j) host[G + 1 + fill[owner[j]]++] = j;
+    std::vector<long long> cost((size_t)nitems);
+    for (int j = 0; j < nitems; ++j) cost[j] = (p->lmax - j / nrb + 1 - 64LL * g0[j]) + kItemOverhead;
+    std::vector<int> host((size_t)G + 1 + nitems, 0);
+    build_work_lists(nitems, cost.data(), G, host.data(), host.data() + G + 1);
     if (!p->sched) {
         e = cudaMalloc(&p->sched, host.size() * sizeof(int));
         if (e != cudaSuccess) {
@@ -714,6 +727,9 @@ int ensure_sched(sht_plan_s *p, cudaStream_t st)
     return SHT_OK;
 }
 
+// Evanescent-skip tables of the tensor-core forms: built on first use (one
+// FP64 pass over the recurrence, synchronous), or detached when disabled; then
+// the work lists for that setting.
 int ensure_warm(sht_plan_s *p, cudaStream_t st)
 {
     sht::DevPlan &d = p->dp;
@@ -1139,6 +1155,16 @@ int sht_skip_evanescent(sht_plan_t p, int enable)
     return SHT_OK;
 }
 
+int sht_work_lists(int nitems, const long long *cost, int nlists, int *off, int *items)
+{
+    if (nitems < 0 || nlists < 1 || !off || (nitems > 0 && (!cost || !items)))
+        return fail(SHT_EINVAL, "sht_work_lists: bad arguments");
+    for (int j = 0; j < nitems; ++j)
+        if (cost[j] < 0) return fail(SHT_EINVAL, "sht_work_lists: negative cost of item %d", j);
+    build_work_lists(nitems, cost, nlists, off, items);
+    return SHT_OK;
+}
+
 int sht_debug_withhold_stage(sht_plan_t p, int stage)
 {
     g_err.clear();
@@ -1483,7 +1509,7 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
             // for its setup and Delta epilogue
             for (int m = 0; m <= p->mmax; ++m)
                 for (int rb = 0; rb < nrb; ++rb)
-                    items.push_back({(long long)(p->lmax - m + 1) - 64LL * g0[(size_t)m * nrb + rb] + 48,
+                    items.push_back({(long long)(p->lmax - m + 1) - 64LL * g0[(size_t)m * nrb + rb] + kItemOverhead,
                                      make_int4(i, m, rb, 0)});
             for (int r : p->rings_smooth_h) smooth.push_back(make_int2(i, r));
             for (int r : p->rings_blue_h) blue.push_back(make_int2(i, r));
@@ -1497,22 +1523,14 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
         int nsm_tc = 0;
         cudaDeviceGetAttribute(&nsm_tc, cudaDevAttrMultiProcessorCount, q->device);
-        const int G = std::max(1, std::min((int)items.size(), nsm_tc));
-        using Slot = std::pair<long long, int>;
-        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
-        for (int b = 0; b < G; ++b) heap.push({0, b});
-        std::vector<int> owner(items.size()), coff((size_t)G + 1, 0);
-        for (size_t j = 0; j < items.size(); ++j) {
-            const Slot t = heap.top();
-            heap.pop();
-            owner[j] = t.second;
-            ++coff[t.second + 1];
-            heap.push({t.first + items[j].cost, t.second});
-        }
-        for (int b = 0; b < G; ++b) coff[b + 1] += coff[b];
-        std::vector<int> fill(coff.begin(), coff.begin() + G);
-        std::vector<int4> w(items.size());
-        for (size_t j = 0; j < items.size(); ++j) w[fill[owner[j]]++] = items[j].w;
+        const int n = (int)items.size();
+        const int G = std::max(1, std::min(n, nsm_tc));
+        std::vector<long long> cost((size_t)n);
+        for (int j = 0; j < n; ++j) cost[j] = items[j].cost;
+        std::vector<int> coff((size_t)G + 1), order((size_t)n);
+        build_work_lists(n, cost.data(), G, coff.data(), order.data());
+        std::vector<int4> w((size_t)n);
+        for (int j = 0; j < n; ++j) w[j] = items[order[j]].w;
         q->ctas = G;
         q->nitems = (int)w.size();
         q->n_smooth = (int)smooth.size();

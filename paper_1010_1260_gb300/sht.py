@@ -88,6 +88,8 @@ def lib():
             L.sht_set_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_debug_withhold_stage.argtypes = [P, I]
             L.sht_skip_evanescent.argtypes = [P, I]
+            L.sht_work_lists.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), I, ctypes.POINTER(I),
+                                         ctypes.POINTER(I)]
             L.sht_map2alm.argtypes = [P, V, V, I, I, V]
             L.sht_map2alm_batch.argtypes = [P, I, V, V, I, I, V]
             L.sht_set_ring_weights.argtypes = [P, V]
@@ -99,7 +101,8 @@ def lib():
                       "sht_profile_read", "sht_sync", "sht_multi_create", "sht_multi_alm2map",
                       "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
                       "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage", "sht_map2alm",
-                      "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent"):
+                      "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent",
+                      "sht_work_lists"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -111,6 +114,20 @@ def check(rc: int):
 
 
 STAGES = ("legendre", "ring", "adj_ring", "adj_legendre", "operand_prep")
+
+
+def work_lists(costs, nlists: int):
+    """The library's work lists (sht_work_lists): items served in order to the
+    list with the least total cost so far.  Returns (off, items) as int32
+    arrays: list b is items[off[b]:off[b + 1]]."""
+    import numpy as np
+    c = np.ascontiguousarray(np.asarray(costs, dtype=np.int64))
+    off = np.zeros(int(nlists) + 1, dtype=np.int32)
+    items = np.zeros(max(1, c.size), dtype=np.int32)
+    check(lib().sht_work_lists(int(c.size), c.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), int(nlists),
+                               off.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               items.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return off, items[:c.size]
 
 
 def kernel_launches() -> int:
