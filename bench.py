@@ -74,6 +74,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The maximum of x over the ranks of the initialised process group (x
+    itself without one): the step time every whole-job figure divides by."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batch_seeds(rank: int, maps: int):
+    """Seeds of the maps of one rank's batch: disjoint across ranks (weak scaling)."""
+    return [(3, rank * maps + b) for b in range(maps)]
+
+
 def workload(args):
     return {"workload": "alm2map HEALPix nside=%d lmax=mmax=%d batch=%d" % (args.nside, args.lmax, args.maps),
             "grid": "healpix", "nside": args.nside, "lmax": args.lmax, "mmax": args.lmax,
@@ -278,8 +295,8 @@ def run_ours(args):
     L, B = args.lmax, args.maps
     plan = sht.Plan(sht.healpix(args.nside), L)
     alm_h = np.empty((B, plan.nalm), dtype=np.complex128)
-    for b in range(B):
-        alm_h[b] = inputs.gaussian_alm(L, L, (3, rank * B + b))[0]
+    for b, seed in enumerate(batch_seeds(rank, B)):
+        alm_h[b] = inputs.gaussian_alm(L, L, seed)[0]
     alm = torch.from_numpy(alm_h).to(dev)
     out = torch.empty((B, plan.npix), dtype=sht.MAP_DTYPE[args.prec], device=dev)
     stream = torch.cuda.current_stream()
@@ -322,11 +339,8 @@ def run_ours(args):
     plan.profile(False)
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+        ms = max_over_ranks(ms, dev)
+        torch.distributed.barrier()
     torch.cuda.synchronize()
 
     # the plain FP64 GPU path on the same batch, for the headline comparison
@@ -345,11 +359,7 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1) / args.fp64_steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms64], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms64 = float(t.item())
+        ms64 = max_over_ranks(ms64, dev)
         fp64_path = {"value": world * B / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                      "steps": args.fp64_steps, "speedup_of_headline": ms64 / ms}
         del out64
@@ -389,11 +399,7 @@ def run_ours(args):
         plan.alm2map_host_stream([a_pins[k % 2] for k in range(args.e2e_steps)], args.prec,
                                  outs=[m_pins[k % 2] for k in range(args.e2e_steps)])
         dt = (time.perf_counter() - t0) / args.e2e_steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dev)
         e2e = {"value": world * B / dt, "unit": UNIT, "h2d_bytes_per_step": int(a_pins[0].numel() * 16),
                "d2h_bytes_per_step": int(m_pins[0].numel() * m_pins[0].element_size()), "ms_per_step": dt * 1000,
                "steps": args.e2e_steps, "pipelined": True}
@@ -427,11 +433,7 @@ def run_ours(args):
         cst = plan.profile_read()
         plan.profile(False)
         cms = c0.elapsed_time(c1) / args.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([cms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            cms = float(t.item())
+        cms = max_over_ranks(cms, dev)
         cached = {"value": world * B / (cms * 1e-3), "unit": UNIT, "ms_per_step": cms, "steps": args.steps,
                   "stages_ms_per_step": {k: v[0] / args.steps for k, v in cst.items() if v[1]},
                   "lambda_bytes": plan.lambda_cache_bytes(args.prec), "build_s": build_s, "clocks": cclocks,
@@ -521,11 +523,7 @@ def run_requests(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, torch.device("cuda", torch.cuda.current_device()))
         res[prec] = {"ms_per_step": ms, "requests_per_s": world * args.requests / (ms * 1e-3),
                      "gpu_launches_per_step": (sht.kernel_launches() - n0) / args.steps}
         multi.close()
