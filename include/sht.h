@@ -174,6 +174,13 @@ long long sht_lambda_cache_bytes(sht_plan_t plan, int prec);
  * a negative cost. */
 int sht_work_lists(int nitems, const long long *cost, int nlists, int *off, int *items);
 
+/* Test hook: enable = 0 makes the plan's later tensor-core launches take their
+ * work items round robin (CTA b runs items b, b + G, ...) instead of the
+ * lists above, enable = 1 restores the lists.  The maps are the same either
+ * way (each item's arithmetic does not depend on its CTA); only the balance
+ * differs.  SHT_EINVAL for a NULL plan. */
+int sht_debug_work_lists(sht_plan_t plan, int enable);
+
 /* Evanescent skip of the tensor-core forms (on by default).  For large m
  * near the poles lambda_lm is far below the FP32 range for many degrees (the
  * region below the turning point, where Algorithm 2's rescaling keeps the

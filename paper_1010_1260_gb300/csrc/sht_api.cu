@@ -49,6 +49,7 @@ struct sht_plan_s {
     void *warm = nullptr;         // the skip tables (one allocation), built on first use
     int *sched = nullptr;         // the tensor-core work lists (DevPlan::sched_off, sched_items)
     int sched_skip = -1;          // skip setting the lists were built for (-1: none yet)
+    bool sched_off = false;       // test hook: round robin instead of the lists
     std::vector<double> wring_h;  // pixel quadrature weight per ring (host copy)
     double *wring_d = nullptr;    // the same on the device (DevPlan::wring)
     size_t lcache_bytes[4] = {};
@@ -688,6 +689,10 @@ int ensure_sched(sht_plan_s *p, cudaStream_t st)
     const int want = d.skip_g ? 1 : 0;
     const int nrb = (p->npairs + 127) / 128;
     const int nitems = nrb * (p->mmax + 1);
+    if (p->sched_off) {
+        d.sched_ctas = 0;
+        return SHT_OK;
+    }
     if (p->sched && p->sched_skip == want) {
         d.sched_off = p->sched;
         d.sched_items = p->sched + d.sched_ctas + 1;
@@ -1162,6 +1167,14 @@ int sht_work_lists(int nitems, const long long *cost, int nlists, int *off, int 
     for (int j = 0; j < nitems; ++j)
         if (cost[j] < 0) return fail(SHT_EINVAL, "sht_work_lists: negative cost of item %d", j);
     build_work_lists(nitems, cost, nlists, off, items);
+    return SHT_OK;
+}
+
+int sht_debug_work_lists(sht_plan_t p, int enable)
+{
+    if (!p) return fail(SHT_EINVAL, "sht_debug_work_lists: NULL plan");
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->sched_off = !enable;
     return SHT_OK;
 }
 

@@ -88,6 +88,7 @@ def lib():
             L.sht_set_tiles.argtypes = [P, ctypes.POINTER(I), I]
             L.sht_debug_withhold_stage.argtypes = [P, I]
             L.sht_skip_evanescent.argtypes = [P, I]
+            L.sht_debug_work_lists.argtypes = [P, I]
             L.sht_work_lists.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), I, ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.sht_map2alm.argtypes = [P, V, V, I, I, V]
@@ -102,7 +103,7 @@ def lib():
                       "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
                       "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage", "sht_map2alm",
                       "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent",
-                      "sht_work_lists"):
+                      "sht_work_lists", "sht_debug_work_lists"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -285,6 +286,11 @@ class Plan:
         """Test hook: the next tensor-core Legendre launch skips one stage's
         operand copies in its first CTA, so its bounded wait runs out."""
         check(lib().sht_debug_withhold_stage(self._h, int(stage)))
+
+    def debug_work_lists(self, enable: bool):
+        """Test hook: False makes the tensor-core launches take their items
+        round robin instead of the balanced work lists (same maps)."""
+        check(lib().sht_debug_work_lists(self._h, 1 if enable else 0))
 
     # ---------------------------------------------------------- analysis --
     def map2alm(self, maps: torch.Tensor, niter: int = 0, out: torch.Tensor | None = None,
