@@ -6,7 +6,13 @@ intrinsics replaced by host equivalents) and checked against IEEE-754.
   correctly rounded product, fma(A, x, +0), bit for bit, including exact ties
   (A with a short significand such as 3 or 1.5) and x = 0;
 - rn_f32 (FP64 -> FP32 on the integer pipe) must round to nearest with ties
-  away from zero, and flush values below the FP32 normal range to signed zero.
+  away from zero, and flush values below the FP32 normal range to signed zero;
+- split_pieces (the operand pieces of the tensor-core forms) must leave exact
+  residuals and rounded (not truncated) pieces, each later piece at most half
+  an ulp of the one before (|lo| <= 2^-11 |v| for TF32; |mid| <= 2^-8 |v|,
+  |lo| <= 2^-16 |v| for BF16): the bounds on the products the forms leave
+  out.  2 TF32 pieces rebuild the value to 2^-23 relative, 3 BF16 pieces
+  exactly (24 bits), both floored at 2^-126 below the FP32 normal range.
 """
 import os
 import re
@@ -89,8 +95,49 @@ int main() {
                 std::printf("rn_f32(%a) = %a, want %a\n", d, (double)got, (double)want);
         }
     }
-    std::printf("mul_coef %ld/%ld bad, rn_f32 %ld/%ld bad\n", bad_mul, n_mul, bad_rn, n_rn);
-    return (bad_mul || bad_rn) ? 1 : 0;
+    // operand pieces: exact residuals and the reconstruction bounds
+    long bad_split = 0, n_split = 0;
+    for (long i = 0; i < 2000000; ++i) {
+        const float v = (float)((uni() - 0.5) * std::ldexp(1.0, (int)(nxt() % 200) - 100));
+        if (v == 0.0f) continue;
+        uint32_t t[2], b[3];
+        sht::split_pieces<false, 2>(v, t);
+        sht::split_pieces<true, 3>(v, b);
+        double rt = v, rb = v;
+        bool ok = true;
+        for (int q = 0; q < 2; ++q) {
+            const double pq = __uint_as_float(t[q]);
+            ok = ok && ((t[q] & 0x1FFFu) == 0u);                       // a TF32 value
+            ok = ok && ((double)(float)(rt - pq) == rt - pq);          // exact residual
+            rt -= pq;
+        }
+        for (int q = 0; q < 3; ++q) {
+            const double pq = __uint_as_float(b[q] & 0xFFFF0000u);
+            ok = ok && ((double)(float)(rb - pq) == rb - pq);
+            rb -= pq;
+        }
+        const double av = std::fabs((double)v);
+        const double t1 = std::fabs((double)__uint_as_float(t[1]));
+        const double b1 = std::fabs((double)__uint_as_float(b[1] & 0xFFFF0000u));
+        const double b2 = std::fabs((double)__uint_as_float(b[2] & 0xFFFF0000u));
+        if (av >= 0x1p-100) {
+            // rounded (not truncated) pieces: each later piece at most half an ulp
+            // of the one before; 3 BF16 pieces hold all 24 bits of an FP32 value
+            ok = ok && t1 <= 0x1.02p-11 * av && std::fabs(rt) <= std::ldexp(av, -23);
+            ok = ok && b1 <= 0x1.02p-8 * av && b2 <= 0x1.04p-16 * av && rb == 0.0;
+        } else {
+            // later pieces may fall below the FP32 normal range: the relative
+            // bounds, floored at its minimum
+            ok = ok && std::fabs(rt) <= std::fmax(std::ldexp(av, -23), 0x1p-126);
+            ok = ok && std::fabs(rb) <= 0x1p-126;
+        }
+        ++n_split;
+        if (!ok && ++bad_split <= 3)
+            std::printf("split_pieces(%a): residuals %a (tf32x2) %a (bf16x3)\n", (double)v, rt, rb);
+    }
+    std::printf("mul_coef %ld/%ld bad, rn_f32 %ld/%ld bad, split %ld/%ld bad\n", bad_mul, n_mul, bad_rn, n_rn,
+                bad_split, n_split);
+    return (bad_mul || bad_rn || bad_split) ? 1 : 0;
 }
 """
 
@@ -107,7 +154,7 @@ def program():
         pytest.skip("g++ not available")
     src = open(SRC).read()
     parts = [_extract(src, "__device__ __forceinline__ float rn_f32(double d)",
-                      "__device__ __forceinline__ uint32_t rn_tf32_bits"),
+                      "// The coefficient product A_l x of the recurrence"),
              _extract(src, "struct XInt {", "// degrees (by position in the stage)")]
     body = "\n".join(parts)
     body = re.sub(r"__device__\s+__forceinline__", "static inline", body)
@@ -126,4 +173,4 @@ def program():
 def test_integer_product_and_rounding_match_ieee(program):
     r = subprocess.run([program], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-2000:]
-    assert "mul_coef 0/" in r.stdout and "rn_f32 0/" in r.stdout
+    assert "mul_coef 0/" in r.stdout and "rn_f32 0/" in r.stdout and "split 0/" in r.stdout
