@@ -132,7 +132,11 @@ int sht_map2alm_batch(sht_plan_t plan, int nbatch, const void *map_dev, void *al
 int sht_set_ring_weights(sht_plan_t plan, const double *w);
 int sht_ring_weights(sht_plan_t plan, double *w);
 
-/* Batched forms: nbatch >= 0 maps, strides nalm and npix.  nbatch == 0 is a no-op. */
+/* Batched forms of sht_alm2map and sht_map2alm_adjoint (Eq. alm2mapDef and its
+ * transpose, map by map): nbatch >= 0 maps stored back to back, alm_dev
+ * nbatch x nalm complex128 and map_dev nbatch x npix of the form's map type
+ * (float64 for SHT_FP64, float32 otherwise); the caller owns both buffers.
+ * nbatch == 0 is a no-op.  Errors as for the single-map calls. */
 int sht_alm2map_batch(sht_plan_t plan, int nbatch, const void *alm_dev, void *map_dev,
                       int prec, void *stream);
 int sht_map2alm_adjoint_batch(sht_plan_t plan, int nbatch, const void *map_dev, void *alm_dev,
