@@ -72,7 +72,9 @@ typedef enum {
     SHT_FP64 = 0,      /* FP64 recurrence, FP64 contraction, FP64 ring FFT; float64 map */
     SHT_FP32_TC = 1,   /* FP64 recurrence, 3xTF32 tensor-core contraction, FP32 ring FFT; float32 map */
     SHT_BF16X3_TC = 2, /* FP64 recurrence, split-BF16 (hi/lo, 3 products) tensor-core contraction,
-                          FP32 ring FFT; float32 map */
+                          FP32 ring FFT; float32 map.  Does NOT meet a 1e-6 relative-L2 error:
+                          two 8-bit pieces carry about 16 significant bits (about 4.9e-6 per
+                          map at lmax 2048); use SHT_BF16X6_TC for 1e-6 */
     SHT_BF16X6_TC = 3  /* as SHT_BF16X3_TC with three BF16 pieces and 6 products (hi*hi, hi*mid,
                           mid*hi, hi*lo, mid*mid, lo*hi) */
 } sht_prec;
@@ -268,8 +270,11 @@ int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *
  * context builds each plan's operand buffer and skip tables (synchronous);
  * while the context runs, the plans' own transforms must not run concurrently
  * (they share those buffers); a bounded device wait that runs out is reported
- * by sht_sync(plans[0]).  1 <= nreq <= 256; all plans on one device; the
- * plans must outlive the context.
+ * by sht_sync(plans[0]).  A plan may appear more than once (requests of
+ * equal grid and band limit): in the tensor-core forms every repeat gets its
+ * own operand buffer, allocated by sht_multi_create (tc operand bytes of that
+ * plan each).  1 <= nreq <= 256; all plans on one device; the plans must
+ * outlive the context.
  * sht_alm2map_multi = create + run + stream synchronize + destroy. */
 typedef struct sht_multi_s *sht_multi_t;
 int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht_multi_t *out);

@@ -22,6 +22,7 @@
 
 namespace sht {
 const DevPlan *plan_dev(sht_plan_t p);
+void plan_fp64_tiles(sht_plan_t p, int *bc, int *ring_g);
 int plan_device(sht_plan_t p);
 std::mutex *plan_mutex(sht_plan_t p);
 int record_error(int code, const char *msg);
@@ -89,10 +90,13 @@ extern "C" int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         // The Legendre step writes every (ring, m) entry of the scratch that
         // the ring step reads, so nothing has to be cleared between calls.
-        e = sht::launch_legendre_fwd_fp64(P, static_cast<const double2 *>(alm_dev), scratch, nbatch, 0, st);
+        // The plan's tile shapes (sht_autotune) apply here as in sht_alm2map_batch.
+        int bc = 0, rg = 0;
+        sht::plan_fp64_tiles(plan, &bc, &rg);
+        e = sht::launch_legendre_fwd_fp64(P, static_cast<const double2 *>(alm_dev), scratch, nbatch, bc, st);
         if (e == cudaSuccess) {
             sht::count_launch();
-            e = sht::launch_ring_synth_fp64(P, scratch, static_cast<double *>(map_dev), nbatch, 0, st);
+            e = sht::launch_ring_synth_fp64(P, scratch, static_cast<double *>(map_dev), nbatch, rg, st);
             if (e == cudaSuccess)
                 for (int i = 0; i < sht::ring_launches(P); ++i) sht::count_launch();
         }

@@ -1443,6 +1443,9 @@ struct sht_multi_s {
     int n_smooth = 0, n_blue = 0, smooth_cap = 0, blue_cap = 0;
     int *d_counter = nullptr;
     void *d_delta = nullptr;
+    // tensor-core forms: a request whose plan already appeared earlier in the
+    // list gets its own B-operand buffer (nullptr: the plan's own)
+    std::vector<void *> bbuf_own;
 };
 
 namespace {
@@ -1581,10 +1584,23 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         std::vector<int2> smooth, blue;
         std::vector<sht::DevPlan> dp(nreq);
         size_t dofs = 0;
+        q->bbuf_own.assign(nreq, nullptr);
         for (int i = 0; i < nreq; ++i) {
             sht_plan_s *p = plans[i];
             std::lock_guard<std::mutex> lk(p->mu);
             if ((rc = ensure_tc(p, prec)) || (rc = ensure_warm(p, nullptr))) break;
+            if (std::find(plans, plans + i, p) != plans + i) {
+                // the plan serves an earlier request too: its operand buffer is taken
+                void *b = nullptr;
+                cudaError_t e = cudaMalloc(&b, sht::tc_bbuf_bytes(p->tc, prec));
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = fail(SHT_ENOMEM, "operand buffer of repeated plan %d: %s", i, cudaGetErrorString(e));
+                    break;
+                }
+                q->allocs.push_back(b);
+                q->bbuf_own[i] = b;
+            }
             dp[i] = p->dp;
             const int nrb = (p->npairs + 127) / 128;
             for (int m = 0; m <= p->mmax; ++m)
@@ -1652,13 +1668,15 @@ extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void
         sht::MultiTcPtrs mp{};
         for (int i = 0; i < q->nreq; ++i) {
             const sht_plan_s *p = q->plans[i];
-            mp.bbuf[i] = p->tc.bbuf;
+            sht::TcWork w = p->tc;
+            if (q->bbuf_own[i]) w.bbuf = q->bbuf_own[i];
+            mp.bbuf[i] = w.bbuf;
             mp.seg[i] = bf16 ? p->tc.seg_bf16 : p->tc.seg_tf32;
             mp.delta[i] = static_cast<char *>(q->d_delta) + q->delta_ofs[i];
             mp.map[i] = map_dev[i];
             mp.cta_off = q->d_cta_off;
             mp.ctas = q->ctas;
-            cudaError_t e = sht::launch_tc_prep(p->dp, p->tc, q->prec, static_cast<const double2 *>(alm_dev[i]), 1, st);
+            cudaError_t e = sht::launch_tc_prep(p->dp, w, q->prec, static_cast<const double2 *>(alm_dev[i]), 1, st);
             if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
             g_launches.fetch_add(1, std::memory_order_relaxed);
         }
@@ -1712,6 +1730,11 @@ extern "C" int sht_alm2map_multi(int nreq, const sht_plan_t *plans, const void *
 // Internal hooks for other translation units of the library (not C ABI).
 namespace sht {
 const DevPlan *plan_dev(sht_plan_t p) { return p ? &p->dp : nullptr; }
+void plan_fp64_tiles(sht_plan_t p, int *bc, int *ring_g)
+{
+    *bc = p ? p->fp64_bc : 0;
+    *ring_g = p ? p->fp64_ring_g : 0;
+}
 int plan_device(sht_plan_t p) { return p ? p->device : -1; }
 std::mutex *plan_mutex(sht_plan_t p) { return p ? &p->mu : nullptr; }
 int record_error(int code, const char *msg) { return fail(code, "%s", msg); }

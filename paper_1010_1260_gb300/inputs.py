@@ -102,3 +102,45 @@ def sample_rings(nrings: int, count: int, seed: int) -> np.ndarray:
             break
         sel.add(int(r))
     return np.asarray(sorted(sel), dtype=np.int32)
+
+
+def _largest_prime_factor(n: int) -> int:
+    best, p = 1, 2
+    while p * p <= n:
+        while n % p == 0:
+            best, n = p, n // p
+        p += 1
+    return max(best, n) if n > 1 else best
+
+
+def healpix_ring_sample(nside: int, count: int, seed: int, large_prime: int = 29, n_large: int = 12,
+                        n_smooth_cap: int = 12):
+    """A seeded, sorted sample of HEALPix RING-scheme ring indices stratified by
+    ring class: both polar rings, the equator, ``n_large`` polar-cap rings whose
+    length 4 i has a prime factor >= ``large_prime``, ``n_smooth_cap`` cap rings
+    whose length has none, and equatorial-belt rings for the rest.  Returns
+    (rings, classes) with classes[r] one of "pole", "equator", "cap_large_prime",
+    "cap_smooth", "belt"."""
+    nrings = 4 * nside - 1
+    rng = np.random.default_rng(seed)
+
+    def cap_i(r):  # ring index -> i of the Gorski numbering (1 .. 2 nside), or None in the belt
+        i = r + 1 if r < 2 * nside else nrings - r
+        return i if i < nside else None
+
+    cls = {}
+    cls[0] = cls[nrings - 1] = "pole"
+    cls[nrings // 2] = "equator"
+    caps_large = [r for r in range(nrings) if r not in cls and cap_i(r) is not None
+                  and _largest_prime_factor(cap_i(r)) >= large_prime]
+    caps_smooth = [r for r in range(nrings) if r not in cls and cap_i(r) is not None
+                   and _largest_prime_factor(cap_i(r)) < large_prime]
+    belt = [r for r in range(nrings) if r not in cls and cap_i(r) is None]
+    for pool, k, name in ((caps_large, n_large, "cap_large_prime"), (caps_smooth, n_smooth_cap, "cap_smooth")):
+        for r in rng.choice(pool, size=min(k, len(pool)), replace=False) if pool else []:
+            cls[int(r)] = name
+    rest = max(0, count - len(cls))
+    for r in rng.choice(belt, size=min(rest, len(belt)), replace=False) if belt else []:
+        cls[int(r)] = "belt"
+    rings = np.asarray(sorted(cls), dtype=np.int32)
+    return rings, {int(r): cls[int(r)] for r in rings}

@@ -143,6 +143,42 @@ def test_multi_log_uniform_requests(oracle_mod, sht):
     assert np.max(np.abs(outs[i].cpu().numpy() - want)) / np.max(np.abs(want)) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6_tc"])
+def test_multi_repeated_plan(sht, prec):
+    """One plan serving several requests with different coefficients: every
+    request's map equals that plan's own transform of its coefficients."""
+    p, q = sht.Plan(sht.healpix(32), 64), sht.Plan(sht.healpix(20), 40)
+    plans = [p, p, q, p]
+    alms = [torch.from_numpy(inputs.gaussian_alm(pl.lmax, pl.lmax, (9, i))[0]).cuda() for i, pl in enumerate(plans)]
+    outs = sht.Multi(plans, prec).alm2map(alms)
+    torch.cuda.synchronize()
+    for pl, a, o in zip(plans, alms, outs):
+        assert torch.equal(o, pl.alm2map(a, prec))
+    assert not torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_tc"])
+def test_multi_largest_request_vs_oracle(oracle_mod, sht, prec):
+    """The largest of 256 log-uniform requests (lmax 2048, nside 1024) inside a
+    multi call, against the oracle on a stratified ring sample."""
+    lmaxs = inputs.request_lmax(256, 4)
+    i = int(np.argmax(lmaxs))
+    L = int(lmaxs[i])
+    plans, alms = _requests(sht, lmaxs)
+    outs = sht.Multi(plans, prec).alm2map(alms)
+    torch.cuda.synchronize()
+    nside = L // 2
+    rings, _ = inputs.healpix_ring_sample(nside, 24, 5, n_large=6, n_smooth_cap=4)
+    want = oracle_mod.alm2map(oracle_mod.healpix_grid(nside), L, L, alms[i].cpu().numpy()[None], rings=rings)[0]
+    got = outs[i].double().cpu().numpy()
+    ok = np.isfinite(want)
+    d = got[ok] - want[ok]
+    if prec == "fp64":
+        assert np.max(np.abs(d)) / np.max(np.abs(want[ok])) < 1e-10
+    else:
+        assert np.linalg.norm(d) / np.linalg.norm(want[ok]) < 1e-5
+
+
 def test_multi_rejects_bad_arguments(sht):
     import ctypes
     L = sht.lib()

@@ -2,8 +2,10 @@
 contraction (3xTF32, split-BF16 with 3 products, BF16 with 3 pieces and 6
 products), FP32 ring step.  Error per map is the relative L2 norm against the
 FP64 oracle, ||s - s_ref||_2 / ||s_ref||_2; targets: 1e-5 for the TF32 form,
-1e-6 for the BF16 forms (the 3-product BF16 form is reported, and checked
-against the bound its two 8-bit pieces allow, 3e-5)."""
+1e-6 for the BF16 forms.  The 3-product BF16 form (two 8-bit pieces, about 16
+significant bits) does NOT meet the 1e-6 target (it measures about 4.9e-6);
+it is checked against the bound its pieces allow, 3e-5, and the 6-product
+form is the one that meets 1e-6."""
 import numpy as np
 import pytest
 import torch
@@ -60,17 +62,20 @@ def test_tc_forms_vs_oracle(oracle_mod, sht, case, prec):
 @pytest.mark.parametrize("prec", ["fp32_tc", "bf16x6_tc"])
 def test_tc_full_size_sampled_rings(oracle_mod, sht, prec):
     """HEALPix nside 1024, lmax 2048, a batch of 64 maps (the benchmark's
-    workload); maps 0 and 63 checked on sampled rings, per map."""
+    workload): every map checked, per map, on a ring sample stratified by ring
+    class -- both poles, the equator, belt rings, polar-cap rings whose length
+    has a prime factor >= 29 and cap rings whose length has none."""
     og, sg = _grids(oracle_mod, sht, "hp", 1024)
     alm = inputs.batch_alm(2048, 2048, 3, 64)
     plan = sht.Plan(sg, 2048)
     out = plan.alm2map(torch.from_numpy(alm).cuda(), prec)
     plan.sync()
-    rings = inputs.sample_rings(og["nrings"], 10, 33)
-    for b in (0, 63):
-        want = oracle_mod.alm2map(og, 2048, 2048, alm[b: b + 1], rings=rings)[0]
-        got = out[b].double().cpu().numpy()
-        assert _rl2(got, want) < TOL[prec]
+    rings, cls = inputs.healpix_ring_sample(1024, 32, 33, n_large=8, n_smooth_cap=6)
+    assert sorted(set(cls.values())) == ["belt", "cap_large_prime", "cap_smooth", "equator", "pole"]
+    want = oracle_mod.alm2map(og, 2048, 2048, alm, rings=rings)
+    got = out.double().cpu().numpy()
+    errs = [_rl2(got[b], want[b]) for b in range(64)]
+    assert max(errs) < TOL[prec], (prec, max(errs))
 
 
 def test_tc_batch_equals_singles(sht):

@@ -31,6 +31,32 @@ def _nerr(a, b):
     return float(torch.max(torch.abs(a - b)) / torch.max(torch.abs(b)))
 
 
+def test_noalloc_allocates_no_device_memory(sht):
+    """On a plan that has never run a transform (so it has no workspace yet),
+    a call leaves the device's free memory unchanged.  The same call on
+    another plan of the same shape runs before, so that loading the library's
+    kernels (which reserves their code and the static scratch) is not counted."""
+    L = sht.lib()
+    stream = torch.cuda.current_stream()
+    warm = sht.Plan(sht.healpix(64), 128)
+    a0 = torch.from_numpy(inputs.batch_alm(128, 128, 400, 3)).cuda()
+    m0 = torch.empty((3, warm.npix), dtype=torch.float64, device="cuda")
+    sht.check(L.sht_alm2map_noalloc(warm.handle, 3, a0.data_ptr(), m0.data_ptr(), stream.cuda_stream))
+    plan = sht.Plan(sht.healpix(64), 128)
+    alm = torch.from_numpy(inputs.batch_alm(128, 128, 403, 3)).cuda()
+    out = torch.empty((3, plan.npix), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    sht.check(L.sht_alm2map_noalloc(plan.handle, 3, alm.data_ptr(), out.data_ptr(), stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    # the ordinary entry point on the same plan does grow its workspace
+    ref = torch.empty_like(out)
+    sht.check(L.sht_alm2map_batch(plan.handle, 3, alm.data_ptr(), ref.data_ptr(), 0, stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert _nerr(out, ref) < TOL64
+
+
 def test_noalloc_matches_batch_entry_point_twice(sht):
     L = sht.lib()
     plan = sht.Plan(sht.healpix(64), 128)
