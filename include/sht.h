@@ -187,6 +187,19 @@ int sht_work_lists(int nitems, const long long *cost, int nlists, int *off, int 
  * differs.  SHT_EINVAL for a NULL plan. */
 int sht_debug_work_lists(sht_plan_t plan, int enable);
 
+/* Test hook: which kernel runs the FP32 ring step (Eq. Delta2map) of the
+ * tensor-core forms.  Two kernels exist: a register-FFT kernel for even rings
+ * whose half-length N is a power of two in [256, 4096] (direct transform) or
+ * at most 2048 (Bluestein's algorithm with a power-of-two length), and the
+ * shared-memory mixed-radix kernel for any ring.  mode 0 (default): the
+ * register kernel for the rings it runs with Bluestein's algorithm, the
+ * shared-memory kernel for the others; mode 1: the shared-memory kernel for
+ * every ring; mode 2: the register kernel for every ring it can run.  The
+ * kernels round differently (each within the form's tolerance), so maps
+ * differ in the last bits between modes.  SHT_EINVAL for a NULL plan or
+ * another mode. */
+int sht_debug_ring_kernel(sht_plan_t plan, int mode);
+
 /* Evanescent skip of the tensor-core forms (on by default).  For large m
  * near the poles lambda_lm is far below the FP32 range for many degrees (the
  * region below the turning point, where Algorithm 2's rescaling keeps the

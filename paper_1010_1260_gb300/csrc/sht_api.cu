@@ -37,6 +37,14 @@ struct sht_plan_s {
     void *ws = nullptr;  // Delta workspace
     size_t ws_bytes = 0;
     std::vector<int> rings_smooth_h, rings_blue_h;  // host copies of the ring lists
+    // FP32 ring step: the register-FFT kernel's ring list and the rings left to
+    // the shared-memory kernel, per kernel choice (sht_debug_ring_kernel)
+    struct RfSet {
+        const int *rings = nullptr, *rest_s = nullptr, *rest_b = nullptr;
+        std::vector<int> rings_h, rest_s_h, rest_b_h;
+    } rf_set[3];
+    int rf_mode = 0;
+    std::vector<int> rf_len_h;
     sht::TcWork tc;      // tensor-core forms: segment tables, status word, B-operand buffer
     size_t tc_bytes = 0;
     // tile shapes (sht_autotune): results do not depend on them
@@ -324,6 +332,30 @@ void fft_pow2_forward(std::vector<double> &re, std::vector<double> &im)
     }
 }
 
+// Point the plan's FP32 ring lists at the set of its current kernel choice.
+void apply_rf_mode(sht_plan_s *p)
+{
+    const auto &f = p->rf_set[p->rf_mode];
+    DevPlan &d = p->dp;
+    d.rf_rings = f.rings;
+    d.rf_n = (int)f.rings_h.size();
+    d.rf_rest_smooth = f.rest_s;
+    d.rf_n_rest_smooth = (int)f.rest_s_h.size();
+    d.rf_rest_blue = f.rest_b;
+    d.rf_n_rest_blue = (int)f.rest_b_h.size();
+}
+
+// Cost of one (ring, pair of maps) unit of the register-FFT ring kernel, for
+// ordering its work: FFT work of length L = |rf_len|, twice for Bluestein
+// rings and for the two rounds of length 4096; shorter transforms leave
+// threads idle, so they count as 2048.
+double rf_cost(int rf_len)
+{
+    const int L = std::abs(rf_len);
+    if (L == 0) return 0.0;
+    return (rf_len < 0 ? 2.0 : 1.0) * (L == 4096 ? 2.0 : 1.0) * std::max(L, 2048) * std::log2((double)L);
+}
+
 int build_tables(sht_plan_s *p, const Rings &R)
 {
     const int L = p->lmax, M = p->mmax, nr = p->nrings;
@@ -505,6 +537,79 @@ int build_tables(sht_plan_s *p, const Rings &R)
             bh32.push_back(make_float2((float)(re[k] / Mb), (float)(im[k] / Mb)));
         }
     }
+    // FP32 ring step with the FFT in registers: the ring's FFT length and, for
+    // Bluestein rings, the chirp and chirp spectrum of that length (per distinct N)
+    std::vector<int> rflen(nr, 0);
+    std::vector<long long> rfco(nr, 0), rfbo(nr, 0);
+    std::vector<float2> rfch, rfbh;
+    std::map<int, std::pair<long long, long long>> rfwhere;
+    const bool rf_fits = (size_t)2 * (((M + 1 + 255) / 256) * 256) * 16 + (size_t)(4096 + 256) * 8 <= kMaxDynSmem;
+    for (int r = 0; r < nr && rf_fits; ++r) {
+        const int n = R.nphi[r];
+        if (n % 2) continue;
+        const int N = n / 2;
+        if ((N & (N - 1)) == 0 && N >= 256 && N <= 4096) {
+            rflen[r] = N;
+            continue;
+        }
+        if (N > 2048) continue;
+        int Lb = 256;
+        while (Lb < 2 * N - 1) Lb <<= 1;
+        rflen[r] = -Lb;
+        auto it = rfwhere.find(N);
+        if (it != rfwhere.end()) {
+            rfco[r] = it->second.first;
+            rfbo[r] = it->second.second;
+            continue;
+        }
+        rfco[r] = (long long)rfch.size();
+        rfbo[r] = (long long)rfbh.size();
+        rfwhere[N] = {rfco[r], rfbo[r]};
+        for (int t = 0; t < N; ++t) {
+            // c_t = e^{i pi t^2 / N}, t^2 reduced mod 2N for an exact angle
+            const long long q = ((long long)t * t) % (2LL * N);
+            const double a = kPi * (double)q / (double)N;
+            rfch.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+        std::vector<double> re(Lb, 0.0), im(Lb, 0.0);
+        for (int t = 0; t < N; ++t) {
+            const long long q = ((long long)t * t) % (2LL * N);
+            const double a = -kPi * (double)q / (double)N;
+            re[t] = std::cos(a);
+            im[t] = std::sin(a);
+            if (t > 0) {
+                re[Lb - t] = re[t];
+                im[Lb - t] = im[t];
+            }
+        }
+        fft_pow2_forward(re, im);
+        for (int k = 0; k < Lb; ++k) rfbh.push_back(make_float2((float)(re[k] / Lb), (float)(im[k] / Lb)));
+    }
+    // ring sets of the FP32 ring step per kernel choice (sht_debug_ring_kernel):
+    // 0 (default): the register kernel runs the rings it transforms with
+    // Bluestein's algorithm (N not a power of two), the shared-memory kernel the
+    // others (measured at nside 1024, 64 maps: register kernel 4.5 ms for the
+    // cap rings with a large prime factor against 6.1 ms, 2.0 ms against 3.0 ms
+    // for the other non-power-of-two caps; shared-memory kernel 3.0 ms for the
+    // equatorial belt against 3.2 ms); 1: shared-memory kernel for every ring;
+    // 2: register kernel for every ring it can run
+    std::vector<int> rfrings[3], rfrest_s[3], rfrest_b[3];
+    for (int mode = 0; mode < 3; ++mode)
+        for (int r = 0; r < nr; ++r) {
+            bool reg = rflen[r] != 0 && mode != 1;
+            if (mode == 0 && rflen[r] > 0) reg = false;
+            if (reg) {
+                rfrings[mode].push_back(r);
+            } else if (bmb[r] > 0) {
+                rfrest_b[mode].push_back(r);
+            } else {
+                rfrest_s[mode].push_back(r);
+            }
+        }
+    // by decreasing cost, rings of equal cost kept in ring order
+    for (auto &v : rfrings)
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return rf_cost(rflen[a]) > rf_cost(rflen[b]); });
+
     std::vector<double2> w2d(sht::kBlueMaxMb);
     std::vector<float2> w2f(sht::kBlueMaxMb);
     for (int q = 0; q < sht::kBlueMaxMb; ++q) {
@@ -563,6 +668,22 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, bh32, &d.bhat32))) return rc;
     if ((rc = upload(p, w2d, &d.w2_64))) return rc;
     if ((rc = upload(p, w2f, &d.w2_32))) return rc;
+    if ((rc = upload(p, rflen, &d.rf_len))) return rc;
+    if ((rc = upload(p, rfco, &d.rf_ch_ofs))) return rc;
+    if ((rc = upload(p, rfbo, &d.rf_bh_ofs))) return rc;
+    if ((rc = upload(p, rfch, &d.rf_ch32))) return rc;
+    if ((rc = upload(p, rfbh, &d.rf_bh32))) return rc;
+    for (int mode = 0; mode < 3; ++mode) {
+        auto &f = p->rf_set[mode];
+        if ((rc = upload(p, rfrings[mode], &f.rings)) || (rc = upload(p, rfrest_s[mode], &f.rest_s)) ||
+            (rc = upload(p, rfrest_b[mode], &f.rest_b)))
+            return rc;
+        f.rings_h = rfrings[mode];
+        f.rest_s_h = rfrest_s[mode];
+        f.rest_b_h = rfrest_b[mode];
+    }
+    p->rf_len_h = rflen;
+    apply_rf_mode(p);
 
     // tensor-core forms: (m, parity) segments of the B operand, padded to
     // whole stages of KC degrees per parity (KC = 8 for TF32, 16 for BF16)
@@ -779,6 +900,28 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
     return ensure_sched(p, st);
 }
 
+double rf_unit_cost(const sht_plan_s *p, int r) { return rf_cost(p->rf_len_h[r]); }
+
+// FP32 ring step of the tensor-core forms: the register-FFT kernel over the
+// plan's rf_rings, then the shared-memory kernel over the other rings (odd
+// lengths, long rings without a power-of-two transform); *nk = kernels launched.
+cudaError_t ring_step_fp32(sht_plan_s *p, const float2 *delta, float *map, int nb, cudaStream_t st, int *nk)
+{
+    *nk = 0;
+    cudaError_t e = sht::launch_ring_reg(p->dp, delta, map, nb, p->tc.status, st);
+    if (e != cudaSuccess) return e;
+    *nk += p->dp.rf_n > 0;
+    if (p->dp.rf_n_rest_smooth + p->dp.rf_n_rest_blue == 0) return cudaSuccess;
+    DevPlan q = p->dp;
+    q.rings_smooth = q.rf_rest_smooth;
+    q.n_smooth = q.rf_n_rest_smooth;
+    q.rings_blue = q.rf_rest_blue;
+    q.n_blue = q.rf_n_rest_blue;
+    e = sht::launch_ring_synth_mf(q, delta, map, nb, p->ring_g[0], p->ring_g[1], p->ring_nt, st);
+    *nk += sht::ring_launches(q);
+    return e;
+}
+
 // Precision forms: FP64 recurrence (or the plan-time Lambda operand, when
 // cached) + tensor-core contraction (groups of at most 64 maps), FP32 Delta,
 // FP32 ring step, float32 maps.
@@ -808,10 +951,10 @@ int alm2map_tc(sht_plan_s *p, int nbatch, const void *alm_dev, void *map_dev, in
         s1.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc launch");
         StageScope s2(p, SHT_STAGE_RING, st);
-        e = sht::launch_ring_synth_mf(p->dp, delta, map + (size_t)b0 * p->npix, nb, p->ring_g[0], p->ring_g[1],
-                                      p->ring_nt, st);
-        s2.done(e, sht::ring_launches(p->dp));
-        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_mf launch");
+        int nk = 0;
+        e = ring_step_fp32(p, delta, map + (size_t)b0 * p->npix, nb, st, &nk);
+        s2.done(e, nk);
+        if (e != cudaSuccess) return cuda_fail(e, "FP32 ring step launch");
     }
     return SHT_OK;
 }
@@ -1070,17 +1213,23 @@ int sht_autotune(sht_plan_t p, int prec, int nbatch, void *stream)
         return ms;
     };
     if (tc) {
-        // FP32 ring step: maps per CTA for the two ring lists x threads per CTA
+        // FP32 ring step: maps per CTA for the two ring lists x threads per CTA of
+        // the shared-memory kernel, on the rings it runs (those outside rf_rings)
         const float2 *d = static_cast<const float2 *>(p->ws);
+        DevPlan q = p->dp;
+        q.rings_smooth = q.rf_rest_smooth;
+        q.n_smooth = q.rf_n_rest_smooth;
+        q.rings_blue = q.rf_rest_blue;
+        q.n_blue = q.rf_n_rest_blue;
         float best = 3.4e38f;
         int bs = p->ring_g[0], bb = p->ring_g[1], bt = p->ring_nt;
         for (int nt : {256, 512})
+            if (q.n_smooth + q.n_blue > 0)
             for (int gsm : {1, 2, 4})
                 for (int gbl : {1, 2}) {
                     const float ms = time_it(
                         [&]() {
-                            return sht::launch_ring_synth_mf(p->dp, d, static_cast<float *>(map), nb, gsm, gbl, nt,
-                                                             st);
+                            return sht::launch_ring_synth_mf(q, d, static_cast<float *>(map), nb, gsm, gbl, nt, st);
                         },
                         2);
                     if (ms < best) {
@@ -1175,6 +1324,18 @@ int sht_debug_work_lists(sht_plan_t p, int enable)
     if (!p) return fail(SHT_EINVAL, "sht_debug_work_lists: NULL plan");
     std::lock_guard<std::mutex> lk(p->mu);
     p->sched_off = !enable;
+    return SHT_OK;
+}
+
+int sht_debug_ring_kernel(sht_plan_t p, int mode)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (mode < 0 || mode > 2) return fail(SHT_EINVAL, "ring kernel choice %d not in 0..2", mode);
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->rf_mode = mode;
+    apply_rf_mode(p);
     return SHT_OK;
 }
 
@@ -1441,6 +1602,9 @@ struct sht_multi_s {
     int nitems = 0, ctas = 0;
     int2 *d_smooth = nullptr, *d_blue = nullptr;
     int n_smooth = 0, n_blue = 0, smooth_cap = 0, blue_cap = 0;
+    // tensor-core forms: (request, ring) units of the register-FFT ring kernel
+    int2 *d_rf = nullptr;
+    int n_rf = 0, rf_mmax = 0;
     int *d_counter = nullptr;
     void *d_delta = nullptr;
     // tensor-core forms: a request whose plan already appeared earlier in the
@@ -1582,6 +1746,7 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         };
         std::vector<Item> items;
         std::vector<int2> smooth, blue;
+        std::vector<std::pair<double, int2>> rf;
         std::vector<sht::DevPlan> dp(nreq);
         size_t dofs = 0;
         q->bbuf_own.assign(nreq, nullptr);
@@ -1608,8 +1773,11 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
                     const long long rows = std::min(128, p->npairs - rb * 128);
                     items.push_back({(long long)(p->lmax - m + 1) * rows, make_int4(i, m, rb, 0)});
                 }
-            for (int r : p->rings_smooth_h) smooth.push_back(make_int2(i, r));
-            for (int r : p->rings_blue_h) blue.push_back(make_int2(i, r));
+            const auto &fs = p->rf_set[p->rf_mode];
+            for (int r : fs.rest_s_h) smooth.push_back(make_int2(i, r));
+            for (int r : fs.rest_b_h) blue.push_back(make_int2(i, r));
+            for (int r : fs.rings_h) rf.push_back({rf_unit_cost(p, r), make_int2(i, r)});
+            if (!fs.rings_h.empty()) q->rf_mmax = std::max(q->rf_mmax, p->mmax);
             q->smooth_cap = std::max(q->smooth_cap, p->dp.fft_cap);
             q->blue_cap = std::max(q->blue_cap, p->dp.blue_cap);
             q->delta_ofs.push_back(dofs);
@@ -1628,8 +1796,14 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         q->nitems = (int)w.size();
         q->n_smooth = (int)smooth.size();
         q->n_blue = (int)blue.size();
+        std::stable_sort(rf.begin(), rf.end(),
+                         [](const std::pair<double, int2> &a, const std::pair<double, int2> &b) { return a.first > b.first; });
+        std::vector<int2> rfu(rf.size());
+        for (size_t j = 0; j < rf.size(); ++j) rfu[j] = rf[j].second;
+        q->n_rf = (int)rfu.size();
         if ((rc = multi_upload(q, dp, &q->d_plans)) || (rc = multi_upload(q, w, &q->d_items)) ||
-            (rc = multi_upload(q, smooth, &q->d_smooth)) || (rc = multi_upload(q, blue, &q->d_blue))) {
+            (rc = multi_upload(q, smooth, &q->d_smooth)) || (rc = multi_upload(q, blue, &q->d_blue)) ||
+            (rc = multi_upload(q, rfu, &q->d_rf))) {
             std::string keep = g_err;
             free_multi(q);
             g_err = keep;
@@ -1684,6 +1858,10 @@ extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void
                                                   q->plans[0]->tc.status, st);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc multi launch");
         g_launches.fetch_add(1, std::memory_order_relaxed);
+        e = sht::launch_ring_reg_multi(q->plans[0]->dp, q->d_plans, q->d_rf, q->n_rf, q->rf_mmax, mp,
+                                       q->plans[0]->tc.status, st);
+        if (e != cudaSuccess) return cuda_fail(e, "ring_reg multi launch");
+        g_launches.fetch_add(q->n_rf > 0, std::memory_order_relaxed);
         e = sht::launch_ring_synth_mf_multi(q->d_plans, q->d_smooth, q->n_smooth, q->smooth_cap, q->d_blue, q->n_blue,
                                             q->blue_cap, mp, st);
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_mf multi launch");

@@ -77,6 +77,20 @@ struct DevPlan {
     const double2 *w2_64;      // e^{2 pi i q / kBlueMaxMb}, q < kBlueMaxMb
     const float2 *w2_32;
     int blue_cap;              // largest Mb (0 if none)
+    // FP32 ring step with the FFT in registers (ring_reg.cu): rf_len[r] = L for
+    // a direct transform of length L = n / 2 (a power of two, 256..4096), -L for
+    // Bluestein's algorithm with a power-of-two length L (n / 2 <= 2048), 0 for a
+    // ring left to the shared-memory kernel (odd n, or no such L).  Bluestein
+    // rings: chirp e^{i pi t^2 / N}, t < N = n / 2, at rf_ch32 + rf_ch_ofs[r] and
+    // FFT_L(e^{-i pi t^2 / N}, wrapped) / L at rf_bh32 + rf_bh_ofs[r].
+    const int *rf_len;
+    const long long *rf_ch_ofs, *rf_bh_ofs;
+    const float2 *rf_ch32, *rf_bh32;
+    const int *rf_rings;       // [rf_n] the rings with rf_len != 0, by decreasing cost
+    int rf_n;
+    // the rings with rf_len == 0, split as rings_smooth / rings_blue are
+    const int *rf_rest_smooth, *rf_rest_blue;
+    int rf_n_rest_smooth, rf_n_rest_blue;
 };
 constexpr int kBlueMinPrime = 29;  // a prime factor at least this large selects Bluestein
 constexpr int kBlueMaxMb = 4096;   // largest Bluestein FFT length (shared-memory bound)
@@ -182,6 +196,19 @@ size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
 cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,
                               cudaStream_t st);
 cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, void *out, cudaStream_t st);
+
+// FP32 ring step of the tensor-core forms with the FFT in registers, over the
+// plan's rf_rings (Delta [ring][m][map] for nmaps maps); status gets
+// SHT_ETIMEOUT if a bounded wait for a Delta copy runs out.  The rings outside
+// rf_rings are left to launch_ring_synth_mf with the rf_rest lists.
+cudaError_t launch_ring_reg(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int *status,
+                            cudaStream_t st);
+// The same over (request, ring) items of one-map requests (items ordered by
+// decreasing cost); max_mmax is the largest mmax over the requests, P any of them.
+cudaError_t launch_ring_reg_multi(const DevPlan &P, const DevPlan *plans_dev, const int2 *items, int nitems,
+                                  int max_mmax, const MultiTcPtrs &mp, int *status, cudaStream_t st);
+// Dynamic shared memory of that kernel for a plan's mmax.
+size_t ring_reg_smem_bytes(int mmax);
 
 // Kernels one ring-step launch issues (one per non-empty ring list).
 inline int ring_launches(const DevPlan &P) { return (P.n_smooth > 0) + (P.n_blue > 0); }

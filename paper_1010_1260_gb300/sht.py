@@ -89,6 +89,7 @@ def lib():
             L.sht_debug_withhold_stage.argtypes = [P, I]
             L.sht_skip_evanescent.argtypes = [P, I]
             L.sht_debug_work_lists.argtypes = [P, I]
+            L.sht_debug_ring_kernel.argtypes = [P, I]
             L.sht_work_lists.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), I, ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.sht_map2alm.argtypes = [P, V, V, I, I, V]
@@ -103,7 +104,7 @@ def lib():
                       "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
                       "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage", "sht_map2alm",
                       "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent",
-                      "sht_work_lists", "sht_debug_work_lists"):
+                      "sht_work_lists", "sht_debug_work_lists", "sht_debug_ring_kernel"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -291,6 +292,12 @@ class Plan:
         """Test hook: False makes the tensor-core launches take their items
         round robin instead of the balanced work lists (same maps)."""
         check(lib().sht_debug_work_lists(self._h, 1 if enable else 0))
+
+    def debug_ring_kernel(self, mode: int):
+        """Test hook: FP32 ring-step kernel choice (0 default: register-FFT kernel
+        for the Bluestein rings, 1: shared-memory kernel for all rings, 2:
+        register-FFT kernel for every ring it can run)."""
+        check(lib().sht_debug_ring_kernel(self._h, int(mode)))
 
     # ---------------------------------------------------------- analysis --
     def map2alm(self, maps: torch.Tensor, niter: int = 0, out: torch.Tensor | None = None,

@@ -41,6 +41,9 @@ CASES = [
     ("hp", 8, 100, 100, 33),    # aliasing; 66 columns -> N = 96
     ("gl", (128, 256), 127, 127, 2),
     ("hp", 64, 130, 130, 65),   # two launch groups (64 + 1 maps), 255 rings -> 2 ring blocks
+    ("hp", 128, 256, 256, 4),   # belt rings of 512 pixels: direct FFT of length 256
+    ("gl", (64, 2048), 63, 63, 2),    # rings of 2048 pixels: direct FFT of length 1024
+    ("gl", (16, 8192), 15, 15, 2),    # rings of 8192 pixels: direct FFT of length 4096, maps in two rounds
 ]
 
 
