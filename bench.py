@@ -74,6 +74,10 @@ def parse():
                     help="batch: 64 maps at lmax 2048 (the headline); requests: 256 one-map requests, "
                          "lmax log-uniform in [64, 2048], nside = lmax // 2, in one multi-request call")
     ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--no-side-forms", action="store_true",
+                    help="skip the batching form (256 requests) and the differentiation form (forward + backward) "
+                         "timed beside the headline")
+    ap.add_argument("--side-steps", type=int, default=3, help="timed steps of each side form")
     return ap.parse_args()
 
 
@@ -459,7 +463,8 @@ def run_ours(args):
         dt = max_over_ranks(dt, dev)
         e2e = {"value": world * B / dt, "unit": UNIT, "h2d_bytes_per_step": int(a_pins[0].numel() * 16),
                "d2h_bytes_per_step": int(m_pins[0].numel() * m_pins[0].element_size()), "ms_per_step": dt * 1000,
-               "steps": args.e2e_steps, "pipelined": True}
+               "steps": args.e2e_steps, "pipelined": True,
+               "api": "sht_alm2map_host (C ABI: pinned host buffers, copies pipelined inside the library)"}
         del a_pins, m_pins
 
     # the same form with the plan-time Lambda operand (the recurrence moved to
@@ -498,6 +503,24 @@ def run_ours(args):
                           "streamed from HBM by every call; results bit-identical to the headline's"}
         plan.lambda_cache(args.prec, False)
 
+    # the differentiation and batching forms beside the headline (one GPU)
+    side = {}
+    if world == 1 and not args.no_side_forms:
+        del alm, out
+        torch.cuda.empty_cache()
+        for name, fn in (("differentiation_form", lambda: measure_differentiation(args, plan, args.side_steps)),
+                         ("batching_form", lambda: measure_requests(args, rank, world, args.side_steps, 1))):
+            try:
+                side[name] = fn()
+            except Exception as exc:  # reported, not fatal: the headline stands on its own
+                side[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            torch.cuda.synchronize()
+        if "lmaxs" in side.get("batching_form", {}):
+            lm = side["batching_form"].pop("lmaxs")
+            side["batching_form"]["workload"] = ("%d one-map requests, lmax log-uniform in [64, 2048] (min %d, max %d), "
+                                                 "nside = lmax // 2, one multi-request call per step"
+                                                 % (args.requests, int(lm.min()), int(lm.max())))
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -526,7 +549,8 @@ def run_ours(args):
             "roofline": roof, "roofline_other_step": {k: v for k, v in rl.items() if k != dom},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
             "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy,
-            "fp64_path": fp64_path}
+            "fp64_path": fp64_path, "differentiation_form": side.get("differentiation_form"),
+            "batching_form": side.get("batching_form")}
     if world == 1 and not args.no_cpu_baseline:
         v, dt, nt, desc = cpu_oracle_sample(args, args.cpu_rings)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc,
@@ -545,6 +569,82 @@ def _peaks():
         return {}
 
 
+def measure_requests(args, rank, world, steps, warmup):
+    """The batching form: 256 one-map requests, lmax log-uniform in [64, 2048],
+    nside = lmax // 2, in one multi-request call per step; requests/s per form."""
+    import torch
+    from paper_1010_1260_gb300 import inputs, sht
+    t0 = time.perf_counter()
+    lmaxs = inputs.request_lmax(args.requests, 4)
+    plans = [sht.Plan(sht.healpix(max(1, int(L) // 2)), int(L)) for L in lmaxs]
+    alms = [torch.from_numpy(inputs.gaussian_alm(int(L), int(L), (4, rank * args.requests + i))[0]).cuda()
+            for i, L in enumerate(lmaxs)]
+    res = {"setup_s": time.perf_counter() - t0, "lmaxs": lmaxs}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "fp32_tc"):
+        multi = sht.Multi(plans, prec)
+        outs = multi.outputs()
+        for _ in range(warmup):
+            multi.alm2map(alms, outs)
+        torch.cuda.synchronize()
+        n0 = sht.kernel_launches()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for k in range(steps):
+            multi.alm2map(alms, outs)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median([ev[k].elapsed_time(ev[k + 1]) for k in range(steps)])
+        ms = max_over_ranks(ms, torch.device("cuda", torch.cuda.current_device()))
+        res[prec] = {"ms_per_step": ms, "requests_per_s": world * args.requests / (ms * 1e-3),
+                     "gpu_launches_per_step": (sht.kernel_launches() - n0) / steps,
+                     "timing": "median of %d steps (CUDA events per step)" % steps}
+        multi.close()
+        del outs
+    res["total_alm"] = int(sum(p.nalm for p in plans))
+    res["total_pixels"] = int(sum(p.npix for p in plans))
+    del alms, plans
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_differentiation(args, plan, steps):
+    """The differentiation form: B = 16 maps at the headline's grid and band
+    limit, loss = sum_p w_p (s_p - d_p)^2 through the autograd op, forward in
+    the headline's form (and in FP64), backward through the FP64 transpose."""
+    import torch
+    from paper_1010_1260_gb300 import autograd, inputs
+    B = 16
+    dev = torch.device("cuda", torch.cuda.current_device())
+    a0 = torch.from_numpy(inputs.batch_alm(args.lmax, args.lmax, 5, B)).to(dev)
+    w, d = inputs.loss_weights(plan.npix, 5, B)
+    w = torch.from_numpy(w).to(dev)
+    d = torch.from_numpy(d).to(dev)
+    stream = torch.cuda.current_stream()
+    out = {"maps": B, "loss": "sum_p w_p (s_p - d_p)^2, w ~ U(0.5, 1.5), d ~ N(0, 1), seed 5"}
+    for fwd in sorted({args.prec, "fp64"}):
+        def step():
+            a = a0.clone().requires_grad_(True)
+            s = autograd.alm2map(a, plan, fwd)
+            loss = (w * (s.double() - d) ** 2).sum()
+            loss.backward()
+            return a.grad
+        step()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for k in range(steps):
+            step()
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median([ev[k].elapsed_time(ev[k + 1]) for k in range(steps)])
+        out["forward_" + fwd] = {"ms_forward_backward": ms, "maps_per_s": B / (ms * 1e-3), "steps": steps,
+                                 "backward": "fp64 transpose (ring analysis + Legendre accumulation)"}
+    del a0, w, d
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_requests(args):
     """The batching form: many uneven one-map requests per call (replicas under torchrun)."""
     import torch
@@ -560,32 +660,8 @@ def run_requests(args):
         _build.build()
     if world > 1:
         torch.distributed.barrier()
-    from paper_1010_1260_gb300 import inputs, sht
-    lmaxs = inputs.request_lmax(args.requests, 4)
-    plans = [sht.Plan(sht.healpix(max(1, int(L) // 2)), int(L)) for L in lmaxs]
-    alms = [torch.from_numpy(inputs.gaussian_alm(int(L), int(L), (4, rank * args.requests + i))[0]).cuda()
-            for i, L in enumerate(lmaxs)]
-    res = {}
-    stream = torch.cuda.current_stream()
-    for prec in ("fp64", "fp32_tc"):
-        multi = sht.Multi(plans, prec)
-        outs = multi.outputs()
-        for _ in range(args.warmup):
-            multi.alm2map(alms, outs)
-        torch.cuda.synchronize()
-        n0 = sht.kernel_launches()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            multi.alm2map(alms, outs)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        ms = max_over_ranks(ms, torch.device("cuda", torch.cuda.current_device()))
-        res[prec] = {"ms_per_step": ms, "requests_per_s": world * args.requests / (ms * 1e-3),
-                     "gpu_launches_per_step": (sht.kernel_launches() - n0) / args.steps}
-        multi.close()
+    res = measure_requests(args, rank, world, args.steps, args.warmup)
+    lmaxs = res.pop("lmaxs")
     if rank == 0:
         line = {"metric": "alm2map requests/s (256 one-map requests, lmax log-uniform [64, 2048], nside = lmax // 2)",
                 "value": res["fp64"]["requests_per_s"], "unit": "requests/s", "n_gpus": world, "steps": args.steps,
@@ -593,7 +669,7 @@ def run_requests(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": "batching form: %d requests" % args.requests,
                            "lmax_min": int(lmaxs.min()), "lmax_max": int(lmaxs.max()),
-                           "total_alm": int(sum(p.nalm for p in plans)), "total_pixels": int(sum(p.npix for p in plans))},
+                           "total_alm": res["total_alm"], "total_pixels": res["total_pixels"]},
                 "forms": res}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -266,6 +266,64 @@ int sht_set_tiles(sht_plan_t plan, const int *vals, int n);
  * entry a call reads is first written by that call. */
 int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *map_dev, void *stream);
 
+/* alm2map of coefficients in host memory into maps in host memory: nsteps
+ * batches of nbatch maps, batch k read from alm_host[k] (nbatch x nalm
+ * complex128, m-major packed) and written to map_host[k] (nbatch x npix,
+ * float64 for SHT_FP64, float32 otherwise), as a caller streaming batches
+ * through the GPU would.  The library pipelines the steps (Eq. alm2mapDef per
+ * batch, as sht_alm2map_batch): batch k + 1's coefficients go up on one copy
+ * stream and batch k - 1's maps come down on another while batch k is
+ * transformed on `stream`, through two device buffer sets the plan allocates
+ * on first use and keeps (2 nbatch (16 nalm + npix x element size) bytes).
+ * The same host array may appear at several steps (each step's copies
+ * complete before the next use of its buffer).  Host arrays should be page-
+ * locked (cudaHostRegister / cudaMallocHost) for the copies to overlap.
+ * Synchronous: returns once every map is in host memory.  Errors: SHT_EINVAL
+ * (NULL plan or pointer, nsteps or nbatch < 0, unknown precision),
+ * SHT_ENOMEM, SHT_ECUDA, and those of sht_alm2map_batch. */
+int sht_alm2map_host(sht_plan_t plan, int nsteps, int nbatch, const void *const *alm_host, void *const *map_host,
+                     int prec, void *stream);
+
+/* ---- One transform split over several parts (GPUs): Algorithm 3 (sec.
+ * 2.2.3).  The orders m are partitioned for the Legendre step, every part
+ * sends each other part the Delta_m(ring) of its orders on that part's rings
+ * (one all-to-all exchange, the caller's: e.g. NCCL all_to_all between GPUs,
+ * or device copies between parts on one GPU), and the rings are partitioned
+ * for the ring step.  Each part's arithmetic is the unpartitioned FP64
+ * path's, so the assembled maps equal sht_alm2map_batch's bit for bit.
+ * Layouts (complex128, nbatch maps): the send buffer of part p is, for each
+ * destination q in order, the rows of q's rings (ascending) x maps x p's
+ * orders (ascending): nrings x nbatch x |M_p| entries; the receive buffer of
+ * part q is, for each source p in order, q's rings x maps x p's orders:
+ * |R_q| x nbatch x (mmax + 1) entries.  The block p -> q has |R_q| x nbatch x
+ * |M_p| entries in both. */
+
+/* Host only (no GPU): a balanced partition of orders and rings over nparts.
+ * Orders go in pairs (m, mmax - m), whose recurrence lengths lmax - m + 1 sum
+ * to a constant when lmax = mmax (the load balancing the paper's conclusion
+ * calls for), each pair to the part with the least work so far; rings go in
+ * contiguous ranges of about equal pixel count (nphi[r] pixels per ring).
+ * Writes m_owner[0..mmax] and ring_owner[0..nrings) in [0, nparts).
+ * SHT_EINVAL for bad sizes or NULL arrays. */
+int sht_partition(int lmax, int mmax, int nrings, const int *nphi, int nparts, int *m_owner, int *ring_owner);
+/* Pixels per ring of the plan (host array of sht_nrings entries). */
+int sht_ring_lengths(sht_plan_t plan, int *nphi);
+/* Legendre step of part `part` (SHT_FP64 only): Delta_m of every ring for the
+ * orders m with m_owner[m] == part, from alm_dev (nbatch x nalm complex128;
+ * only those orders are read), into send_dev in the send layout above.
+ * m_owner, ring_owner: host arrays as sht_partition writes them.  Uploads its
+ * index tables synchronously (after the work already queued on stream).  Errors: SHT_EINVAL, SHT_EUNSUPPORTED (another
+ * precision), SHT_ENOMEM, SHT_ECUDA. */
+int sht_alm2map_mpart(sht_plan_t plan, int nbatch, int nparts, const int *m_owner, const int *ring_owner, int part,
+                      const void *alm_dev, void *send_dev, int prec, void *stream);
+/* Ring step of part `part` (SHT_FP64 only): from recv_dev (the receive layout
+ * above, every order of every ring with ring_owner[r] == part), the pixels of
+ * those rings in map_dev (nbatch x npix float64; other rings untouched).  The
+ * orders are gathered into the plan's workspace (grown as needed), then the
+ * ring kernels run over the part's rings.  Errors as sht_alm2map_mpart. */
+int sht_ring_synth_part(sht_plan_t plan, int nbatch, int nparts, const int *m_owner, const int *ring_owner, int part,
+                        const void *recv_dev, void *map_dev, int prec, void *stream);
+
 /* Many requests of different grids and band limits (one map each) in one
  * call: the batching form.  Request i transforms alm_dev[i] (plans[i]'s
  * nalm complex128) into map_dev[i] (plans[i]'s npix reals).  FP64: the
@@ -274,8 +332,8 @@ int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *
  * an atomic counter, then one launch per ring list does all rings; the
  * context is capturable in a CUDA graph (no allocation or host sync inside
  * sht_multi_alm2map; pointers are kernel parameters, so a captured graph
- * replays with the pointers it was captured with).  Tensor-core forms: the
- * operand prep of each request (one small launch each), then one persistent
+ * replays with the pointers it was captured with).  Tensor-core forms: one
+ * operand-prep launch over all requests' (request, m) items, then one persistent
  * tensor-core Legendre launch over all requests' (request, m, ring block)
  * items (one CTA per SM; each CTA runs a fixed list: the items, longest
  * first, each given to the CTA with the least work so far), then one

@@ -23,6 +23,8 @@
 // when |p| > 2^256 and contributes nothing (the true value is < 2^-256).
 #include "sht_internal.cuh"
 
+#include <algorithm>
+
 namespace sht {
 namespace {
 
@@ -38,10 +40,18 @@ __device__ __forceinline__ bool above_hi(double v)
 
 // One work item: order m, ring pairs [pair_block * 128, + 128), maps [b0, b0 + BC).
 // Every thread of the CTA must call it (it synchronises the CTA).
+// Where an item writes: Delta of ring r, map b at delta[row_off[r] + b bstride
+// + col] (row_off == nullptr: the full layout [map][ring][m], col = m).
+struct OutMap {
+    const long long *row_off = nullptr;
+    long long bstride = 0;
+    int col = 0;
+};
+
 template <int BC>
 __device__ __forceinline__ void legendre_item(const DevPlan &P, const double2 *__restrict__ alm,
                                               double2 *__restrict__ delta, int nmaps, int m, int pair_block,
-                                              int b0, double *sA, double2 (*sa)[BC])
+                                              int b0, double *sA, double2 (*sa)[BC], const OutMap &om = OutMap())
 {
     const int L = P.lmax;
     const int pair = pair_block * kThreads + threadIdx.x;
@@ -144,6 +154,16 @@ __device__ __forceinline__ void legendre_item(const DevPlan &P, const double2 *_
     if (!live) return;
     const int2 rr = P.pair_ring[pair];
     const int M1 = P.mmax + 1;
+    if (om.row_off) {
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+            if (b0 + b >= nmaps) break;
+            const long long o = (long long)(b0 + b) * om.bstride + om.col;
+            delta[om.row_off[rr.x] + o] = make_double2(er[b] + orr[b], ei[b] + oi[b]);
+            if (rr.y >= 0) delta[om.row_off[rr.y] + o] = make_double2(er[b] - orr[b], ei[b] - oi[b]);
+        }
+        return;
+    }
 #pragma unroll
     for (int b = 0; b < BC; ++b) {
         if (b0 + b >= nmaps) break;
@@ -161,6 +181,37 @@ legendre_fwd_fp64_kernel(const __grid_constant__ DevPlan P, const double2 *__res
     __shared__ double sA[kChunk];        // A_{l+1} for l in the chunk
     __shared__ double2 sa[kChunk][BC];   // C_l a_lm for the CTA's maps
     legendre_item<BC>(P, alm, delta, nmaps, blockIdx.y, blockIdx.x, blockIdx.z * BC, sA, sa);
+}
+
+// Orders mlist[blockIdx.y] only, written through row_off (an m-partition of
+// Algorithm 3); the arithmetic of every (m, ring pair) is the full launch's.
+template <int BC>
+__global__ void __launch_bounds__(kThreads)
+legendre_mpart_fp64_kernel(const __grid_constant__ DevPlan P, const double2 *__restrict__ alm,
+                           double2 *__restrict__ delta, int nmaps, const int *__restrict__ mlist, int nm,
+                           const long long *__restrict__ row_off)
+{
+    __shared__ double sA[kChunk];
+    __shared__ double2 sa[kChunk][BC];
+    OutMap om;
+    om.row_off = row_off;
+    om.bstride = nm;
+    om.col = blockIdx.y;
+    legendre_item<BC>(P, alm, delta, nmaps, mlist[blockIdx.y], blockIdx.x, blockIdx.z * BC, sA, sa, om);
+}
+
+__global__ void delta_gather_kernel(const double2 *__restrict__ src, double2 *__restrict__ dst, int nmaps, int nrows,
+                                    int M1, const long long *__restrict__ m_off, const int *__restrict__ m_cnt,
+                                    const int *__restrict__ m_col)
+{
+    const long long total = (long long)nmaps * nrows * M1;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(t % M1);
+        const long long br = t / M1;  // b nrows + row
+        const int row = (int)(br % nrows), b = (int)(br / nrows);
+        dst[t] = src[m_off[m] + ((long long)row * nmaps + b) * m_cnt[m] + m_col[m]];
+    }
 }
 
 // Many requests (one map each) in one persistent launch: CTAs take work
@@ -201,6 +252,33 @@ cudaError_t launch_legendre_multi_fp64(const DevPlan *plans, const int4 *items, 
 {
     if (nitems <= 0) return cudaSuccess;
     legendre_multi_fp64_kernel<<<nctas, kThreads, 0, st>>>(plans, items, nitems, counter, ptrs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_legendre_mpart_fp64(const DevPlan &P, const double2 *alm, double2 *delta, int nmaps,
+                                       const int *mlist, int nm, const long long *row_off, cudaStream_t st)
+{
+    if (nmaps <= 0 || nm <= 0) return cudaSuccess;
+    const int bc = nmaps >= 8 ? 8 : nmaps >= 4 ? 4 : nmaps >= 2 ? 2 : 1;
+    dim3 grid((P.npairs + kThreads - 1) / kThreads, nm, (nmaps + bc - 1) / bc);
+    if (bc == 8)
+        legendre_mpart_fp64_kernel<8><<<grid, kThreads, 0, st>>>(P, alm, delta, nmaps, mlist, nm, row_off);
+    else if (bc == 4)
+        legendre_mpart_fp64_kernel<4><<<grid, kThreads, 0, st>>>(P, alm, delta, nmaps, mlist, nm, row_off);
+    else if (bc == 2)
+        legendre_mpart_fp64_kernel<2><<<grid, kThreads, 0, st>>>(P, alm, delta, nmaps, mlist, nm, row_off);
+    else
+        legendre_mpart_fp64_kernel<1><<<grid, kThreads, 0, st>>>(P, alm, delta, nmaps, mlist, nm, row_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delta_gather(const double2 *src, double2 *dst, int nmaps, int nrows, int mmax,
+                                const long long *m_off, const int *m_cnt, const int *m_col, cudaStream_t st)
+{
+    const long long total = (long long)nmaps * nrows * (mmax + 1);
+    if (total <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+    delta_gather_kernel<<<blocks, 256, 0, st>>>(src, dst, nmaps, nrows, mmax + 1, m_off, m_cnt, m_col);
     return cudaGetLastError();
 }
 

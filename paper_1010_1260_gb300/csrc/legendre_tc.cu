@@ -1159,20 +1159,23 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
 // degrees of one parity, 16-byte chunks swizzled by bit 2 of the row.  Entry
 // (par, c, k) holds the pieces of C_l a_lm(map c/2, re or im), l = m + par + 2k,
 // zero for l > lmax, for maps beyond nmaps and for Im of m = 0.
+// The pieces of order m's segment; the (stage, par, c, kk) elements are split
+// over threads t0, t0 + tstep, ... (each element is computed on its own, so
+// the split does not change a bit).
 template <bool BF16, int NPB>
-__global__ void prep_b_kernel(const DevPlan P, const double2 *__restrict__ alm, const int *__restrict__ seg_off,
-                              unsigned char *__restrict__ bout, int nmaps, int ncols)
+__device__ __forceinline__ void prep_b_order(const DevPlan &P, const double2 *__restrict__ alm,
+                                             const int *__restrict__ seg_off, unsigned char *__restrict__ bout,
+                                             int nmaps, int ncols, int m, int t0, int tstep)
 {
     constexpr int KC = BF16 ? 16 : 8;
     constexpr int ESZ = BF16 ? 2 : 4;
     constexpr size_t SB = (size_t)2 * NPB * kTileBytes;
-    const int m = blockIdx.y;
     const int L = P.lmax;
     const int nst = (L - m + 1 + 2 * KC - 1) / (2 * KC);
     const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
     unsigned char *blk = bout + (size_t)(seg_off[2 * m] / (2 * KC)) * SB;
     const int total = nst * 2 * ncols * KC;  // (stage, par, c, kk), kk fastest
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    for (int idx = t0; idx < total; idx += tstep) {
         const int kk = idx % KC;
         const int c = (idx / KC) % ncols;
         const int par = (idx / (KC * ncols)) % 2;
@@ -1197,6 +1200,26 @@ __global__ void prep_b_kernel(const DevPlan P, const double2 *__restrict__ alm, 
                 *reinterpret_cast<uint32_t *>(dst) = pc[q];
         }
     }
+}
+
+template <bool BF16, int NPB>
+__global__ void prep_b_kernel(const DevPlan P, const double2 *__restrict__ alm, const int *__restrict__ seg_off,
+                              unsigned char *__restrict__ bout, int nmaps, int ncols)
+{
+    prep_b_order<BF16, NPB>(P, alm, seg_off, bout, nmaps, ncols, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x,
+                            gridDim.x * blockDim.x);
+}
+
+// Operand prep of many one-map requests in one launch: block i converts order
+// items[i].y of request items[i].x into that request's B operand image.
+template <bool BF16, int NPB>
+__global__ void prep_b_multi_kernel(const DevPlan *__restrict__ plans, const int2 *__restrict__ items,
+                                    const __grid_constant__ MultiTcPtrs mp)
+{
+    const int2 it = items[blockIdx.x];
+    prep_b_order<BF16, NPB>(plans[it.x], static_cast<const double2 *>(mp.alm[it.x]), mp.seg[it.x],
+                            static_cast<unsigned char *>(const_cast<void *>(mp.bbuf[it.x])), 1, tc_ncols(1), it.y,
+                            threadIdx.x, blockDim.x);
 }
 
 template <bool BF16, int NPA, int NPB>
@@ -1446,6 +1469,19 @@ cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const do
     if (prec == SHT_FP32_TC) return run_prep<false, 2, 2>(P, W, alm, nmaps, st);
     if (prec == SHT_BF16X3_TC) return run_prep<true, 2, 2>(P, W, alm, nmaps, st);
     return run_prep<true, 3, 3>(P, W, alm, nmaps, st);
+}
+
+cudaError_t launch_tc_prep_multi(const DevPlan *plans_dev, const int2 *items, int nitems, const MultiTcPtrs &mp,
+                                 int prec, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (prec == SHT_FP32_TC)
+        prep_b_multi_kernel<false, 2><<<nitems, 256, 0, st>>>(plans_dev, items, mp);
+    else if (prec == SHT_BF16X3_TC)
+        prep_b_multi_kernel<true, 2><<<nitems, 256, 0, st>>>(plans_dev, items, mp);
+    else
+        prep_b_multi_kernel<true, 3><<<nitems, 256, 0, st>>>(plans_dev, items, mp);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_main(const DevPlan &P, const TcWork &W, int prec, const void *acache, float2 *delta, int nmaps,

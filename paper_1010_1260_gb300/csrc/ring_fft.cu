@@ -494,7 +494,8 @@ __device__ __forceinline__ void ring_synth_body(const DevPlan &P, int r, const t
     }
 
     for (int b = b_begin; b < b_end; ++b) {
-        const C *D = delta + ((size_t)b * P.nrings + r) * (size_t)(M + 1);
+        const size_t row = P.ring_row ? (size_t)b * P.delta_rows + P.ring_row[r] : (size_t)b * P.nrings + r;
+        const C *D = delta + row * (size_t)(M + 1);
         // 1. phase shift + fold onto the half spectrum, into buf1[0..nb);
         //    the phase index (m ps) mod 2n advances by (n ps) mod 2n along m = k, k + n, ...
         const int pstep = (ps >= 0) ? (int)(((long long)n * ps) % (2 * n)) : 0;

@@ -37,6 +37,7 @@ struct sht_plan_s {
     void *ws = nullptr;  // Delta workspace
     size_t ws_bytes = 0;
     std::vector<int> rings_smooth_h, rings_blue_h;  // host copies of the ring lists
+    std::vector<int> nphi_h;                       // pixels per ring (host copy)
     // FP32 ring step: the register-FFT kernel's ring list and the rings left to
     // the shared-memory kernel, per kernel choice (sht_debug_ring_kernel)
     struct RfSet {
@@ -60,6 +61,16 @@ struct sht_plan_s {
     bool sched_off = false;       // test hook: round robin instead of the lists
     std::vector<double> wring_h;  // pixel quadrature weight per ring (host copy)
     double *wring_d = nullptr;    // the same on the device (DevPlan::wring)
+    // host-buffer pipeline (sht_alm2map_host): two device buffer sets, two copy
+    // streams and the events that order them (created on first use)
+    void *hp_buf = nullptr;
+    size_t hp_bytes = 0;
+    cudaStream_t hp_up = nullptr, hp_down = nullptr;
+    cudaEvent_t hp_ev[8] = {};
+    // index tables of the partitioned transform (sht_alm2map_mpart,
+    // sht_ring_synth_part), grown on demand
+    void *part_buf = nullptr;
+    size_t part_bytes = 0;
     size_t lcache_bytes[4] = {};
     std::mutex mu;
 };
@@ -239,6 +250,12 @@ void free_plan(sht_plan_s *p)
         for (void *c : p->lcache)
             if (c) cudaFree(c);
         if (p->warm) cudaFree(p->warm);
+        if (p->hp_buf) cudaFree(p->hp_buf);
+        if (p->part_buf) cudaFree(p->part_buf);
+        if (p->hp_up) cudaStreamDestroy(p->hp_up);
+        if (p->hp_down) cudaStreamDestroy(p->hp_down);
+        for (auto e : p->hp_ev)
+            if (e) cudaEventDestroy(e);
         if (p->sched) cudaFree(p->sched);
         for (auto &e : p->prof_pending) {
             cudaEventDestroy(e.a);
@@ -654,6 +671,7 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, tw64, &d.tw64))) return rc;
     if ((rc = upload(p, tw32, &d.tw32))) return rc;
     p->rings_smooth_h = rsmooth;
+    p->nphi_h = R.nphi;
     p->rings_blue_h = rblue;
     d.n_smooth = (int)rsmooth.size();
     d.n_blue = (int)rblue.size();
@@ -1406,6 +1424,81 @@ int sht_alm2map(sht_plan_t p, const void *alm_dev, void *map_dev, int prec, void
     return sht_alm2map_batch(p, 1, alm_dev, map_dev, prec, stream);
 }
 
+int sht_alm2map_host(sht_plan_t p, int nsteps, int nbatch, const void *const *alm_host, void *const *map_host,
+                     int prec, void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (nsteps < 0 || nbatch < 0) return fail(SHT_EINVAL, "nsteps < 0 or nbatch < 0");
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
+        return fail(SHT_EINVAL, "unknown precision %d", prec);
+    if (nsteps == 0 || nbatch == 0) return SHT_OK;
+    if (!alm_host || !map_host) return fail(SHT_EINVAL, "null pointer array");
+    for (int k = 0; k < nsteps; ++k)
+        if (!alm_host[k] || !map_host[k]) return fail(SHT_EINVAL, "null host pointer for step %d", k);
+    const size_t ab = (size_t)nbatch * p->nalm * 16;
+    const size_t mb = (size_t)nbatch * p->npix * (prec == SHT_FP64 ? 8 : 4);
+    const size_t ab_al = (ab + 255) & ~(size_t)255, mb_al = (mb + 255) & ~(size_t)255;
+    cudaStream_t comp = static_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        DeviceGuard dg(p->device);
+        cudaError_t e = cudaSuccess;
+        if (!p->hp_up) e = cudaStreamCreateWithFlags(&p->hp_up, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !p->hp_down) e = cudaStreamCreateWithFlags(&p->hp_down, cudaStreamNonBlocking);
+        for (auto &ev : p->hp_ev)
+            if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "host pipeline set-up");
+        const size_t need = 2 * (ab_al + mb_al);
+        if (p->hp_bytes < need) {
+            if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            if (p->hp_buf) cudaFree(p->hp_buf);
+        if (p->part_buf) cudaFree(p->part_buf);
+            p->hp_buf = nullptr;
+            p->hp_bytes = 0;
+            if ((e = cudaMalloc(&p->hp_buf, need)) != cudaSuccess) {
+                p->hp_buf = nullptr;
+                cudaGetLastError();
+                return fail(SHT_ENOMEM, "host pipeline buffers cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+            }
+            p->hp_bytes = need;
+        }
+    }
+    char *base = static_cast<char *>(p->hp_buf);
+    void *d_alm[2] = {base, base + ab_al};
+    void *d_map[2] = {base + 2 * ab_al, base + 2 * ab_al + mb_al};
+    // events per buffer parity: uploaded, consumed (input buffer free), done, downloaded (output buffer free)
+    cudaEvent_t *up_ev = p->hp_ev, *cons_ev = p->hp_ev + 2, *done_ev = p->hp_ev + 4, *down_ev = p->hp_ev + 6;
+    DeviceGuard dg(p->device);
+    auto upload = [&](int k) -> cudaError_t {
+        const int b = k & 1;
+        cudaError_t e = cudaSuccess;
+        if (k >= 2) e = cudaStreamWaitEvent(p->hp_up, cons_ev[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_alm[b], alm_host[k], ab, cudaMemcpyHostToDevice, p->hp_up);
+        if (e == cudaSuccess) e = cudaEventRecord(up_ev[b], p->hp_up);
+        return e;
+    };
+    cudaError_t e = upload(0);
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        const int b = k & 1;
+        if (k + 1 < nsteps && (e = upload(k + 1)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(comp, up_ev[b], 0)) != cudaSuccess) break;
+        if (k >= 2 && (e = cudaStreamWaitEvent(comp, down_ev[b], 0)) != cudaSuccess) break;
+        if ((rc = sht_alm2map_batch(p, nbatch, d_alm[b], d_map[b], prec, stream))) return rc;
+        if ((e = cudaEventRecord(cons_ev[b], comp)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(done_ev[b], comp)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(p->hp_down, done_ev[b], 0)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(map_host[k], d_map[b], mb, cudaMemcpyDeviceToHost, p->hp_down)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(down_ev[b], p->hp_down)) != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->hp_down);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->hp_up);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(comp);
+    if (e != cudaSuccess) return cuda_fail(e, "host pipeline");
+    return SHT_OK;
+}
+
 int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, void *alm_dev,
                               int prec, void *stream)
 {
@@ -1589,6 +1682,237 @@ int sht_map2alm_adjoint(sht_plan_t p, const void *map_dev, void *alm_dev, int pr
 
 }  // extern "C"
 
+// ------------------------------------------------ partitioned transform --
+// Algorithm 3 of the paper: the orders m are split over parts for the
+// Legendre step, Delta is exchanged all-to-all, and the rings are split over
+// parts for the ring step.  The library computes each part's share; the
+// exchange between parts (GPUs) is the caller's (e.g. an NCCL all-to-all).
+
+namespace {
+
+struct PartLayout {
+    std::vector<int> mlist;             // this part's orders, ascending
+    std::vector<std::vector<int>> rings;  // rings of every part, ascending
+    std::vector<std::vector<int>> ms;     // orders of every part, ascending
+};
+
+int part_layout(const sht_plan_s *p, int nparts, const int *m_owner, const int *ring_owner, int part, PartLayout &pl)
+{
+    if (nparts < 1 || part < 0 || part >= nparts) return fail(SHT_EINVAL, "need 0 <= part < nparts");
+    if (!m_owner || !ring_owner) return fail(SHT_EINVAL, "null owner array");
+    pl.rings.assign(nparts, {});
+    pl.ms.assign(nparts, {});
+    for (int m = 0; m <= p->mmax; ++m) {
+        if (m_owner[m] < 0 || m_owner[m] >= nparts) return fail(SHT_EINVAL, "m_owner[%d] = %d outside [0, %d)", m, m_owner[m], nparts);
+        pl.ms[m_owner[m]].push_back(m);
+    }
+    for (int r = 0; r < p->nrings; ++r) {
+        if (ring_owner[r] < 0 || ring_owner[r] >= nparts)
+            return fail(SHT_EINVAL, "ring_owner[%d] = %d outside [0, %d)", r, ring_owner[r], nparts);
+        pl.rings[ring_owner[r]].push_back(r);
+    }
+    pl.mlist = pl.ms[part];
+    return SHT_OK;
+}
+
+// Device copy of host tables into the plan's partition scratch (synchronous:
+// waits for the work already queued on st, which may still read the tables).
+int part_upload(sht_plan_s *p, const std::vector<std::pair<const void *, size_t>> &parts, std::vector<char *> &out,
+                cudaStream_t st)
+{
+    cudaError_t e0 = cudaStreamSynchronize(st);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "cudaStreamSynchronize");
+    size_t need = 0;
+    for (auto &q : parts) need += (q.second + 255) & ~(size_t)255;
+    if (p->part_bytes < need) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        if (p->part_buf) cudaFree(p->part_buf);
+        p->part_buf = nullptr;
+        p->part_bytes = 0;
+        if ((e = cudaMalloc(&p->part_buf, need)) != cudaSuccess) {
+            p->part_buf = nullptr;
+            cudaGetLastError();
+            return fail(SHT_ENOMEM, "partition tables cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        }
+        p->part_bytes = need;
+    }
+    char *b = static_cast<char *>(p->part_buf);
+    out.clear();
+    for (auto &q : parts) {
+        if (q.second) {
+            cudaError_t e = cudaMemcpy(b, q.first, q.second, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "partition tables");
+        }
+        out.push_back(b);
+        b += (q.second + 255) & ~(size_t)255;
+    }
+    return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" int sht_partition(int lmax, int mmax, int nrings, const int *nphi, int nparts, int *m_owner,
+                             int *ring_owner)
+{
+    g_err.clear();
+    if (lmax < 0 || mmax < 0 || mmax > lmax || nrings < 1 || nparts < 1 || !nphi || !m_owner || !ring_owner)
+        return fail(SHT_EINVAL, "sht_partition: bad arguments");
+    const int L = lmax, M = mmax;
+    // orders in pairs (m, M - m), whose recurrence lengths (L - m + 1) sum to a
+    // constant when L = M, each pair (longest first) to the part with the least
+    // work so far
+    std::vector<std::pair<long long, std::pair<int, int>>> units;
+    for (int m = 0; 2 * m <= M; ++m) {
+        const int m2 = M - m;
+        const long long c = (L - m + 1) + (m2 != m ? (L - m2 + 1) : 0);
+        units.push_back({c, {m, m2}});
+    }
+    std::stable_sort(units.begin(), units.end(),
+                     [](const std::pair<long long, std::pair<int, int>> &a,
+                        const std::pair<long long, std::pair<int, int>> &b) { return a.first > b.first; });
+    std::vector<long long> load(nparts, 0);
+    for (auto &u : units) {
+        const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[q] += u.first;
+        m_owner[u.second.first] = q;
+        m_owner[u.second.second] = q;
+    }
+    // rings in contiguous ranges of about equal pixel count: ring r goes to the
+    // part whose share [q total / nparts, (q + 1) total / nparts) holds its first pixel
+    long long total = 0;
+    for (int r = 0; r < nrings; ++r) {
+        if (nphi[r] < 1) return fail(SHT_EINVAL, "sht_partition: nphi[%d] < 1", r);
+        total += nphi[r];
+    }
+    long long first = 0;
+    int q = 0;
+    for (int r = 0; r < nrings; ++r) {
+        while (q + 1 < nparts && first >= (total * (q + 1)) / nparts) ++q;
+        ring_owner[r] = q;
+        first += nphi[r];
+    }
+    return SHT_OK;
+}
+
+extern "C" int sht_ring_lengths(sht_plan_t p, int *nphi)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!nphi) return fail(SHT_EINVAL, "null output array");
+    std::copy(p->nphi_h.begin(), p->nphi_h.end(), nphi);
+    return SHT_OK;
+}
+
+extern "C" int sht_alm2map_mpart(sht_plan_t p, int nbatch, int nparts, const int *m_owner, const int *ring_owner,
+                                 int part, const void *alm_dev, void *send_dev, int prec, void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (nbatch < 0) return fail(SHT_EINVAL, "nbatch < 0");
+    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "the partitioned transform is built for SHT_FP64");
+    PartLayout pl;
+    if ((rc = part_layout(p, nparts, m_owner, ring_owner, part, pl))) return rc;
+    if (nbatch == 0 || pl.mlist.empty()) return SHT_OK;
+    if (!alm_dev || !send_dev) return fail(SHT_EINVAL, "null device pointer");
+    const int nm = (int)pl.mlist.size();
+    // send layout: for destination q, its rings' rows [row][map][order of this part]
+    std::vector<long long> row_off(p->nrings);
+    long long off = 0;
+    for (int q = 0; q < nparts; ++q)
+        for (size_t i = 0; i < pl.rings[q].size(); ++i) {
+            row_off[pl.rings[q][i]] = off;
+            off += (long long)nbatch * nm;
+        }
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    std::vector<char *> d;
+    if ((rc = part_upload(p, {{pl.mlist.data(), pl.mlist.size() * sizeof(int)},
+                              {row_off.data(), row_off.size() * sizeof(long long)}},
+                          d, static_cast<cudaStream_t>(stream))))
+        return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    StageScope s1(p, SHT_STAGE_LEGENDRE, st);
+    cudaError_t e = sht::launch_legendre_mpart_fp64(p->dp, static_cast<const double2 *>(alm_dev),
+                                                    static_cast<double2 *>(send_dev), nbatch,
+                                                    reinterpret_cast<const int *>(d[0]), nm,
+                                                    reinterpret_cast<const long long *>(d[1]), st);
+    s1.done(e);
+    if (e != cudaSuccess) return cuda_fail(e, "legendre_mpart launch");
+    return SHT_OK;
+}
+
+extern "C" int sht_ring_synth_part(sht_plan_t p, int nbatch, int nparts, const int *m_owner, const int *ring_owner,
+                                   int part, const void *recv_dev, void *map_dev, int prec, void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (nbatch < 0) return fail(SHT_EINVAL, "nbatch < 0");
+    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "the partitioned transform is built for SHT_FP64");
+    PartLayout pl;
+    if ((rc = part_layout(p, nparts, m_owner, ring_owner, part, pl))) return rc;
+    const std::vector<int> &mine = pl.rings[part];
+    if (nbatch == 0 || mine.empty()) return SHT_OK;
+    if (!recv_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
+    const int nrows = (int)mine.size();
+    if (nbatch > 32768) return fail(SHT_EUNSUPPORTED, "nbatch > 32768");
+    // receive layout: block of source q = [row][map][order of q]
+    std::vector<long long> m_off(p->mmax + 1);
+    std::vector<int> m_cnt(p->mmax + 1), m_col(p->mmax + 1);
+    long long off = 0;
+    for (int q = 0; q < nparts; ++q) {
+        for (size_t i = 0; i < pl.ms[q].size(); ++i) {
+            const int m = pl.ms[q][i];
+            m_off[m] = off;
+            m_cnt[m] = (int)pl.ms[q].size();
+            m_col[m] = (int)i;
+        }
+        off += (long long)nrows * nbatch * (long long)pl.ms[q].size();
+    }
+    std::vector<int> row(p->nrings, -1), rs, rb;
+    for (int i = 0; i < nrows; ++i) row[mine[i]] = i;
+    for (int r : p->rings_smooth_h)
+        if (row[r] >= 0) rs.push_back(r);
+    for (int r : p->rings_blue_h)
+        if (row[r] >= 0) rb.push_back(r);
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    const size_t dbytes = (size_t)nbatch * nrows * (p->mmax + 1) * sizeof(double2);
+    if ((rc = ensure_ws(p, dbytes))) return rc;
+    std::vector<char *> d;
+    if ((rc = part_upload(p, {{m_off.data(), m_off.size() * sizeof(long long)},
+                              {m_cnt.data(), m_cnt.size() * sizeof(int)},
+                              {m_col.data(), m_col.size() * sizeof(int)},
+                              {row.data(), row.size() * sizeof(int)},
+                              {rs.data(), rs.size() * sizeof(int)},
+                              {rb.data(), rb.size() * sizeof(int)}},
+                          d, static_cast<cudaStream_t>(stream))))
+        return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double2 *delta = static_cast<double2 *>(p->ws);
+    cudaError_t e = sht::launch_delta_gather(static_cast<const double2 *>(recv_dev), delta, nbatch, nrows, p->mmax,
+                                             reinterpret_cast<const long long *>(d[0]),
+                                             reinterpret_cast<const int *>(d[1]),
+                                             reinterpret_cast<const int *>(d[2]), st);
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "delta gather launch");
+    DevPlan q = p->dp;
+    q.ring_row = reinterpret_cast<const int *>(d[3]);
+    q.delta_rows = nrows;
+    q.rings_smooth = rs.empty() ? nullptr : reinterpret_cast<const int *>(d[4]);
+    q.n_smooth = (int)rs.size();
+    q.rings_blue = rb.empty() ? nullptr : reinterpret_cast<const int *>(d[5]);
+    q.n_blue = (int)rb.size();
+    StageScope s2(p, SHT_STAGE_RING, st);
+    e = sht::launch_ring_synth_fp64(q, delta, static_cast<double *>(map_dev), nbatch, p->fp64_ring_g, st);
+    s2.done(e, sht::ring_launches(q));
+    if (e != cudaSuccess) return cuda_fail(e, "ring_synth_part launch");
+    return SHT_OK;
+}
+
 // ----------------------------------------------------------- multi-request --
 
 struct sht_multi_s {
@@ -1605,6 +1929,9 @@ struct sht_multi_s {
     // tensor-core forms: (request, ring) units of the register-FFT ring kernel
     int2 *d_rf = nullptr;
     int n_rf = 0, rf_mmax = 0;
+    // tensor-core forms: (request, m) items of the one-launch operand prep
+    int2 *d_prep = nullptr;
+    int n_prep = 0;
     int *d_counter = nullptr;
     void *d_delta = nullptr;
     // tensor-core forms: a request whose plan already appeared earlier in the
@@ -1747,6 +2074,7 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         std::vector<Item> items;
         std::vector<int2> smooth, blue;
         std::vector<std::pair<double, int2>> rf;
+        std::vector<int2> prep;
         std::vector<sht::DevPlan> dp(nreq);
         size_t dofs = 0;
         q->bbuf_own.assign(nreq, nullptr);
@@ -1773,6 +2101,7 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
                     const long long rows = std::min(128, p->npairs - rb * 128);
                     items.push_back({(long long)(p->lmax - m + 1) * rows, make_int4(i, m, rb, 0)});
                 }
+            for (int m = 0; m <= p->mmax; ++m) prep.push_back(make_int2(i, m));
             const auto &fs = p->rf_set[p->rf_mode];
             for (int r : fs.rest_s_h) smooth.push_back(make_int2(i, r));
             for (int r : fs.rest_b_h) blue.push_back(make_int2(i, r));
@@ -1801,9 +2130,10 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         std::vector<int2> rfu(rf.size());
         for (size_t j = 0; j < rf.size(); ++j) rfu[j] = rf[j].second;
         q->n_rf = (int)rfu.size();
+        q->n_prep = (int)prep.size();
         if ((rc = multi_upload(q, dp, &q->d_plans)) || (rc = multi_upload(q, w, &q->d_items)) ||
             (rc = multi_upload(q, smooth, &q->d_smooth)) || (rc = multi_upload(q, blue, &q->d_blue)) ||
-            (rc = multi_upload(q, rfu, &q->d_rf))) {
+            (rc = multi_upload(q, rfu, &q->d_rf)) || (rc = multi_upload(q, prep, &q->d_prep))) {
             std::string keep = g_err;
             free_multi(q);
             g_err = keep;
@@ -1842,19 +2172,18 @@ extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void
         sht::MultiTcPtrs mp{};
         for (int i = 0; i < q->nreq; ++i) {
             const sht_plan_s *p = q->plans[i];
-            sht::TcWork w = p->tc;
-            if (q->bbuf_own[i]) w.bbuf = q->bbuf_own[i];
-            mp.bbuf[i] = w.bbuf;
+            mp.alm[i] = alm_dev[i];
+            mp.bbuf[i] = q->bbuf_own[i] ? q->bbuf_own[i] : p->tc.bbuf;
             mp.seg[i] = bf16 ? p->tc.seg_bf16 : p->tc.seg_tf32;
             mp.delta[i] = static_cast<char *>(q->d_delta) + q->delta_ofs[i];
             mp.map[i] = map_dev[i];
             mp.cta_off = q->d_cta_off;
             mp.ctas = q->ctas;
-            cudaError_t e = sht::launch_tc_prep(p->dp, w, q->prec, static_cast<const double2 *>(alm_dev[i]), 1, st);
-            if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
-            g_launches.fetch_add(1, std::memory_order_relaxed);
         }
-        cudaError_t e = sht::launch_tc_main_multi(q->plans[0]->dp, q->d_plans, q->d_items, q->nitems, mp, q->prec,
+        cudaError_t e = sht::launch_tc_prep_multi(q->d_plans, q->d_prep, q->n_prep, mp, q->prec, st);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prep launch");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        e = sht::launch_tc_main_multi(q->plans[0]->dp, q->d_plans, q->d_items, q->nitems, mp, q->prec,
                                                   q->plans[0]->tc.status, st);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_tc multi launch");
         g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -91,6 +91,10 @@ struct DevPlan {
     // the rings with rf_len == 0, split as rings_smooth / rings_blue are
     const int *rf_rest_smooth, *rf_rest_blue;
     int rf_n_rest_smooth, rf_n_rest_blue;
+    // FP64 ring step over a ring partition (sht_ring_synth_part): Delta row of
+    // ring r is ring_row[r] of delta_rows per map (ring_row == nullptr: row r of nrings)
+    const int *ring_row;
+    int delta_rows;
 };
 constexpr int kBlueMinPrime = 29;  // a prime factor at least this large selects Bluestein
 constexpr int kBlueMaxMb = 4096;   // largest Bluestein FFT length (shared-memory bound)
@@ -108,6 +112,17 @@ struct MultiPtrs {
 //   bc = maps per CTA (1, 2, 4, 8; 0 = 8), a tile shape only: results do not depend on it.
 cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, double2 *delta,
                                      int nmaps, int bc, cudaStream_t st);
+
+// Legendre step in FP64 for the orders mlist[0..nm) only (an m-partition):
+// Delta_{mlist[i]} of ring r and map b goes to delta[row_off[r] + b nm + i]
+// (complex128), row_off[r] laying out the rings for an all-to-all exchange.
+cudaError_t launch_legendre_mpart_fp64(const DevPlan &P, const double2 *alm, double2 *delta, int nmaps,
+                                       const int *mlist, int nm, const long long *row_off, cudaStream_t st);
+// Gather of the exchanged blocks into the ring step's layout: for order m,
+// rows of the partition's rings, maps b:
+//   dst[(b nrows + row) (mmax + 1) + m] = src[m_off[m] + (row nmaps + b) m_cnt[m] + m_col[m]].
+cudaError_t launch_delta_gather(const double2 *src, double2 *dst, int nmaps, int nrows, int mmax,
+                                const long long *m_off, const int *m_cnt, const int *m_col, cudaStream_t st);
 
 // Legendre step of many one-map requests in one persistent launch over the
 // work list items[] = (request, m, ring block, -); counter must be 0 at launch.
@@ -158,10 +173,11 @@ struct TcWork {
     void *bbuf = nullptr;
     int *status = nullptr;
 };
-inline int tc_ncols(int nmaps) { return ((2 * nmaps + 31) / 32) * 32; }
+__host__ __device__ inline int tc_ncols(int nmaps) { return ((2 * nmaps + 31) / 32) * 32; }
 
 // Per-request operands of a many-request tensor-core launch (one map each).
 struct MultiTcPtrs {
+    const void *alm[kMaxReq];   // the request's coefficients, complex128
     const void *bbuf[kMaxReq];  // B operand image of the request's plan
     const int *seg[kMaxReq];    // its (m, parity) segment table for the form
     void *delta[kMaxReq];       // its Delta, complex64 [ring][m]
@@ -174,6 +190,9 @@ struct MultiTcPtrs {
 size_t tc_bbuf_bytes(const TcWork &W, int prec);
 cudaError_t launch_tc_prep(const DevPlan &P, const TcWork &W, int prec, const double2 *alm, int nmaps,
                            cudaStream_t st);
+// Operand prep of many one-map requests in one launch over items (request, m).
+cudaError_t launch_tc_prep_multi(const DevPlan *plans_dev, const int2 *items, int nitems, const MultiTcPtrs &mp,
+                                 int prec, cudaStream_t st);
 // delta: [ring][m][map] for the launch's nmaps maps (a row's maps contiguous,
 // so every store fills whole sectors).  acache: the plan-time Lambda operand
 // of form prec (launch_lambda_build), or nullptr to run the FP64 recurrence in

@@ -90,6 +90,12 @@ def lib():
             L.sht_skip_evanescent.argtypes = [P, I]
             L.sht_debug_work_lists.argtypes = [P, I]
             L.sht_debug_ring_kernel.argtypes = [P, I]
+            L.sht_alm2map_host.argtypes = [P, I, I, PP, PP, I, V]
+            IP = ctypes.POINTER(I)
+            L.sht_partition.argtypes = [I, I, I, IP, I, IP, IP]
+            L.sht_ring_lengths.argtypes = [P, IP]
+            L.sht_alm2map_mpart.argtypes = [P, I, I, IP, IP, I, V, V, I, V]
+            L.sht_ring_synth_part.argtypes = [P, I, I, IP, IP, I, V, V, I, V]
             L.sht_work_lists.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), I, ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.sht_map2alm.argtypes = [P, V, V, I, I, V]
@@ -104,7 +110,9 @@ def lib():
                       "sht_multi_destroy", "sht_alm2map_multi", "sht_lambda_cache", "sht_autotune",
                       "sht_tiles", "sht_set_tiles", "sht_debug_withhold_stage", "sht_map2alm",
                       "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent",
-                      "sht_work_lists", "sht_debug_work_lists", "sht_debug_ring_kernel"):
+                      "sht_work_lists", "sht_debug_work_lists", "sht_debug_ring_kernel",
+                      "sht_alm2map_host", "sht_partition", "sht_ring_lengths", "sht_alm2map_mpart",
+                      "sht_ring_synth_part"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -135,6 +143,61 @@ def work_lists(costs, nlists: int):
 def kernel_launches() -> int:
     """Kernels launched by libsht in this process so far."""
     return int(lib().sht_kernel_launches())
+
+
+# ------------------------------------------------- partitioned transform --
+# Algorithm 3: orders split over parts for the Legendre step, one all-to-all
+# of Delta, rings split over parts for the ring step (see sht_partition).
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def partition(lmax: int, mmax: int, nphi, nparts: int):
+    """(m_owner, ring_owner) int32 arrays of the library's balanced partition
+    (host only, no GPU)."""
+    nphi = np.ascontiguousarray(nphi, dtype=np.int32)
+    mo = np.zeros(mmax + 1, dtype=np.int32)
+    ro = np.zeros(len(nphi), dtype=np.int32)
+    check(lib().sht_partition(int(lmax), int(mmax), len(nphi), _ip(nphi), int(nparts), _ip(mo), _ip(ro)))
+    return mo, ro
+
+
+def exchange_sizes(m_owner, ring_owner, nparts: int, nbatch: int):
+    """Complex entries of every block of the all-to-all: sizes[p][q] = block
+    from part p to part q = |rings of q| x nbatch x |orders of p|."""
+    nm = np.bincount(np.asarray(m_owner), minlength=nparts)
+    nr = np.bincount(np.asarray(ring_owner), minlength=nparts)
+    return [[int(nr[q]) * nbatch * int(nm[p]) for q in range(nparts)] for p in range(nparts)]
+
+
+def alm2map_distributed(plan: "Plan", alm: torch.Tensor, m_owner, ring_owner, group=None,
+                        out: torch.Tensor | None = None) -> torch.Tensor:
+    """One FP64 alm2map split over the ranks of a torch.distributed group
+    (rank = part): this rank's orders through the Legendre step, one
+    all_to_all_single of Delta, this rank's rings through the ring step.
+    Returns the maps with this rank's rings filled (other rings untouched)."""
+    import torch.distributed as dist
+    part, nparts = dist.get_rank(group), dist.get_world_size(group)
+    a = alm.reshape(-1, plan.nalm).contiguous()
+    B = a.shape[0]
+    send = plan.alm2map_mpart(a, m_owner, ring_owner, part, nparts)
+    recv = exchange(send, m_owner, ring_owner, B, group)
+    return plan.ring_synth_part(recv, m_owner, ring_owner, part, nparts, B, out=out)
+
+
+def exchange(send: torch.Tensor, m_owner, ring_owner, nbatch: int, group=None) -> torch.Tensor:
+    """The all-to-all of Algorithm 3 over a torch.distributed group: this
+    rank's send buffer (blocks by destination) in, its receive buffer (blocks
+    by source) out; complex128 exchanged as pairs of float64."""
+    import torch.distributed as dist
+    part, nparts = dist.get_rank(group), dist.get_world_size(group)
+    sizes = exchange_sizes(m_owner, ring_owner, nparts, nbatch)
+    recv = torch.empty(sum(sizes[p][part] for p in range(nparts)), dtype=torch.complex128, device=send.device)
+    dist.all_to_all_single(torch.view_as_real(recv).reshape(-1), torch.view_as_real(send).reshape(-1),
+                           output_split_sizes=[2 * sizes[p][part] for p in range(nparts)],
+                           input_split_sizes=[2 * sizes[part][q] for q in range(nparts)], group=group)
+    return recv
 
 
 # ------------------------------------------------------------------ grids --
@@ -242,6 +305,41 @@ class Plan:
                                               _stream_ptr(stream)))
         return out.reshape(self.nalm) if single else out.reshape(B, self.nalm)
 
+    # ------------------------------------------------ partitioned transform --
+    def ring_lengths(self) -> np.ndarray:
+        out = np.zeros(self.nrings, dtype=np.int32)
+        check(lib().sht_ring_lengths(self._h, _ip(out)))
+        return out
+
+    def alm2map_mpart(self, alm: torch.Tensor, m_owner, ring_owner, part: int, nparts: int,
+                      send: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Legendre step of one part (FP64): the send buffer of the all-to-all
+        (complex128, nrings x B x |orders of part|, grouped by destination)."""
+        a = alm.reshape(-1, self.nalm).contiguous()
+        B = a.shape[0]
+        mo = np.ascontiguousarray(m_owner, dtype=np.int32)
+        ro = np.ascontiguousarray(ring_owner, dtype=np.int32)
+        n = self.nrings * B * int(np.sum(mo == part))
+        if send is None:
+            send = torch.empty(n, dtype=torch.complex128, device=a.device)
+        elif not (send.is_contiguous() and send.dtype == torch.complex128 and send.numel() >= n):
+            raise TypeError("bad send buffer")
+        check(lib().sht_alm2map_mpart(self._h, B, int(nparts), _ip(mo), _ip(ro), int(part), a.data_ptr(),
+                                      send.data_ptr(), PREC["fp64"], _stream_ptr(stream)))
+        return send
+
+    def ring_synth_part(self, recv: torch.Tensor, m_owner, ring_owner, part: int, nparts: int, nbatch: int,
+                        out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Ring step of one part (FP64) from its receive buffer: the pixels of
+        the part's rings in ``out`` (float64 [nbatch, npix])."""
+        mo = np.ascontiguousarray(m_owner, dtype=np.int32)
+        ro = np.ascontiguousarray(ring_owner, dtype=np.int32)
+        if out is None:
+            out = torch.zeros((nbatch, self.npix), dtype=torch.float64, device=recv.device)
+        check(lib().sht_ring_synth_part(self._h, int(nbatch), int(nparts), _ip(mo), _ip(ro), int(part),
+                                        recv.data_ptr(), out.data_ptr(), PREC["fp64"], _stream_ptr(stream)))
+        return out
+
     # ------------------------------------------------- Lambda operand --
     def lambda_cache_bytes(self, prec: str) -> int:
         """Device bytes the plan-time Lambda operand of form ``prec`` needs."""
@@ -347,82 +445,37 @@ class Plan:
 
     # ------------------------------------------------------- host buffers --
     def alm2map_host(self, alm: torch.Tensor, prec: str = "fp64", out: torch.Tensor | None = None) -> torch.Tensor:
-        """alm2map of host coefficients into a host map: copies in on the
-        current stream, transforms, copies out, and waits.  Pinned host tensors
-        make the copies asynchronous."""
+        """alm2map of host coefficients into a host map through the library's
+        host-buffer call (one step); pinned host tensors make the copies
+        asynchronous."""
         if alm.is_cuda or alm.dtype != torch.complex128:
             raise TypeError("alm must be a host complex128 tensor")
-        a = alm.reshape(-1, self.nalm)
-        B = a.shape[0]
-        key = (B, prec)
-        if getattr(self, "_host_bufs", None) is None or self._host_bufs[0] != key:
-            dev = torch.device("cuda", torch.cuda.current_device())
-            self._host_bufs = (key, torch.empty((B, self.nalm), dtype=torch.complex128, device=dev),
-                               torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], device=dev))
-        _, d_alm, d_map = self._host_bufs
+        a = alm.reshape(-1, self.nalm).contiguous()
         if out is None:
-            out = torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], pin_memory=True)
-        d_alm.copy_(a, non_blocking=True)
-        self.alm2map(d_alm, prec, out=d_map)
-        out.copy_(d_map, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return out
-
+            out = torch.empty((a.shape[0], self.npix), dtype=MAP_DTYPE[prec], pin_memory=True)
+        return self.alm2map_host_stream([a], prec, outs=[out])[0]
 
     def alm2map_host_stream(self, alms, prec: str = "fp64", outs=None) -> list:
         """alm2map of a sequence of host batches (complex128, ideally pinned)
-        into host maps, pipelined: batch k+1's coefficients go up on one copy
-        stream and batch k-1's maps come down on another while batch k is
-        transformed on the current stream (two device buffer sets).  Every
-        batch's copies and transform happen; returns the host maps after
-        waiting for all of them."""
+        into host maps through the library's pipelined host-buffer call
+        (sht_alm2map_host): batch k+1's coefficients go up and batch k-1's maps
+        come down while batch k is transformed.  Returns the host maps."""
         alms = [a.reshape(-1, self.nalm) for a in alms]
         if not alms:
             return []
         B = alms[0].shape[0]
         for a in alms:
-            if a.is_cuda or a.dtype != torch.complex128 or a.shape[0] != B:
-                raise TypeError("host complex128 batches of equal size expected")
-        dev = torch.device("cuda", torch.cuda.current_device())
-        key = (B, prec)
-        if getattr(self, "_stream_bufs", None) is None or self._stream_bufs[0] != key:
-            self._stream_bufs = (key, [torch.empty((B, self.nalm), dtype=torch.complex128, device=dev) for _ in range(2)],
-                                 [torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], device=dev) for _ in range(2)])
-        _, d_alm, d_map = self._stream_bufs
+            if a.is_cuda or a.dtype != torch.complex128 or a.shape[0] != B or not a.is_contiguous():
+                raise TypeError("contiguous host complex128 batches of equal size expected")
         if outs is None:
             outs = [torch.empty((B, self.npix), dtype=MAP_DTYPE[prec], pin_memory=True) for _ in alms]
-        comp = torch.cuda.current_stream()
-        up, down = torch.cuda.Stream(), torch.cuda.Stream()
-        uploaded = [torch.cuda.Event() for _ in alms]
-        done = [torch.cuda.Event() for _ in alms]
-        consumed = [torch.cuda.Event() for _ in alms]   # input buffer free again
-        downloaded = [torch.cuda.Event() for _ in alms]  # output buffer free again
+        for o in outs:
+            if o.is_cuda or o.dtype != MAP_DTYPE[prec] or o.numel() != B * self.npix or not o.is_contiguous():
+                raise TypeError("bad host output tensor")
         n = len(alms)
-
-        def upload(k):
-            with torch.cuda.stream(up):
-                if k >= 2:
-                    up.wait_event(consumed[k - 2])
-                d_alm[k % 2].copy_(alms[k], non_blocking=True)
-                uploaded[k].record(up)
-
-        upload(0)
-        for k in range(n):
-            if k + 1 < n:
-                upload(k + 1)
-            comp.wait_event(uploaded[k])
-            if k >= 2:
-                comp.wait_event(downloaded[k - 2])
-            self.alm2map(d_alm[k % 2], prec, out=d_map[k % 2])
-            consumed[k].record(comp)
-            done[k].record(comp)
-            with torch.cuda.stream(down):
-                down.wait_event(done[k])
-                outs[k].copy_(d_map[k % 2], non_blocking=True)
-                downloaded[k].record(down)
-        down.synchronize()
-        up.synchronize()
-        comp.synchronize()
+        a_arr = (ctypes.c_void_p * n)(*[a.data_ptr() for a in alms])
+        m_arr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        check(lib().sht_alm2map_host(self._h, n, B, a_arr, m_arr, PREC[prec], _stream_ptr(None)))
         return outs
 
 

@@ -85,6 +85,21 @@ def test_multi_tensor_core_form(sht, prec):
         assert float(torch.linalg.norm(o - ref) / torch.linalg.norm(ref)) < (1e-5 if prec == "fp32_tc" else 1e-6)
 
 
+def test_multi_tensor_core_launch_count(sht):
+    """A tensor-core multi call is a fixed handful of launches whatever the
+    number of requests: one operand prep, one Legendre launch, and the ring
+    launches (register-FFT kernel and at most two shared-memory ring lists)."""
+    lmaxs = inputs.request_lmax(40, 11, 16, 160)
+    plans, alms = _requests(sht, lmaxs)
+    multi = sht.Multi(plans, "fp32_tc")
+    outs = multi.alm2map(alms)
+    torch.cuda.synchronize()
+    n0 = sht.kernel_launches()
+    multi.alm2map(alms, outs)
+    torch.cuda.synchronize()
+    assert 3 <= sht.kernel_launches() - n0 <= 5
+
+
 def test_multi_tensor_core_graph_replay(sht):
     lmaxs = [64, 128, 90, 256]
     plans, alms = _requests(sht, lmaxs)
