@@ -269,9 +269,11 @@ def check_accuracy(args, alm_h, outs):
 
 # --------------------------------------------------------------- our impl --
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel (else None)."""
+def traffic_for(kernel: str, algorithmic_bytes: float):
+    """DRAM bytes per launch of `kernel` at the benchmark's size: the
+    measured/algorithmic ratio of a one-kernel ncu capture on a smaller case
+    (profiles/traffic.json) times this launch's algorithmic bytes, while the
+    kernel's sources are unchanged since the capture (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -283,11 +285,24 @@ def traffic_for(kernel: str):
     ent = tab.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, ent["source"])
-    if not os.path.exists(src):
+    m = hashlib.sha256()
+    for src in ent["sources"]:
+        fp = os.path.join(ROOT, src)
+        if not os.path.exists(fp):
+            return None
+        m.update(open(fp, "rb").read())
+    if m.hexdigest()[:16] != ent.get("sources_sha256_16"):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+    return ent["ratio"] * algorithmic_bytes
+
+
+def tc_bop_bytes(L: int, M: int, prec: str) -> int:
+    """Bytes of the tensor-core B operand image (pieces of C_l a_lm per (m,
+    parity) segment, padded to whole stages of KC degrees, 128 columns)."""
+    kc = 8 if prec == "fp32_tc" else 16
+    kall = sum(2 * (((L - m + 1 + 2 * kc - 1) // (2 * kc)) * kc) for m in range(M + 1))
+    pieces, esz = {"fp32_tc": (2, 4), "bf16x3_tc": (2, 2), "bf16x6_tc": (3, 2)}[prec]
+    return pieces * 128 * kall * esz
 
 
 def legendre_flops(R: int, L: int, M: int, B: int, prec: str):
@@ -308,16 +323,18 @@ def stage_roofline(stage: str, ms: float, args, R: int, lambda_bytes):
         by = B * (nrings * (L + 1) * 2 * esz + npix * esz)
         ach = by / (ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
-        return {"kernel": "ring_synth (smooth and Bluestein ring lists, 2 launches)", "bound": "hbm",
-                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": traffic_for("ring_synth_fp64" if args.prec == "fp64" else "ring_synth_mf"),
+        return {"kernel": ("ring_synth (FP64, smooth and Bluestein ring lists)" if args.prec == "fp64" else
+                           "FP32 ring step: ring_reg (Bluestein rings) + ring_synth_mf (power-of-two and odd rings)"),
+                "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None if args.prec == "fp64" else traffic_for("ring_step", by),
+                "traffic_source": "ncu DRAM bytes of nside 512 / lmax 1024 / 64 maps scaled by algorithmic bytes",
                 "bytes_per_step": by, "bytes": "Delta read (complex) + map written", "ms_per_step": ms,
                 "peak_source": "MEASURED_PEAKS hbm_gbs"}
     if args.prec == "fp64":
         fl = legendre_flops(R, L, L, B, args.prec)
         ach = fl / (ms * 1e-3) / 1e12
         return {"kernel": "legendre_fwd_fp64", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_fwd_fp64"),
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2070 MHz)",
                 "flops_per_launch": fl, "ms_per_launch": ms}
     tpk = peaks.get("bf16_tflops_sustained", 1691.3) * TENSOR_PEAK_RATIO[args.prec]
@@ -332,14 +349,18 @@ def stage_roofline(stage: str, ms: float, args, R: int, lambda_bytes):
         ach = by / (ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         return {"kernel": "legendre_tc_stream (cached Lambda)", "bound": "hbm", "achieved": ach, "peak": peak,
-                "unit": "GB/s", "frac": ach / peak, "traffic": traffic_for("legendre_tc_stream"),
+                "unit": "GB/s", "frac": ach / peak, "traffic": traffic_for("legendre_tc_stream", by),
+                "traffic_source": "ncu DRAM bytes of nside 512 / lmax 1024 / 64 maps scaled by algorithmic bytes",
                 "bytes_per_launch": by, "ms_per_launch": ms, "peak_source": "MEASURED_PEAKS hbm_gbs",
                 "bytes": "Lambda operand + a_lm (complex128) + Delta (complex64)", "tensor": tensor}
     # the FP64 recurrence (3 flops per (l, m, ring pair)) bounds the kernel
     fl64 = 3.0 * R * nlm
     ach = fl64 / (ms * 1e-3) / 1e12
+    alg_by = tc_bop_bytes(L, L, args.prec) + B * nrings * (L + 1) * 8
     return {"kernel": "legendre_tc", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_tc"),
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("legendre_tc", alg_by),
+            "algorithmic_bytes": alg_by, "bytes": "B operand image + Delta written",
+            "traffic_source": "ncu DRAM bytes of nside 512 / lmax 1024 / 64 maps scaled by algorithmic bytes",
             "peak_source": "nominal FP64 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2070 MHz)",
             "flops_per_launch": fl64, "ms_per_launch": ms, "tensor": tensor}
 
