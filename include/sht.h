@@ -187,6 +187,18 @@ int sht_work_lists(int nitems, const long long *cost, int nlists, int *off, int 
  * differs.  SHT_EINVAL for a NULL plan. */
 int sht_debug_work_lists(sht_plan_t plan, int enable);
 
+/* Index checks of a debug build (the library compiled with -DSHT_DEBUG,
+ * `build(debug=True)`; no counterpart in the paper): the kernels check their
+ * tile, stage, tensor-memory, shared-memory and global offsets, count a
+ * violation in the plan's device words and clamp the offending index to 0
+ * instead of touching memory outside a buffer.  out (host, 5 entries):
+ * out[0] = 1 if the library was built with the checks (0: release build,
+ * the other entries 0), out[1] = violations since the last report, out[2] =
+ * tag of the first (the check's site), out[3] = its index, out[4] = its
+ * bound.  Synchronises the device and resets the count.  SHT_EINVAL for a
+ * NULL plan or array. */
+int sht_debug_report(sht_plan_t plan, unsigned long long *out);
+
 /* Test hook: which kernel runs the FP32 ring step (Eq. Delta2map) of the
  * tensor-core forms.  Two kernels exist: a register-FFT kernel for even rings
  * whose half-length N is a power of two in [256, 4096] (direct transform) or

@@ -31,7 +31,21 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags=()) -> str:
+DEBUG_BUILD = os.path.join(BUILD, "debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "libsht.so")
+
+
+def build(verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Compile libsht.so (sm_103a).  debug=True builds the index-checked
+    variant (-DSHT_DEBUG: every checked tile, stage and buffer offset counts
+    violations in the plan's debug words, see sht_debug_report) into
+    _build/debug/libsht.so; the release library is untouched."""
+    if debug:
+        return _build_into(DEBUG_BUILD, DEBUG_LIB, verbose, ("-DSHT_DEBUG",) + tuple(extra_flags))
+    return _build_into(BUILD, LIB, verbose, tuple(extra_flags))
+
+
+def _build_into(BUILD, LIB, verbose, extra_flags) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h")))

@@ -60,9 +60,10 @@ __device__ __forceinline__ void legendre_item(const DevPlan &P, const double2 *_
     double x = 0.0, p0 = 0.0, p1 = 0.0;
     int k = 0;
     if (live) {
+        const size_t so = SHT_IDX(P.dbg, (size_t)m * P.npairs + pair, (size_t)(P.mmax + 1) * P.npairs, 101);
         x = P.pair_x[pair];
-        p1 = P.start_v[(size_t)m * P.npairs + pair];
-        k = P.start_k[(size_t)m * P.npairs + pair];
+        p1 = P.start_v[so];
+        k = P.start_k[so];
     }
     double er[BC], ei[BC], orr[BC], oi[BC];
 #pragma unroll
@@ -83,7 +84,7 @@ __device__ __forceinline__ void legendre_item(const DevPlan &P, const double2 *_
             const long long q = mofs + (l0 - m) + j;
             const double c = P.coefC[q];
             double2 a = make_double2(0.0, 0.0);
-            if (b0 + b < nmaps) a = alm[(size_t)(b0 + b) * P.nalm + q];
+            if (b0 + b < nmaps) a = alm[SHT_IDX(P.dbg, (size_t)(b0 + b) * P.nalm + q, (size_t)nmaps * P.nalm, 102)];
             if (m == 0) a.y = 0.0;  // real field: Im(a_l0) is ignored
             sa[j][b] = make_double2(c * a.x, c * a.y);
         }
@@ -159,17 +160,20 @@ __device__ __forceinline__ void legendre_item(const DevPlan &P, const double2 *_
         for (int b = 0; b < BC; ++b) {
             if (b0 + b >= nmaps) break;
             const long long o = (long long)(b0 + b) * om.bstride + om.col;
-            delta[om.row_off[rr.x] + o] = make_double2(er[b] + orr[b], ei[b] + oi[b]);
-            if (rr.y >= 0) delta[om.row_off[rr.y] + o] = make_double2(er[b] - orr[b], ei[b] - oi[b]);
+            const long long tot = (long long)P.nrings * nmaps * om.bstride;
+            delta[SHT_IDX(P.dbg, om.row_off[rr.x] + o, tot, 103)] = make_double2(er[b] + orr[b], ei[b] + oi[b]);
+            if (rr.y >= 0)
+                delta[SHT_IDX(P.dbg, om.row_off[rr.y] + o, tot, 103)] = make_double2(er[b] - orr[b], ei[b] - oi[b]);
         }
         return;
     }
 #pragma unroll
     for (int b = 0; b < BC; ++b) {
         if (b0 + b >= nmaps) break;
-        double2 *d = delta + (size_t)(b0 + b) * P.nrings * M1;
-        d[(size_t)rr.x * M1 + m] = make_double2(er[b] + orr[b], ei[b] + oi[b]);
-        if (rr.y >= 0) d[(size_t)rr.y * M1 + m] = make_double2(er[b] - orr[b], ei[b] - oi[b]);
+        const size_t tot = (size_t)nmaps * P.nrings * M1, o = (size_t)(b0 + b) * P.nrings * M1;
+        delta[SHT_IDX(P.dbg, o + (size_t)rr.x * M1 + m, tot, 104)] = make_double2(er[b] + orr[b], ei[b] + oi[b]);
+        if (rr.y >= 0)
+            delta[SHT_IDX(P.dbg, o + (size_t)rr.y * M1 + m, tot, 104)] = make_double2(er[b] - orr[b], ei[b] - oi[b]);
     }
 }
 

@@ -634,7 +634,7 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
             double x = 0.0, p0 = 0.0, p1 = 0.0;
             int k = 0;
             if (live) {
-                const size_t o = (size_t)m * Q.npairs + pair;
+                const size_t o = SHT_IDX(Q.dbg, (size_t)m * Q.npairs + pair, (size_t)(Q.mmax + 1) * Q.npairs, 401);
                 x = Q.pair_x[pair];
                 if (s0 > 0) {
                     p0 = Q.warm_p0[o];
@@ -691,6 +691,7 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                 tc_fence_after();
                 for (int c0 = 0; c0 < 2 * ncols; c0 += 32) {
                     uint32_t v[32];
+                    SHT_CHECK(Q.dbg, 256 * set + c0 + 32 <= 512 && c0 + 32 <= 256, 402);
                     tmem_ld32(tmem + lane_base + (uint32_t)(256 * set + c0), v);
                     float *tp = tot + (size_t)c0 * kRows + row;
                     if (g == 0) {
@@ -753,6 +754,8 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                             const float4 v =
                                 *reinterpret_cast<const float4 *>(slot(side == 0 ? 32 * k : ncols + 32 * k, rw, 4 * sg));
                             if (ring >= 0) {
+                                // maps b, b + 1 are stored only where they exist (b < nmaps)
+                                SHT_CHECK(Q.dbg, ring < Q.nrings && m < M1, 403);
                                 float2 *d = w.dl + ((size_t)ring * M1 + m) * nmaps + b;
                                 if (vec && b + 1 < nmaps) {
                                     *reinterpret_cast<float4 *>(d) = v;
@@ -785,6 +788,10 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                 const unsigned char *blk = w.bb + (size_t)(w.seg[2 * m] / C::STEPS) * SB;
                 const int nst = nstages_of(Q, m);
                 const int s0 = first_stage(Q, m, w.rb);
+                // the item's stages stay inside its (m, parity) segments
+                SHT_CHECK(Q.dbg, w.seg[2 * m] % C::STEPS == 0 && nst * (C::STEPS / 2) <= w.seg[2 * m + 1] - w.seg[2 * m] + 0,
+                          404);
+                SHT_CHECK(Q.dbg, s0 >= 0 && s0 <= nst, 405);
                 for (int i = s0; i < s0 + kPrefetch && i < nst; ++i) bulk_prefetch_l2(blk + (size_t)i * SB, SB);
                 for (int i = s0; i < nst; ++i) {
                     const int s = (int)(gs % C::NS);
@@ -838,6 +845,7 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                             break;
                         }
                         tc_fence_after();
+                        SHT_CHECK(Q.dbg, 256 * set + 2 * ncols <= 512 && s < C::NS, 406);
 #pragma unroll
                         for (int par = 0; par < 2; ++par) {
                             const uint32_t d = tmem + (uint32_t)(256 * set + par * ncols);
@@ -1113,6 +1121,7 @@ legendre_tc_stream_kernel(const DevPlan P, const unsigned char *__restrict__ bbu
                             break;
                         }
                         tc_fence_after();
+                        SHT_CHECK(P.dbg, 256 * set + 2 * ncols <= 512 && s < NS, 407);
 #pragma unroll
                         for (int par = 0; par < 2; ++par) {
                             const uint32_t d = tmem + (uint32_t)(256 * set + par * ncols);

@@ -494,7 +494,8 @@ __device__ __forceinline__ void ring_synth_body(const DevPlan &P, int r, const t
     }
 
     for (int b = b_begin; b < b_end; ++b) {
-        const size_t row = P.ring_row ? (size_t)b * P.delta_rows + P.ring_row[r] : (size_t)b * P.nrings + r;
+        const size_t row = P.ring_row ? (size_t)b * P.delta_rows + SHT_IDX(P.dbg, P.ring_row[r], P.delta_rows, 201)
+                                      : (size_t)b * P.nrings + r;
         const C *D = delta + row * (size_t)(M + 1);
         // 1. phase shift + fold onto the half spectrum, into buf1[0..nb);
         //    the phase index (m ps) mod 2n advances by (n ps) mod 2n along m = k, k + n, ...
@@ -551,6 +552,7 @@ __device__ __forceinline__ void ring_synth_body(const DevPlan &P, int r, const t
                       : stockham<true, R>(buf0, buf1, N, W, s_rad, s_np);
 
         // 4. store the ring
+        SHT_CHECK(P.dbg, P.ofs[r] + n <= P.npix, 202);
         R *out = map + (size_t)b * P.npix + P.ofs[r];
         if (even) {
             for (int j = tid; j < N; j += kThreads) {
@@ -646,6 +648,8 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restric
 
     // 1. phase shift + fold of the gn maps onto the half spectrum, into A_g[0..nb):
     //    F_k = sum_{m = k mod n} Delta_m e^{i m phi0} + sum_{m >= 1, -m = k mod n} conj(...)
+    SHT_CHECK(P.dbg, r >= 0 && r < P.nrings && b0 + gn <= nmaps, 203);
+    SHT_CHECK(P.dbg, !(M + 1 <= cap) || (size_t)G * (M + 1) <= (size_t)G * capP, 204);
     const C *D = delta + (size_t)r * (M + 1) * nmaps + b0;  // D[m nmaps + g]
     const bool staged = M + 1 <= cap;
     const int n2 = 2 * n;
@@ -811,6 +815,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restric
 
     // 4. store the rings (Bluestein rings: times the chirp; even n: pixel pairs
     //    as one 8-byte store when aligned)
+    SHT_CHECK(P.dbg, P.ofs[r] + n <= P.npix, 205);
     for (int g = 0; g < gn; ++g) {
         const C *z = src + g * gs;
         R *out = map + (size_t)(b0 + g) * P.npix + P.ofs[r];

@@ -328,6 +328,7 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
                 const Unit U = unit_of(u);
                 const int M1 = U.P->mmax + 1;
                 const int nbox = (M1 + kBoxRows - 1) / kBoxRows;
+                SHT_CHECK(U.P->dbg, nbox * kBoxRows <= A.slot_rows && U.b0 % 2 == 0 && U.b0 + 2 <= U.nmaps, 308);
                 const uint32_t b = smem_u32(&bar[s]);
                 asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(b),
                              "r"((uint32_t)(nbox * kBoxRows * 16))
@@ -346,6 +347,7 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
                 const int M = U.P->mmax;
                 const float2 *src = U.delta + (size_t)U.r * (M + 1) * U.nmaps + U.b0;
                 const bool v16 = U.gn == 2 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (U.nmaps % 2 == 0);
+                SHT_CHECK(U.P->dbg, M < A.slot_rows, 309);
                 for (int m = tid; m <= M; m += kRT) {
                     const float2 *sm = src + (size_t)m * U.nmaps;
                     float2 *d = reinterpret_cast<float2 *>(dst + m);
@@ -423,6 +425,8 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
             if (rd > 0) __syncthreads();  // the previous round's last reads of the exchange buffer
             if (active) {
                 const float2 *D = reinterpret_cast<const float2 *>(slot) + gi;  // Delta_m at D[2 m]
+                SHT_CHECK(P.dbg, M < A.slot_rows && 2 * N <= n && N <= (blue ? L : L), 301);
+                SHT_CHECK(P.dbg, (h + 1) * (L + (L >> 4)) <= kXElems, 302);
                 // Table phases (phi0 = pi ps / n): the aliases m = k + t n of bin k share
                 // the phase e^{i k phi0} up to sg^t, sg = (-1)^ps, and the conjugated
                 // aliases m = t n - k contribute sg^t conj(Delta_m) e^{i k phi0}, so
@@ -466,9 +470,9 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
                     const int k = j + T * q;
                     float2 z = c2(0.f, 0.f);
                     if (k < N) {
-                        const float2 w = __ldg(Tw + 2 * k);  // e^{2 pi i k / n}
+                        const float2 w = __ldg(Tw + SHT_IDX(P.dbg, 2 * k, n2, 305));  // e^{2 pi i k / n}
                         if (one_alias) {
-                            const float2 ph = __ldg(Tw + pk);  // e^{i k phi0}
+                            const float2 ph = __ldg(Tw + SHT_IDX(P.dbg, pk, n2, 304));  // e^{i k phi0}
                             const float2 d1 = dget(k), d2 = dget(n - k), d3 = dget(N - k), d4 = dget(N + k);
                             const float2 a = c2(d1.x + sg * d2.x, d1.y - sg * d2.y);
                             const float2 b = cmul(cN, c2(d3.x + sg * d4.x, -(d3.y - sg * d4.y)));
@@ -484,7 +488,7 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
                         }
                         if (blue) z = cconj(cmul(z, __ldg(chirp + k)));
                     }
-                    xb[PX(k)] = z;
+                    xb[SHT_IDX(P.dbg, PX(k), L + (L >> 4), 303)] = z;
                     pk += dpk;
                     if (pk >= n2) pk -= n2;
                 }
@@ -505,10 +509,11 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
                 fft_reg(x, xb, j, T, L, W, active);
                 if (blue && f == 0 && active) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) x[q] = cmul(cconj(x[q]), __ldg(bh + j + T * q));
+                    for (int q = 0; q < 16; ++q) x[q] = cmul(cconj(x[q]), __ldg(bh + SHT_IDX(P.dbg, j + T * q, L, 307)));
                 }
             }
             if (active) {
+                SHT_CHECK(P.dbg, P.ofs[r] + n <= P.npix && U.b0 + gi < U.nmaps, 306);
                 float *out = U.map + (size_t)(U.b0 + gi) * P.npix + P.ofs[r];
                 const bool al = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
 #pragma unroll

@@ -725,6 +725,17 @@ int build_tables(sht_plan_s *p, const Rings &R)
             p->tc.kall_bf16 = off;
         }
     }
+#ifdef SHT_DEBUG
+    {
+        // debug words of the kernels' index checks (count, first tag, index, bound)
+        void *w = nullptr;
+        cudaError_t e = cudaMalloc(&w, 4 * sizeof(unsigned long long));
+        if (e != cudaSuccess) return fail(SHT_ENOMEM, "cudaMalloc(debug words): %s", cudaGetErrorString(e));
+        p->allocs.push_back(w);
+        if ((e = cudaMemset(w, 0, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+        d.dbg = static_cast<unsigned long long *>(w);
+    }
+#endif
     {
         void *st = nullptr;
         cudaError_t e = cudaMalloc(&st, sizeof(int));
@@ -1342,6 +1353,24 @@ int sht_debug_work_lists(sht_plan_t p, int enable)
     if (!p) return fail(SHT_EINVAL, "sht_debug_work_lists: NULL plan");
     std::lock_guard<std::mutex> lk(p->mu);
     p->sched_off = !enable;
+    return SHT_OK;
+}
+
+int sht_debug_report(sht_plan_t p, unsigned long long *out)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!out) return fail(SHT_EINVAL, "null output array");
+    out[0] = out[1] = out[2] = out[3] = out[4] = 0;
+#ifdef SHT_DEBUG
+    out[0] = 1;
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out + 1, p->dp.dbg, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->dp.dbg, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e, "debug words");
+#endif
     return SHT_OK;
 }
 

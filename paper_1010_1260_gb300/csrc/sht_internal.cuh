@@ -18,6 +18,30 @@ namespace sht {
 constexpr int kScaleUnit = 512;
 constexpr int kScaleHi = 256;
 
+// Debug builds (compiled with -DSHT_DEBUG, see build.py): index checks on the
+// kernels' tile, stage, shared-memory, tensor-memory and global offsets.  A
+// failed check counts in the plan's debug words (dbg[0] = violations, dbg[1]
+// = tag of the first, dbg[2] = its index, dbg[3] = its bound) and the index
+// is clamped to 0, so the kernel goes on without touching memory outside its
+// buffers (no trap).  Release builds compile the checks away.
+#ifdef SHT_DEBUG
+__device__ __forceinline__ long long sht_dbg_idx(unsigned long long *dbg, long long i, long long n, int tag)
+{
+    if (i >= 0 && i < n) return i;
+    if (dbg && atomicAdd(dbg, 1ull) == 0ull) {
+        dbg[1] = (unsigned long long)tag;
+        dbg[2] = (unsigned long long)i;
+        dbg[3] = (unsigned long long)n;
+    }
+    return 0;
+}
+#define SHT_IDX(dbg, i, n, tag) sht_dbg_idx((dbg), (long long)(i), (long long)(n), (tag))
+#define SHT_CHECK(dbg, cond, tag) ((cond) ? (void)0 : (void)sht_dbg_idx((dbg), -1, 0, (tag)))
+#else
+#define SHT_IDX(dbg, i, n, tag) (i)
+#define SHT_CHECK(dbg, cond, tag) ((void)0)
+#endif
+
 // Device-side view of a plan, passed by value to every kernel.
 struct DevPlan {
     int lmax, mmax, nrings, npairs;
@@ -95,6 +119,7 @@ struct DevPlan {
     // ring r is ring_row[r] of delta_rows per map (ring_row == nullptr: row r of nrings)
     const int *ring_row;
     int delta_rows;
+    unsigned long long *dbg;  // debug words of the index checks (nullptr unless built with SHT_DEBUG)
 };
 constexpr int kBlueMinPrime = 29;  // a prime factor at least this large selects Bluestein
 constexpr int kBlueMaxMb = 4096;   // largest Bluestein FFT length (shared-memory bound)

@@ -19,7 +19,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsht.so")
+# SHT_LIBRARY selects another build of the library (e.g. the index-checked
+# debug build, _build/debug/libsht.so); it must exist like the default.
+LIB_PATH = os.environ.get("SHT_LIBRARY") or os.path.join(_HERE, "_build", "libsht.so")
 
 SHT_OK = 0
 SHT_EINVAL = -1
@@ -96,6 +98,7 @@ def lib():
             L.sht_ring_lengths.argtypes = [P, IP]
             L.sht_alm2map_mpart.argtypes = [P, I, I, IP, IP, I, V, V, I, V]
             L.sht_ring_synth_part.argtypes = [P, I, I, IP, IP, I, V, V, I, V]
+            L.sht_debug_report.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
             L.sht_work_lists.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), I, ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.sht_map2alm.argtypes = [P, V, V, I, I, V]
@@ -112,7 +115,7 @@ def lib():
                       "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent",
                       "sht_work_lists", "sht_debug_work_lists", "sht_debug_ring_kernel",
                       "sht_alm2map_host", "sht_partition", "sht_ring_lengths", "sht_alm2map_mpart",
-                      "sht_ring_synth_part"):
+                      "sht_ring_synth_part", "sht_debug_report"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -390,6 +393,13 @@ class Plan:
         """Test hook: False makes the tensor-core launches take their items
         round robin instead of the balanced work lists (same maps)."""
         check(lib().sht_debug_work_lists(self._h, 1 if enable else 0))
+
+    def debug_report(self) -> dict:
+        """Index-check report of a debug build (checks_built False in release builds)."""
+        out = (ctypes.c_ulonglong * 5)()
+        check(lib().sht_debug_report(self._h, out))
+        return {"checks_built": bool(out[0]), "violations": int(out[1]), "first_tag": int(out[2]),
+                "first_index": int(out[3]), "first_bound": int(out[4])}
 
     def debug_ring_kernel(self, mode: int):
         """Test hook: FP32 ring-step kernel choice (0 default: register-FFT kernel
