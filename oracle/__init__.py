@@ -20,6 +20,12 @@ marshals numpy arrays.  Each function follows the paper (Hupca et al.,
                            map2almDef with the integral's measure), written out
                            as the literal transpose applied to w * y, divided
                            by the transpose's factor 2 for m > 0.
+* ``lam_spin2``         -- the spin-2 functions 2lambda_lm (orders m and -m)
+                           from the scalar lambda_lm, lambda_{l-1,m} by two
+                           spin raisings (an extension beyond the paper, for
+                           the polarisation field; definitions in sht_oracle.c).
+* ``alm2map_spin2``     -- Q + iU = -sum (E + iB) 2Y_lm over all m of both
+                           signs, pixel by pixel of each ring.
 * ``gl_grid``, ``healpix_grid`` -- ring geometry (Gauss-Legendre by Newton
                            iteration; HEALPix RING from Gorski et al. 2005).
 
@@ -70,8 +76,11 @@ def _load():
             lib.orc_lambda.argtypes = [I, I, D, D, I, P]
             lib.orc_alm2map.argtypes = [I, I, I, P, P, P, P, P, Lg, I, P, P, I, P, I]
             lib.orc_map2alm_adjoint.argtypes = [I, I, I, P, P, P, P, P, Lg, I, P, P, I, P, I]
+            lib.orc_lambda_spin2.argtypes = [I, I, D, D, P, P]
+            lib.orc_alm2map_spin2.argtypes = [I, I, I, P, P, P, P, P, Lg, I, P, P, P, P, I, P, I]
             for f in (lib.orc_gl_nodes, lib.orc_healpix_rings, lib.orc_lambda,
-                      lib.orc_alm2map, lib.orc_map2alm_adjoint):
+                      lib.orc_alm2map, lib.orc_map2alm_adjoint, lib.orc_lambda_spin2,
+                      lib.orc_alm2map_spin2):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -212,3 +221,42 @@ def map2alm(grid: dict, lmax: int, mmax: int, maps: np.ndarray, weights=None) ->
     m_of = np.concatenate([np.full(lmax + 1 - m, m) for m in range(mmax + 1)])
     g[:, m_of > 0] *= 0.5
     return g
+
+
+def lam_spin2(lmax: int, mmax: int, x: float, s: float | None = None):
+    """(plus, minus): 2lambda_lm(x) for orders m and -m, m-major packed (l < 2: 0)."""
+    lib = _load()
+    if s is None:
+        s = float(np.sqrt((1.0 - x) * (1.0 + x)))
+    plus = np.zeros(nalm(lmax, mmax))
+    minus = np.zeros(nalm(lmax, mmax))
+    if lib.orc_lambda_spin2(lmax, mmax, float(x), float(s), _p(plus), _p(minus)) != 0:
+        raise ValueError("bad lmax/mmax or sin(theta) <= 0")
+    return plus, minus
+
+
+def alm2map_spin2(grid: dict, lmax: int, mmax: int, elm: np.ndarray, blm: np.ndarray, rings=None,
+                  nthreads: int = 0):
+    """(Q, U) maps of (nmaps, nalm) complex E and B coefficients; pixels of
+    rings not selected are NaN."""
+    lib = _load()
+    elm = np.ascontiguousarray(np.atleast_2d(elm), dtype=np.complex128)
+    blm = np.ascontiguousarray(np.atleast_2d(blm), dtype=np.complex128)
+    nmaps = elm.shape[0]
+    if elm.shape != blm.shape or elm.shape[1] != nalm(lmax, mmax):
+        raise ValueError("E and B need shape (nmaps, nalm)")
+    sel = np.arange(grid["nrings"], dtype=np.int32) if rings is None else \
+        np.ascontiguousarray(rings, dtype=np.int32)
+    q = np.full((nmaps, grid["npix"]), np.nan)
+    u = np.full((nmaps, grid["npix"]), np.nan)
+    x = np.ascontiguousarray(grid["x"], dtype=np.float64)
+    st = np.ascontiguousarray(grid["st"], dtype=np.float64)
+    phi0 = np.ascontiguousarray(grid["phi0"], dtype=np.float64)
+    nphi = np.ascontiguousarray(grid["nphi"], dtype=np.int32)
+    ofs = np.ascontiguousarray(grid["ofs"], dtype=np.int64)
+    nt = lib.orc_alm2map_spin2(lmax, mmax, grid["nrings"], _p(x), _p(st), _p(phi0), _p(nphi), _p(ofs),
+                               grid["npix"], nmaps, _p(elm), _p(blm), _p(q), _p(u), len(sel), _p(sel),
+                               int(nthreads))
+    if nt < 0:
+        raise RuntimeError("orc_alm2map_spin2 failed (%d)" % nt)
+    return q, u

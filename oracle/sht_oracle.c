@@ -478,3 +478,204 @@ int orc_map2alm_adjoint(int lmax, int mmax, int nrings, const double *x, const d
     free(mu); free(jobs); free(th); free(part);
     return st_;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Spin-2 (polarisation) synthesis: the Q/U maps of E/B coefficients.        */
+/*                                                                            */
+/* Not in the paper (an extension of its transform to the CMB's polarisation  */
+/* field).  Definitions, written out here and pinned by the tests:            */
+/*   spin-raising  ð f = -(sin t)^s (d/dt + (i / sin t) d/dphi) ((sin t)^-s f) */
+/*   lowering      ð̄ f = -(sin t)^-s (d/dt - (i / sin t) d/dphi) ((sin t)^s f) */
+/*   2Y_lm = ð ð Y_lm / K_l,  -2Y_lm = ð̄ ð̄ Y_lm / K_l,                        */
+/*   K_l = sqrt((l-1) l (l+1) (l+2)), l >= 2, Y_lm = lambda_lm e^{i m phi}     */
+/*   (Y_{l,-m} = (-1)^m conj(Y_lm), Condon-Shortley as the scalar part),     */
+/*   Q + i U = - sum_{l>=2} sum_{|m|<=l} (E_lm + i B_lm) 2Y_lm,               */
+/*   E_{l,-m} = (-1)^m conj(E_lm), B likewise (Q, U real).                    */
+/* With L = lambda_lm, D = d lambda_lm / d theta, c = cos t, s = sin t, the  */
+/* two raisings give (m of either sign)                                       */
+/*   K_l 2lambda_lm = D'' - D (c + 2m)/s + L (2 m c + m^2)/s^2                 */
+/* and the Legendre equation D'' = -(c/s) D + (m^2/s^2 - l(l+1)) L with       */
+/* s D = l c L - c_lm lambda_{l-1,m}, c_lm = sqrt((2l+1)(l^2-m^2)/(2l-1)),   */
+/* turn it into values of lambda_lm and lambda_{l-1,m} only:                  */
+/*   K_l 2lambda_lm = -2 (c + m) (l c L - c_lm L1)/s^2                        */
+/*                    + L ((2 m^2 + 2 m c)/s^2 - l (l+1)).                    */
+/* The oracle evaluates this for every m in [-M, M] (lambda_{l,-m} =          */
+/* (-1)^m lambda_lm) and sums the definition literally, pixel by pixel of    */
+/* each ring, over all m of both signs.  sin t must be > 0.                   */
+/* ------------------------------------------------------------------------ */
+
+/* 2lambda_lm(t) for m >= 0 (plus) and for -m (minus), m-major packed like the
+ * scalar table (entries with l < 2 are 0).  lam: the scalar table at this
+ * ring (true values, from orc_lambda_impl). */
+static void orc_spin2_from_scalar(int lmax, int mmax, double x, double s, const double *lam,
+                                  double *plus, double *minus)
+{
+    const double u = 1.0 / (s * s);
+    for (int m = 0; m <= mmax; m++) {
+        const long c = orc_mofs(lmax, m);
+        for (int l = m; l <= lmax; l++) {
+            if (l < 2) {
+                plus[c + l - m] = 0.0;
+                minus[c + l - m] = 0.0;
+                continue;
+            }
+            const double L = lam[c + l - m];
+            const double L1 = (l - 1 >= m) ? lam[c + l - 1 - m] : 0.0;
+            const double clm = sqrt((2.0 * l + 1.0) * ((double)l * l - (double)m * m) / (2.0 * l - 1.0));
+            const double K = sqrt((l - 1.0) * l * (l + 1.0) * (l + 2.0));
+            const double sD = l * x * L - clm * L1; /* s dlambda/dtheta */
+            for (int sg = 0; sg < 2; sg++) {
+                /* order mm = +m or -m: lambda_{l,-m} = (-1)^m lambda_lm (and likewise L1) */
+                const double mm = sg ? -(double)m : (double)m;
+                const double f = (sg && (m & 1)) ? -1.0 : 1.0;
+                const double Lm = f * L, sDm = f * sD;
+                const double v = (-2.0 * (x + mm) * sDm * u + Lm * ((2.0 * mm * mm + 2.0 * mm * x) * u - l * (l + 1.0))) / K;
+                if (sg)
+                    minus[c + l - m] = v;
+                else
+                    plus[c + l - m] = v;
+            }
+        }
+    }
+}
+
+int orc_lambda_spin2(int lmax, int mmax, double x, double s, double *plus, double *minus)
+{
+    if (lmax < 0 || mmax < 0 || mmax > lmax || !(s > 0.0)) return -1;
+    double *mu = (double *)malloc(sizeof(double) * (mmax + 1));
+    double *lam = (double *)malloc(sizeof(double) * orc_nalm(lmax, mmax));
+    if (!mu || !lam) { free(mu); free(lam); return -2; }
+    orc_mu(mmax, mu);
+    orc_lambda_impl(lmax, mmax, x, s, 1, mu, lam);
+    orc_spin2_from_scalar(lmax, mmax, x, s, lam, plus, minus);
+    free(mu); free(lam);
+    return 0;
+}
+
+typedef struct {
+    int lmax, mmax, nmaps;
+    const double *x, *st, *phi0;
+    const int *nphi;
+    const long *ofs;
+    const double *elm, *blm; /* [nmaps][nalm][2] */
+    double *qmap, *umap;     /* [nmaps][npix] */
+    long npix;
+    const int *rings;
+    int nsel;
+    const double *mu;
+    int tid, nthreads;
+    int status;
+} orc_spin_job;
+
+static void *orc_spin_worker(void *arg)
+{
+    orc_spin_job *J = (orc_spin_job *)arg;
+    const int L = J->lmax, M = J->mmax;
+    const long nalm = orc_nalm(L, M);
+    double *lam = (double *)malloc(sizeof(double) * nalm);
+    double *lp = (double *)malloc(sizeof(double) * nalm);
+    double *lmn = (double *)malloc(sizeof(double) * nalm);
+    double *cr = (double *)malloc(sizeof(double) * (2 * M + 1)); /* C_m, m = -M..M */
+    double *ci = (double *)malloc(sizeof(double) * (2 * M + 1));
+    if (!lam || !lp || !lmn || !cr || !ci) {
+        J->status = -2;
+        free(lam); free(lp); free(lmn); free(cr); free(ci);
+        return NULL;
+    }
+    for (int q = J->tid; q < J->nsel; q += J->nthreads) {
+        const int r = J->rings[q];
+        const int np = J->nphi[r];
+        orc_lambda_impl(L, M, J->x[r], J->st[r], 1, J->mu, lam);
+        orc_spin2_from_scalar(L, M, J->x[r], J->st[r], lam, lp, lmn);
+        /* tab[q] = e^{2 pi i q / np}; ph[m + M] = e^{i m phi0} */
+        double *tab = (double *)malloc(sizeof(double) * 2 * np);
+        double *ph = (double *)malloc(sizeof(double) * 2 * (2 * M + 1));
+        if (!tab || !ph) { free(tab); free(ph); J->status = -2; break; }
+        for (int t = 0; t < np; t++) {
+            tab[2 * t] = cos(2.0 * ORC_PI * t / np);
+            tab[2 * t + 1] = sin(2.0 * ORC_PI * t / np);
+        }
+        for (int m = -M; m <= M; m++) {
+            ph[2 * (m + M)] = cos(m * J->phi0[r]);
+            ph[2 * (m + M) + 1] = sin(m * J->phi0[r]);
+        }
+        for (int b = 0; b < J->nmaps; b++) {
+            const double *E = J->elm + (long)b * nalm * 2, *B = J->blm + (long)b * nalm * 2;
+            /* C_m = - sum_l (E_lm + i B_lm) 2lambda_lm for m = -M..M, with
+             * E_{l,-m} = (-1)^m conj(E_lm) and B likewise */
+            for (int m = -M; m <= M; m++) {
+                const int am = m < 0 ? -m : m;
+                const long c = orc_mofs(L, am);
+                const double f = (m < 0 && (am & 1)) ? -1.0 : 1.0;
+                double sr = 0.0, si = 0.0;
+                for (int l = am; l <= L; l++) {
+                    double er = E[2 * (c + l - am)], ei = E[2 * (c + l - am) + 1];
+                    double br = B[2 * (c + l - am)], bi = B[2 * (c + l - am) + 1];
+                    if (am == 0) { ei = 0.0; bi = 0.0; } /* real fields: E_l0, B_l0 real */
+                    if (m < 0) { er *= f; ei *= -f; br *= f; bi *= -f; }
+                    const double y = (m < 0) ? lmn[c + l - am] : lp[c + l - am];
+                    /* (E + i B) y = (er - bi) y + i (ei + br) y */
+                    sr -= (er - bi) * y;
+                    si -= (ei + br) * y;
+                }
+                cr[m + M] = sr;
+                ci[m + M] = si;
+            }
+            /* Q + i U at phi_j = phi0 + 2 pi j / np: sum_m C_m e^{i m phi_j}, with
+             * e^{i m phi_j} = e^{i m phi0} e^{2 pi i ((m j) mod np) / np} */
+            double *qo = J->qmap + (long)b * J->npix + J->ofs[r];
+            double *uo = J->umap + (long)b * J->npix + J->ofs[r];
+            for (int j = 0; j < np; j++) {
+                double ar = 0.0, ai = 0.0;
+                for (int m = -M; m <= M; m++) {
+                    long qq = ((long)m * j) % np;
+                    if (qq < 0) qq += np;
+                    const double pr = ph[2 * (m + M)], pi_ = ph[2 * (m + M) + 1];
+                    const double tr = tab[2 * qq], ti = tab[2 * qq + 1];
+                    const double er = pr * tr - pi_ * ti, ei = pr * ti + pi_ * tr;
+                    ar += cr[m + M] * er - ci[m + M] * ei;
+                    ai += cr[m + M] * ei + ci[m + M] * er;
+                }
+                qo[j] = ar;
+                uo[j] = ai;
+            }
+        }
+        free(tab);
+        free(ph);
+    }
+    free(lam); free(lp); free(lmn); free(cr); free(ci);
+    return NULL;
+}
+
+/* Spin-2 synthesis on the selected rings: elm, blm [nmaps][nalm] complex
+ * (m-major packed, entries with l < 2 ignored), qmap, umap [nmaps][npix].
+ * Returns the number of threads used or a negative error (-1 also when a
+ * selected ring has sin(theta) = 0). */
+int orc_alm2map_spin2(int lmax, int mmax, int nrings, const double *x, const double *st,
+                      const double *phi0, const int *nphi, const long *ofs, long npix, int nmaps,
+                      const double *elm, const double *blm, double *qmap, double *umap, int nsel,
+                      const int *rings, int nthreads)
+{
+    if (lmax < 0 || mmax < 0 || mmax > lmax || nmaps < 0 || nsel < 0) return -1;
+    for (int q = 0; q < nsel; q++)
+        if (rings[q] < 0 || rings[q] >= nrings || !(st[rings[q]] > 0.0)) return -1;
+    const int nt = orc_nthreads(nthreads);
+    double *mu = (double *)malloc(sizeof(double) * (mmax + 1));
+    orc_spin_job *jobs = (orc_spin_job *)calloc(nt, sizeof(orc_spin_job));
+    pthread_t *th = (pthread_t *)calloc(nt, sizeof(pthread_t));
+    if (!mu || !jobs || !th) { free(mu); free(jobs); free(th); return -2; }
+    orc_mu(mmax, mu);
+    for (int t = 0; t < nt; t++) {
+        orc_spin_job j = {lmax, mmax, nmaps, x, st, phi0, nphi, ofs, elm, blm, qmap, umap, npix,
+                          rings, nsel, mu, t, nt, 0};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, orc_spin_worker, &jobs[t]);
+    }
+    int st_ = nt;
+    for (int t = 0; t < nt; t++) {
+        pthread_join(th[t], NULL);
+        if (jobs[t].status) st_ = jobs[t].status;
+    }
+    free(mu); free(jobs); free(th);
+    return st_;
+}
