@@ -530,6 +530,7 @@ def run_ours(args):
         del alm, out
         torch.cuda.empty_cache()
         for name, fn in (("differentiation_form", lambda: measure_differentiation(args, plan, args.side_steps)),
+                         ("polarisation_form", lambda: measure_spin2(args, plan, args.side_steps)),
                          ("batching_form", lambda: measure_requests(args, rank, world, args.side_steps, 1))):
             try:
                 side[name] = fn()
@@ -571,6 +572,7 @@ def run_ours(args):
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
             "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e, "accuracy": accuracy,
             "fp64_path": fp64_path, "differentiation_form": side.get("differentiation_form"),
+            "polarisation_form": side.get("polarisation_form"),
             "batching_form": side.get("batching_form")}
     if world == 1 and not args.no_cpu_baseline:
         v, dt, nt, desc = cpu_oracle_sample(args, args.cpu_rings)
@@ -664,6 +666,32 @@ def measure_differentiation(args, plan, steps):
     del a0, w, d
     torch.cuda.empty_cache()
     return out
+
+
+def measure_spin2(args, plan, steps):
+    """The polarisation (spin-2) synthesis, FP64: 4 maps of E and B at the
+    headline's grid and band limit into Q and U, median of `steps` calls."""
+    import torch
+    from paper_1010_1260_gb300 import inputs
+    B = 4
+    dev = torch.device("cuda", torch.cuda.current_device())
+    e = torch.from_numpy(inputs.batch_alm(args.lmax, args.lmax, 61, B)).to(dev)
+    b = torch.from_numpy(inputs.batch_alm(args.lmax, args.lmax, 62, B)).to(dev)
+    out = torch.empty((B, 2, plan.npix), dtype=torch.float64, device=dev)
+    plan.alm2map_spin2(e, b, out=out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        plan.alm2map_spin2(e, b, out=out)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median([ev[k].elapsed_time(ev[k + 1]) for k in range(steps)])
+    del e, b, out
+    torch.cuda.empty_cache()
+    return {"maps": B, "ms_per_call": ms, "qu_maps_per_s": B / (ms * 1e-3), "steps": steps, "dtype": "f64",
+            "workload": "E, B Gaussian (C_l = 1/(l(l+1))) -> Q, U on the headline grid"}
 
 
 def run_requests(args):

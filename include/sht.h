@@ -278,6 +278,26 @@ int sht_set_tiles(sht_plan_t plan, const int *vals, int n);
  * entry a call reads is first written by that call. */
 int sht_alm2map_noalloc(sht_plan_t plan, int nbatch, const void *alm_dev, void *map_dev, void *stream);
 
+/* Spin-2 (polarisation) synthesis, SHT_FP64 only; not in the paper (its
+ * transform extended to the CMB's Q/U field).  Q + i U = -sum_{l>=2}
+ * sum_{|m|<=l} (E_lm + i B_lm) 2Y_lm with the spin-weighted harmonics
+ * 2Y_lm = ð ð Y_lm / K_l, K_l = sqrt((l-1) l (l+1) (l+2)), ð f = -(sin t)^s
+ * (d/dt + (i/sin t) d/dphi)((sin t)^-s f) on spin-s quantities, Y_lm as in
+ * sht_alm2map (Condon-Shortley), E_{l,-m} = (-1)^m conj(E_lm) and B alike.
+ * elm_dev, blm_dev: nbatch x nalm complex128 each (layout of sht_alm2map;
+ * entries with l < 2 and Im of m = 0 are ignored); map_dev: nbatch x 2 x npix
+ * float64, map b's Q then its U.  Each map's Q and U go through the ring step
+ * of sht_alm2map as two real syntheses of Delta_m^Q = -sum_l (E F1 + i B F2),
+ * Delta_m^U = -sum_l (B F1 - i E F2), F1, F2 the half sum and half difference
+ * of the spin +2 and -2 functions, built from the scalar recurrence (Eq.
+ * assLegRec) and its derivative relation.  Every ring needs sin(theta) > 0
+ * (SHT_EUNSUPPORTED otherwise); the accuracy near the poles is limited by
+ * cancellation of terms of size l^2 / sin^2(theta) (relative 1e-11 at the
+ * first HEALPix ring of nside 1024).  Errors: SHT_EINVAL, SHT_EUNSUPPORTED,
+ * SHT_ENOMEM, SHT_ECUDA. */
+int sht_alm2map_spin2(sht_plan_t plan, int nbatch, const void *elm_dev, const void *blm_dev, void *map_dev, int prec,
+                      void *stream);
+
 /* alm2map of coefficients in host memory into maps in host memory: nsteps
  * batches of nbatch maps, batch k read from alm_host[k] (nbatch x nalm
  * complex128, m-major packed) and written to map_host[k] (nbatch x npix,

@@ -38,6 +38,7 @@ struct sht_plan_s {
     size_t ws_bytes = 0;
     std::vector<int> rings_smooth_h, rings_blue_h;  // host copies of the ring lists
     std::vector<int> nphi_h;                       // pixels per ring (host copy)
+    double min_sin = 0.0;                          // smallest sin(theta) over the rings
     // FP32 ring step: the register-FFT kernel's ring list and the rings left to
     // the shared-memory kernel, per kernel choice (sht_debug_ring_kernel)
     struct RfSet {
@@ -672,6 +673,7 @@ int build_tables(sht_plan_s *p, const Rings &R)
     if ((rc = upload(p, tw32, &d.tw32))) return rc;
     p->rings_smooth_h = rsmooth;
     p->nphi_h = R.nphi;
+    p->min_sin = R.s.empty() ? 0.0 : *std::min_element(R.s.begin(), R.s.end());
     p->rings_blue_h = rblue;
     d.n_smooth = (int)rsmooth.size();
     d.n_blue = (int)rblue.size();
@@ -1451,6 +1453,45 @@ int sht_alm2map_batch(sht_plan_t p, int nbatch, const void *alm_dev, void *map_d
 int sht_alm2map(sht_plan_t p, const void *alm_dev, void *map_dev, int prec, void *stream)
 {
     return sht_alm2map_batch(p, 1, alm_dev, map_dev, prec, stream);
+}
+
+int sht_alm2map_spin2(sht_plan_t p, int nbatch, const void *elm_dev, const void *blm_dev, void *map_dev, int prec,
+                      void *stream)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (nbatch < 0) return fail(SHT_EINVAL, "nbatch < 0");
+    if (prec != SHT_FP64 && prec != SHT_FP32_TC && prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
+        return fail(SHT_EINVAL, "unknown precision %d", prec);
+    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "the spin-2 transform is built for SHT_FP64");
+    if (!(p->min_sin > 0.0)) return fail(SHT_EUNSUPPORTED, "spin-2 transform: a ring lies on a pole (sin theta = 0)");
+    if (nbatch == 0) return SHT_OK;
+    if (!elm_dev || !blm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
+    if (2LL * nbatch > 32768) return fail(SHT_EUNSUPPORTED, "nbatch > 16384");
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t per_map = (size_t)p->nrings * (p->mmax + 1) * sizeof(double2);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nbatch, max_ws_bytes() / (2 * per_map)));
+    if ((rc = ensure_ws(p, 2 * per_map * chunk))) return rc;
+    double2 *delta = static_cast<double2 *>(p->ws);
+    for (int b0 = 0; b0 < nbatch; b0 += chunk) {
+        const int nb = std::min(chunk, nbatch - b0);
+        StageScope s1(p, SHT_STAGE_LEGENDRE, st);
+        cudaError_t e = sht::launch_legendre_spin2_fp64(p->dp, static_cast<const double2 *>(elm_dev) + (size_t)b0 * p->nalm,
+                                                        static_cast<const double2 *>(blm_dev) + (size_t)b0 * p->nalm,
+                                                        delta, nb, st);
+        s1.done(e);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_spin2_fp64 launch");
+        // Q and U of every map are two real syntheses of the ring step
+        StageScope s2(p, SHT_STAGE_RING, st);
+        e = sht::launch_ring_synth_fp64(p->dp, delta, static_cast<double *>(map_dev) + (size_t)2 * b0 * p->npix, 2 * nb,
+                                        p->fp64_ring_g, st);
+        s2.done(e, sht::ring_launches(p->dp));
+        if (e != cudaSuccess) return cuda_fail(e, "ring_synth_fp64 launch (spin 2)");
+    }
+    return SHT_OK;
 }
 
 int sht_alm2map_host(sht_plan_t p, int nsteps, int nbatch, const void *const *alm_host, void *const *map_host,

@@ -38,7 +38,7 @@ __device__ __forceinline__ long long sht_dbg_idx(unsigned long long *dbg, long l
 #define SHT_IDX(dbg, i, n, tag) sht_dbg_idx((dbg), (long long)(i), (long long)(n), (tag))
 #define SHT_CHECK(dbg, cond, tag) ((cond) ? (void)0 : (void)sht_dbg_idx((dbg), -1, 0, (tag)))
 #else
-#define SHT_IDX(dbg, i, n, tag) (i)
+#define SHT_IDX(dbg, i, n, tag) ((void)(n), (i))
 #define SHT_CHECK(dbg, cond, tag) ((void)0)
 #endif
 
@@ -143,6 +143,11 @@ cudaError_t launch_legendre_fwd_fp64(const DevPlan &P, const double2 *alm, doubl
 // (complex128), row_off[r] laying out the rings for an all-to-all exchange.
 cudaError_t launch_legendre_mpart_fp64(const DevPlan &P, const double2 *alm, double2 *delta, int nmaps,
                                        const int *mlist, int nm, const long long *row_off, cudaStream_t st);
+// Spin-2 Legendre step (polarisation), FP64: E, B [map][nalm] complex128 ->
+// Delta of Q and U, delta[((2 b + q) nrings + ring) (mmax + 1) + m], q = 0 (Q), 1 (U);
+// the ring step then runs on 2 nmaps "maps" and writes [map][Q, U][npix].
+cudaError_t launch_legendre_spin2_fp64(const DevPlan &P, const double2 *elm, const double2 *blm, double2 *delta,
+                                       int nmaps, cudaStream_t st);
 // Gather of the exchanged blocks into the ring step's layout: for order m,
 // rows of the partition's rings, maps b:
 //   dst[(b nrows + row) (mmax + 1) + m] = src[m_off[m] + (row nmaps + b) m_cnt[m] + m_col[m]].

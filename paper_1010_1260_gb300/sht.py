@@ -99,6 +99,7 @@ def lib():
             L.sht_alm2map_mpart.argtypes = [P, I, I, IP, IP, I, V, V, I, V]
             L.sht_ring_synth_part.argtypes = [P, I, I, IP, IP, I, V, V, I, V]
             L.sht_debug_report.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
+            L.sht_alm2map_spin2.argtypes = [P, I, V, V, V, I, V]
             L.sht_work_lists.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), I, ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.sht_map2alm.argtypes = [P, V, V, I, I, V]
@@ -115,7 +116,7 @@ def lib():
                       "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent",
                       "sht_work_lists", "sht_debug_work_lists", "sht_debug_ring_kernel",
                       "sht_alm2map_host", "sht_partition", "sht_ring_lengths", "sht_alm2map_mpart",
-                      "sht_ring_synth_part", "sht_debug_report"):
+                      "sht_ring_synth_part", "sht_debug_report", "sht_alm2map_spin2"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -293,6 +294,27 @@ class Plan:
         check(lib().sht_alm2map_batch(self._h, B, a.data_ptr(), out.data_ptr(), PREC[prec],
                                       _stream_ptr(stream)))
         return out.reshape(self.npix) if single else out.reshape(B, self.npix)
+
+    def alm2map_spin2(self, elm: torch.Tensor, blm: torch.Tensor, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+        """Q and U maps (float64 [B, 2, npix] or [2, npix]) of spin-2 E and B
+        coefficients (cuda complex128, [B, nalm] or [nalm]); FP64."""
+        for t in (elm, blm):
+            if not (t.is_cuda and t.dtype == torch.complex128):
+                raise TypeError("E and B must be CUDA complex128 tensors")
+        single = elm.dim() == 1
+        e = elm.reshape(-1, self.nalm).contiguous()
+        b = blm.reshape(-1, self.nalm).contiguous()
+        if e.shape != b.shape:
+            raise ValueError("E and B differ in shape")
+        B = e.shape[0]
+        if out is None:
+            out = torch.empty((B, 2, self.npix), dtype=torch.float64, device=e.device)
+        elif not (out.is_contiguous() and out.dtype == torch.float64 and out.numel() == 2 * B * self.npix):
+            raise TypeError("bad output tensor")
+        check(lib().sht_alm2map_spin2(self._h, B, e.data_ptr(), b.data_ptr(), out.data_ptr(), PREC["fp64"],
+                                      _stream_ptr(stream)))
+        return out.reshape(2, self.npix) if single else out.reshape(B, 2, self.npix)
 
     def map2alm_adjoint(self, maps: torch.Tensor, prec: str = "fp64", out: torch.Tensor | None = None,
                         stream=None) -> torch.Tensor:

@@ -61,6 +61,10 @@ def main():
             recv = torch.cat([sends[p][sum(sizes[p][:q]): sum(sizes[p][:q]) + sizes[p][q]] for p in range(3)])
             plan.ring_synth_part(recv, mo, ro, q, 3, B, out=out)
         res["errors"][name + "/partitioned"] = rl2(out.cpu().numpy(), want)
+        bb = inputs.batch_alm(L, L, 950 + L, B)
+        qu = plan.alm2map_spin2(ad, torch.from_numpy(bb).cuda()).cpu().numpy()
+        qw, uw = oracle.alm2map_spin2(og, L, L, a, bb)
+        res["errors"][name + "/spin2/fp64"] = max(rl2(qu[:, 0], qw), rl2(qu[:, 1], uw))
         hosted = plan.alm2map_host_stream([torch.from_numpy(a).pin_memory()] * 3, "bf16x6_tc")
         res["errors"][name + "/host"] = rl2(hosted[-1].double().numpy(), want)
     # the batching form, both kinds, over the three plans

@@ -69,6 +69,7 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.sht_ring_synth_part(None, 1, 1, None, None, 0, None, None, 0, None) == sht.SHT_EINVAL
     assert lib.sht_ring_lengths(None, None) == sht.SHT_EINVAL
     assert lib.sht_debug_report(None, None) == sht.SHT_EINVAL
+    assert lib.sht_alm2map_spin2(None, 1, None, None, None, 0, None) == sht.SHT_EINVAL
     assert lib.sht_skip_evanescent(None, 1) == sht.SHT_EINVAL
     assert lib.sht_map2alm_batch(None, 1, None, None, 0, 0, None) == sht.SHT_EINVAL
     assert lib.sht_set_ring_weights(None, None) == sht.SHT_EINVAL
