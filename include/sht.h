@@ -212,6 +212,27 @@ int sht_debug_report(sht_plan_t plan, unsigned long long *out);
  * another mode. */
 int sht_debug_ring_kernel(sht_plan_t plan, int mode);
 
+/* Orders of the tensor-core forms' Delta that can be nonzero, per ring (no
+ * counterpart in the paper; it follows from the evanescent skip below): out
+ * (host, nrings entries) receives for ring r the limit M_r such that every
+ * recurrence value lambda_lm(theta_r) / C_l at orders m >= M_r, l <= lmax,
+ * is below the FP32 range (rounds to zero in the precision forms), so that
+ * Delta_m(theta_r) is exactly zero there.  The Legendre launches of those
+ * forms skip the (m, ring block) items whose order is past every ring of the
+ * block, and the FP32 ring kernels read only m < M_r.  mmax + 1 for every
+ * ring while the skip is disabled.  Builds the skip tables if needed (one
+ * FP64 pass over the recurrence, synchronous).  SHT_EINVAL for a NULL plan or
+ * array. */
+int sht_order_limits(sht_plan_t plan, int *out);
+
+/* Test hook: overwrite the plan's Delta workspace with 0xFF bytes (NaN in
+ * FP32 and FP64) and synchronise the device.  The tensor-core forms leave
+ * unwritten the Delta entries that are exactly zero past a ring's last
+ * nonzero order, and the ring kernels must not read them: after this call a
+ * kernel that did would put NaN into the maps.  No effect before the first
+ * transform (no workspace yet).  SHT_EINVAL for a NULL plan. */
+int sht_debug_poison_delta(sht_plan_t plan);
+
 /* Evanescent skip of the tensor-core forms (on by default).  For large m
  * near the poles lambda_lm is far below the FP32 range for many degrees (the
  * region below the turning point, where Algorithm 2's rescaling keeps the
@@ -383,6 +404,10 @@ typedef struct sht_multi_s *sht_multi_t;
 int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht_multi_t *out);
 int sht_multi_alm2map(sht_multi_t multi, const void *const *alm_dev, void *const *map_dev, void *stream);
 int sht_multi_destroy(sht_multi_t multi);
+
+/* Test hook: sht_debug_poison_delta for the Delta workspace of a
+ * multi-request context.  SHT_EINVAL for a NULL context. */
+int sht_multi_debug_poison_delta(sht_multi_t multi);
 int sht_alm2map_multi(int nreq, const sht_plan_t *plans, const void *const *alm_dev, void *const *map_dev,
                       int prec, void *stream);
 

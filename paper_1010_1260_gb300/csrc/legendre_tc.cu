@@ -1249,11 +1249,13 @@ cudaError_t run_prep(const DevPlan &P, const TcWork &W, const double2 *alm, int 
 // operations), rescaled as soon as |p| > 2^256 while k < 0; rescaling by 2^-512
 // is exact, so a producer that starts from this state computes the same values
 // as one that starts at degree m, and the values it skips would all have
-// rounded to zero.  At least one group is kept per item.  One CTA of 128
-// threads per (ring block, m).
+// rounded to zero.  At least one group is kept per item.  pair_lim[pair]
+// becomes 1 + the largest m at which the pair has a representable value (its
+// Delta is exactly zero at every larger order).  One CTA of 128 threads per
+// (ring block, m).
 __global__ void __launch_bounds__(kRows)
 warm_start_kernel(const DevPlan P, int *__restrict__ skip_g, double *__restrict__ wp0, double *__restrict__ wp1,
-                  int *__restrict__ wk)
+                  int *__restrict__ wk, int *__restrict__ pair_lim)
 {
     __shared__ int s_first;
     const int L = P.lmax;
@@ -1276,6 +1278,7 @@ warm_start_kernel(const DevPlan P, int *__restrict__ skip_g, double *__restrict_
         for (int l = m; l <= L && live; ++l) {
             if (k == 0 && fabs(p1) >= 0x1p-126) {
                 atomicMin(&s_first, l);
+                atomicMax(&pair_lim[pair], m + 1);
                 break;
             }
             const double a = (l + 1 <= L) ? __ldg(&P.coefA[mofs + (l + 1 - m)]) : 0.0;
@@ -1449,10 +1452,10 @@ size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec)
 }
 
 cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,
-                              cudaStream_t st)
+                              int *pair_lim, cudaStream_t st)
 {
     dim3 grid((P.npairs + kRows - 1) / kRows, P.mmax + 1);
-    warm_start_kernel<<<grid, kRows, 0, st>>>(P, skip_g, warm_p0, warm_p1, warm_k);
+    warm_start_kernel<<<grid, kRows, 0, st>>>(P, skip_g, warm_p0, warm_p1, warm_k, pair_lim);
     return cudaGetLastError();
 }
 

@@ -633,7 +633,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restric
     const int gs = capP;
     const int tid = threadIdx.x;
     const int n = P.nphi[r];
-    const int M = P.mmax;
+    const int M = ring_mtop(P, r);  // Delta_m is zero past it (never read)
     const C *T = tw_table<R>(P) + P.twofs[r];  // T[q] = e^{i pi q / n}, q < 2n
     const int ps = P.ps[r];
     const double phi0 = P.phi0[r];
@@ -650,7 +650,7 @@ ring_synth_mf_kernel(const __grid_constant__ DevPlan P0, const float2 *__restric
     //    F_k = sum_{m = k mod n} Delta_m e^{i m phi0} + sum_{m >= 1, -m = k mod n} conj(...)
     SHT_CHECK(P.dbg, r >= 0 && r < P.nrings && b0 + gn <= nmaps, 203);
     SHT_CHECK(P.dbg, !(M + 1 <= cap) || (size_t)G * (M + 1) <= (size_t)G * capP, 204);
-    const C *D = delta + (size_t)r * (M + 1) * nmaps + b0;  // D[m nmaps + g]
+    const C *D = delta + (size_t)r * (P.mmax + 1) * nmaps + b0;  // D[m nmaps + g]
     const bool staged = M + 1 <= cap;
     const int n2 = 2 * n;
     // Phase indices (m ps) mod 2n advance incrementally: bin k starts at k ps, the

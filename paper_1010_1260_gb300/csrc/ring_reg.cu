@@ -326,7 +326,7 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
         if (A.use_tma) {
             if (tid == 0 && u < A.nunits) {
                 const Unit U = unit_of(u);
-                const int M1 = U.P->mmax + 1;
+                const int M1 = ring_mtop(*U.P, U.r) + 1;  // orders past it are never read
                 const int nbox = (M1 + kBoxRows - 1) / kBoxRows;
                 SHT_CHECK(U.P->dbg, nbox * kBoxRows <= A.slot_rows && U.b0 % 2 == 0 && U.b0 + 2 <= U.nmaps, 308);
                 const uint32_t b = smem_u32(&bar[s]);
@@ -345,10 +345,11 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
             if (u < A.nunits) {
                 const Unit U = unit_of(u);
                 const int M = U.P->mmax;
+                const int Mr = ring_mtop(*U.P, U.r);  // orders past it are never read
                 const float2 *src = U.delta + (size_t)U.r * (M + 1) * U.nmaps + U.b0;
                 const bool v16 = U.gn == 2 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (U.nmaps % 2 == 0);
                 SHT_CHECK(U.P->dbg, M < A.slot_rows, 309);
-                for (int m = tid; m <= M; m += kRT) {
+                for (int m = tid; m <= Mr; m += kRT) {
                     const float2 *sm = src + (size_t)m * U.nmaps;
                     float2 *d = reinterpret_cast<float2 *>(dst + m);
                     if (v16) {
@@ -397,7 +398,7 @@ ring_reg_kernel(const __grid_constant__ DevPlan P0, const __grid_constant__ RegA
         const DevPlan &P = *U.P;
         const int r = U.r;
         const int n = P.nphi[r];
-        const int M = P.mmax;
+        const int M = ring_mtop(P, r);  // Delta_m is zero past it
         const int N = n >> 1;
         const int Lc = P.rf_len[r];
         const bool blue = Lc < 0;

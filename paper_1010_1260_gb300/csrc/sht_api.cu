@@ -60,6 +60,9 @@ struct sht_plan_s {
     int *sched = nullptr;         // the tensor-core work lists (DevPlan::sched_off, sched_items)
     int sched_skip = -1;          // skip setting the lists were built for (-1: none yet)
     bool sched_off = false;       // test hook: round robin instead of the lists
+    std::vector<int> blim_h;      // per ring block: 1 + largest order with a nonzero Delta (skip tables)
+    std::vector<int> ring_mlim_h;   // per ring: the same (host copy of DevPlan::ring_mlim)
+    std::vector<int2> pair_ring_h;  // (northern ring, southern ring or -1) per pair (host copy)
     std::vector<double> wring_h;  // pixel quadrature weight per ring (host copy)
     double *wring_d = nullptr;    // the same on the device (DevPlan::wring)
     // host-buffer pipeline (sht_alm2map_host): two device buffer sets, two copy
@@ -648,6 +651,7 @@ int build_tables(sht_plan_s *p, const Rings &R)
     int rc;
     if ((rc = upload(p, px, &d.pair_x))) return rc;
     if ((rc = upload(p, pr, &d.pair_ring))) return rc;
+    p->pair_ring_h = pr;
     if ((rc = upload(p, sv, &d.start_v))) return rc;
     if ((rc = upload(p, sk, &d.start_k))) return rc;
     if ((rc = upload(p, cA, &d.coefA))) return rc;
@@ -862,12 +866,22 @@ int ensure_sched(sht_plan_s *p, cudaStream_t st)
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "work lists");
     }
-    std::vector<long long> cost((size_t)nitems);
-    for (int j = 0; j < nitems; ++j) cost[j] = (p->lmax - j / nrb + 1 - 64LL * g0[j]) + kItemOverhead;
-    std::vector<int> host((size_t)G + 1 + nitems, 0);
-    build_work_lists(nitems, cost.data(), G, host.data(), host.data() + G + 1);
+    // items past every ring of their block (Delta exactly zero there) are left out
+    const bool cut = d.skip_g && d.ring_mlim && (int)p->blim_h.size() == nrb;
+    std::vector<int> keep;
+    std::vector<long long> cost;
+    for (int j = 0; j < nitems; ++j) {
+        if (cut && j / nrb >= p->blim_h[j % nrb]) continue;
+        keep.push_back(j);
+        cost.push_back((p->lmax - j / nrb + 1 - 64LL * g0[j]) + kItemOverhead);
+    }
+    const int nkept = (int)keep.size();
+    std::vector<int> host((size_t)G + 1 + nkept, 0);
+    build_work_lists(nkept, cost.data(), G, host.data(), host.data() + G + 1);
+    for (int j = 0; j < nkept; ++j) host[G + 1 + j] = keep[host[G + 1 + j]];
     if (!p->sched) {
-        e = cudaMalloc(&p->sched, host.size() * sizeof(int));
+        // sized for every item: the lists of the other skip setting reuse it
+        e = cudaMalloc(&p->sched, ((size_t)G + 1 + nitems) * sizeof(int));
         if (e != cudaSuccess) {
             p->sched = nullptr;
             cudaGetLastError();
@@ -886,7 +900,9 @@ int ensure_sched(sht_plan_s *p, cudaStream_t st)
 
 // Evanescent-skip tables of the tensor-core forms: built on first use (one
 // FP64 pass over the recurrence, synchronous), or detached when disabled; then
-// the work lists for that setting.
+// the work lists for that setting.  The same pass gives each ring the orders
+// at which its Delta can be nonzero (DevPlan::ring_mlim) and each ring block
+// the largest of them (blim_h), past which the block's items are left out.
 int ensure_warm(sht_plan_s *p, cudaStream_t st)
 {
     sht::DevPlan &d = p->dp;
@@ -894,14 +910,20 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
         d.skip_g = nullptr;
         d.warm_p0 = d.warm_p1 = nullptr;
         d.warm_k = nullptr;
+        d.ring_mlim = nullptr;
         return ensure_sched(p, st);
     }
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t nrb = (size_t)((p->npairs + 127) / 128), M1 = (size_t)p->mmax + 1;
     const size_t nst = M1 * (size_t)p->npairs;
-    const size_t b_g = (M1 * nrb * sizeof(int) + 255) / 256 * 256;
+    const size_t b_g = up(M1 * nrb * sizeof(int));
     const size_t b_p = nst * sizeof(double);
+    const size_t o_k = b_g + 2 * b_p;
+    const size_t o_lim = o_k + up(nst * sizeof(int));
+    const size_t o_rl = o_lim + up((size_t)p->npairs * sizeof(int));
+    const size_t total = o_rl + (size_t)p->nrings * sizeof(int);
     if (!p->warm) {
-        cudaError_t e = cudaMalloc(&p->warm, b_g + 2 * b_p + nst * sizeof(int));
+        cudaError_t e = cudaMalloc(&p->warm, total);
         if (e != cudaSuccess) {
             p->warm = nullptr;
             cudaGetLastError();
@@ -910,16 +932,37 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
         char *b = static_cast<char *>(p->warm);
         int *g = reinterpret_cast<int *>(b);
         double *w0 = reinterpret_cast<double *>(b + b_g), *w1 = reinterpret_cast<double *>(b + b_g + b_p);
-        int *wk = reinterpret_cast<int *>(b + b_g + 2 * b_p);
+        int *wk = reinterpret_cast<int *>(b + o_k);
+        int *plim = reinterpret_cast<int *>(b + o_lim);
         d.skip_g = nullptr;  // the build itself starts every item at degree m
-        e = sht::launch_warm_start(d, g, w0, w1, wk, st);
+        d.ring_mlim = nullptr;
+        e = cudaMemsetAsync(plim, 0, (size_t)p->npairs * sizeof(int), st);
+        if (e == cudaSuccess) e = sht::launch_warm_start(d, g, w0, w1, wk, plim, st);
         if (e == cudaSuccess) {
             g_launches.fetch_add(1, std::memory_order_relaxed);
             e = cudaStreamSynchronize(st);
         }
+        // per ring: its pair's limit; per ring block: the largest over its pairs
+        std::vector<int> pl((size_t)p->npairs), rl((size_t)p->nrings, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pl.data(), plim, pl.size() * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            p->blim_h.assign(nrb, 1);
+            for (int q = 0; q < p->npairs; ++q) {
+                const int lim = std::min(std::max(pl[q], 1), p->mmax + 1);
+                const int2 rr = p->pair_ring_h[q];
+                rl[rr.x] = lim;
+                if (rr.y >= 0) rl[rr.y] = lim;
+                int &bl = p->blim_h[q / 128];
+                bl = std::max(bl, lim);
+            }
+            e = cudaMemcpy(b + o_rl, rl.data(), rl.size() * sizeof(int), cudaMemcpyHostToDevice);
+            p->ring_mlim_h = rl;
+        }
         if (e != cudaSuccess) {
             cudaFree(p->warm);
             p->warm = nullptr;
+            p->blim_h.clear();
             return cuda_fail(e, "warm_start");
         }
     }
@@ -927,7 +970,8 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
     d.skip_g = reinterpret_cast<const int *>(b);
     d.warm_p0 = reinterpret_cast<const double *>(b + b_g);
     d.warm_p1 = reinterpret_cast<const double *>(b + b_g + b_p);
-    d.warm_k = reinterpret_cast<const int *>(b + b_g + 2 * b_p);
+    d.warm_k = reinterpret_cast<const int *>(b + o_k);
+    d.ring_mlim = reinterpret_cast<const int *>(b + o_rl);
     return ensure_sched(p, st);
 }
 
@@ -1386,6 +1430,33 @@ int sht_debug_ring_kernel(sht_plan_t p, int mode)
     p->rf_mode = mode;
     apply_rf_mode(p);
     return SHT_OK;
+}
+
+int sht_order_limits(sht_plan_t p, int *out)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!out) return fail(SHT_EINVAL, "null output array");
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    if (p->skip_evanescent && (rc = ensure_warm(p, nullptr))) return rc;
+    for (int r = 0; r < p->nrings; ++r)
+        out[r] = p->skip_evanescent && !p->ring_mlim_h.empty() ? p->ring_mlim_h[r] : p->mmax + 1;
+    return SHT_OK;
+}
+
+int sht_debug_poison_delta(sht_plan_t p)
+{
+    g_err.clear();
+    int rc = check_plan(p);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard dg(p->device);
+    if (!p->ws) return SHT_OK;
+    cudaError_t e = cudaMemset(p->ws, 0xFF, p->ws_bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? SHT_OK : cuda_fail(e, "poison");
 }
 
 int sht_debug_withhold_stage(sht_plan_t p, int stage)
@@ -2166,8 +2237,11 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
             }
             dp[i] = p->dp;
             const int nrb = (p->npairs + 127) / 128;
+            // items past every ring of their block (Delta exactly zero there) are left out
+            const bool cut = p->dp.ring_mlim && (int)p->blim_h.size() == nrb;
             for (int m = 0; m <= p->mmax; ++m)
                 for (int rb = 0; rb < nrb; ++rb) {
+                    if (cut && m >= p->blim_h[rb]) continue;
                     const long long rows = std::min(128, p->npairs - rb * 128);
                     items.push_back({(long long)(p->lmax - m + 1) * rows, make_int4(i, m, rb, 0)});
                 }
@@ -2224,6 +2298,23 @@ extern "C" int sht_multi_destroy(sht_multi_t q)
 {
     free_multi(q);
     return SHT_OK;
+}
+
+extern "C" int sht_multi_debug_poison_delta(sht_multi_t q)
+{
+    g_err.clear();
+    if (!q) return fail(SHT_EINVAL, "null multi context");
+    DeviceGuard dg(q->device);
+    size_t bytes = 0;
+    if (!q->d_delta) return SHT_OK;
+    for (int i = 0; i < (int)q->plans.size(); ++i) {
+        const sht_plan_s *p = q->plans[i];
+        const size_t el = q->prec == SHT_FP64 ? sizeof(double2) : sizeof(float2);
+        bytes = std::max(bytes, q->delta_ofs[i] + (size_t)p->nrings * (p->mmax + 1) * el);
+    }
+    cudaError_t e = cudaMemset(q->d_delta, 0xFF, bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? SHT_OK : cuda_fail(e, "poison");
 }
 
 extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void *const *map_dev, void *stream)

@@ -72,6 +72,13 @@ struct DevPlan {
     const int *skip_g;
     const double *warm_p0, *warm_p1;
     const int *warm_k;
+    // Orders of the tensor-core forms' Delta that can be nonzero (nullptr: all,
+    // set with the skip tables): Delta_m of ring r is exactly zero for
+    // m >= ring_mlim[r], because every recurrence value of the ring's pair at
+    // those orders rounds to zero in FP32.  The Legendre launches leave out the
+    // items whose order is past every ring of their block, so those Delta
+    // entries are never written, and the FP32 ring kernels read m < ring_mlim[r].
+    const int *ring_mlim;
     // Work lists of the persistent tensor-core launches (sched_ctas == 0:
     // round robin): CTA b of sched_ctas runs items sched_items[sched_off[b] ..
     // sched_off[b + 1]), item = m nrb + rb.  The lists replay a work queue
@@ -121,6 +128,11 @@ struct DevPlan {
     int delta_rows;
     unsigned long long *dbg;  // debug words of the index checks (nullptr unless built with SHT_DEBUG)
 };
+// Largest order of ring r whose FP32 Delta can be nonzero (DevPlan::ring_mlim).
+__device__ __forceinline__ int ring_mtop(const DevPlan &P, int r)
+{
+    return P.ring_mlim ? min(P.mmax, P.ring_mlim[r] - 1) : P.mmax;
+}
 constexpr int kBlueMinPrime = 29;  // a prime factor at least this large selects Bluestein
 constexpr int kBlueMaxMb = 4096;   // largest Bluestein FFT length (shared-memory bound)
 
@@ -241,9 +253,11 @@ cudaError_t launch_ring_synth_mf_multi(const DevPlan *plans_dev, const int2 *smo
                                        int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
                                        const MultiTcPtrs &mp, cudaStream_t st);
 size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
-// Fill the evanescent-skip tables (skip_g: [mmax+1][nrb]; warm_*: [mmax+1][npairs]).
+// Fill the evanescent-skip tables (skip_g: [mmax+1][nrb]; warm_*: [mmax+1][npairs])
+// and raise pair_lim[pair] (zeroed by the caller) to 1 + the largest order with
+// a recurrence value of the pair representable in FP32.
 cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,
-                              cudaStream_t st);
+                              int *pair_lim, cudaStream_t st);
 cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, void *out, cudaStream_t st);
 
 // FP32 ring step of the tensor-core forms with the FFT in registers, over the

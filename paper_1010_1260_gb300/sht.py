@@ -92,6 +92,9 @@ def lib():
             L.sht_skip_evanescent.argtypes = [P, I]
             L.sht_debug_work_lists.argtypes = [P, I]
             L.sht_debug_ring_kernel.argtypes = [P, I]
+            L.sht_debug_poison_delta.argtypes = [P]
+            L.sht_order_limits.argtypes = [P, ctypes.POINTER(I)]
+            L.sht_multi_debug_poison_delta.argtypes = [P]
             L.sht_alm2map_host.argtypes = [P, I, I, PP, PP, I, V]
             IP = ctypes.POINTER(I)
             L.sht_partition.argtypes = [I, I, I, IP, I, IP, IP]
@@ -116,7 +119,8 @@ def lib():
                       "sht_map2alm_batch", "sht_set_ring_weights", "sht_ring_weights", "sht_skip_evanescent",
                       "sht_work_lists", "sht_debug_work_lists", "sht_debug_ring_kernel",
                       "sht_alm2map_host", "sht_partition", "sht_ring_lengths", "sht_alm2map_mpart",
-                      "sht_ring_synth_part", "sht_debug_report", "sht_alm2map_spin2"):
+                      "sht_ring_synth_part", "sht_debug_report", "sht_alm2map_spin2", "sht_debug_poison_delta",
+                      "sht_multi_debug_poison_delta", "sht_order_limits"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -429,6 +433,16 @@ class Plan:
         register-FFT kernel for every ring it can run)."""
         check(lib().sht_debug_ring_kernel(self._h, int(mode)))
 
+    def debug_poison_delta(self):
+        """Test hook: fill the plan's Delta workspace with NaN bytes (synchronises)."""
+        check(lib().sht_debug_poison_delta(self._h))
+
+    def order_limits(self) -> np.ndarray:
+        """Per ring, 1 + the largest order whose FP32 Delta can be nonzero."""
+        out = np.zeros(self.nrings, dtype=np.int32)
+        check(lib().sht_order_limits(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return out
+
     # ---------------------------------------------------------- analysis --
     def map2alm(self, maps: torch.Tensor, niter: int = 0, out: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
@@ -533,6 +547,10 @@ class Multi:
             self.close()
         except Exception:
             pass
+
+    def debug_poison_delta(self):
+        """Test hook: fill the context's Delta workspace with NaN bytes (synchronises)."""
+        check(lib().sht_multi_debug_poison_delta(self._h))
 
     def outputs(self, device=None):
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
