@@ -554,6 +554,13 @@ def run_ours(args):
           for k, v in stages.items() if v[1] and k in ("legendre", "ring")}
     dom = max(rl, key=lambda k: stages[k][0]) if rl else None
     roof = rl.get(dom)
+    if "ring" in rl and args.prec != "fp64":
+        # the FP32 ring kernels read only the orders below each ring's limit
+        # (Delta is exactly zero past it); the algorithmic count keeps every order
+        lim = plan.order_limits()
+        kept = float(lim.astype(np.float64).sum()) / (lim.size * (L + 1))
+        rl["ring"]["delta_orders_read"] = kept
+        rl["ring"]["bytes_read_by_kernels"] = int(B * (lim.astype(np.int64).sum() * 8 + 12 * args.nside ** 2 * 4))
     if cached is not None:
         cst = cached["stages_ms_per_step"]
         cached["roofline"] = {k: stage_roofline(k, cst[k], args, R, cached["lambda_bytes"])
