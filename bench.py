@@ -640,8 +640,10 @@ def measure_requests(args, rank, world, steps, warmup):
 
 def measure_differentiation(args, plan, steps):
     """The differentiation form: B = 16 maps at the headline's grid and band
-    limit, loss = sum_p w_p (s_p - d_p)^2 through the autograd op, forward in
-    the headline's form (and in FP64), backward through the FP64 transpose."""
+    limit, loss = sum_p w_p (s_p - d_p)^2 through the autograd op: forward in
+    FP64 and in the headline's form with the FP64 transpose as backward, and
+    (BF16 forms) forward from the plan-time Lambda operand with the tensor-core
+    transpose of the same form as backward."""
     import torch
     from paper_1010_1260_gb300 import autograd, inputs
     B = 16
@@ -652,7 +654,18 @@ def measure_differentiation(args, plan, steps):
     d = torch.from_numpy(d).to(dev)
     stream = torch.cuda.current_stream()
     out = {"maps": B, "loss": "sum_p w_p (s_p - d_p)^2, w ~ U(0.5, 1.5), d ~ N(0, 1), seed 5"}
-    for fwd in sorted({args.prec, "fp64"}):
+    had_cache = args.prec in plan.lambda_cached
+    variants = [("fp64", False)]
+    if args.prec != "fp64" and not had_cache:
+        variants.append((args.prec, False))
+    if args.prec in ("bf16x6_tc", "bf16x3_tc"):
+        variants.append((args.prec, True))
+    for fwd, cached in variants:
+        if cached and not had_cache:
+            t0 = time.perf_counter()
+            plan.lambda_cache(fwd)
+            out["lambda_build_s"] = time.perf_counter() - t0
+
         def step():
             a = a0.clone().requires_grad_(True)
             s = autograd.alm2map(a, plan, fwd)
@@ -668,8 +681,14 @@ def measure_differentiation(args, plan, steps):
             ev[k + 1].record(stream)
         torch.cuda.synchronize()
         ms = statistics.median([ev[k].elapsed_time(ev[k + 1]) for k in range(steps)])
-        out["forward_" + fwd] = {"ms_forward_backward": ms, "maps_per_s": B / (ms * 1e-3), "steps": steps,
-                                 "backward": "fp64 transpose (ring analysis + Legendre accumulation)"}
+        tc_bwd = fwd in ("bf16x6_tc", "bf16x3_tc") and fwd in plan.lambda_cached
+        key = "forward_" + fwd + ("_cached_tc_backward" if cached else "")
+        out[key] = {"ms_forward_backward": ms, "maps_per_s": B / (ms * 1e-3), "steps": steps,
+                    "backward": ("%s tensor-core transpose (FP32 ring analysis + contraction over ring pairs "
+                                 "from the Lambda operand)" % fwd) if tc_bwd else
+                    "fp64 transpose (ring analysis + Legendre accumulation)"}
+        if cached and not had_cache:
+            plan.lambda_cache(fwd, False)
     del a0, w, d
     torch.cuda.empty_cache()
     return out

@@ -108,7 +108,17 @@ int sht_alm2map(sht_plan_t plan, const void *alm_dev, void *map_dev, int prec, v
  *   g_lm = c_m sum_p y_p lambda_lm(theta_p) e^{-i m phi_p},  c_0 = 1, c_m = 2 (m > 0),
  *   Im g_l0 = 0, so that <alm2map(a), y> = sum Re(a) Re(g) + Im(a) Im(g).
  * map_dev: npix reals (float64; float32 for the tensor-core forms); alm_dev:
- * nalm complex128, fully overwritten. */
+ * nalm complex128, fully overwritten.
+ * prec SHT_FP64: FP64 ring analysis and Legendre accumulation.
+ * prec SHT_BF16X6_TC / SHT_BF16X3_TC: FP32 ring analysis, then the Legendre
+ * step on the tensor cores as per-m GEMMs over the ring pairs, reading the
+ * plan-time Lambda operand of that form transposed; it must have been built
+ * (sht_lambda_cache), else SHT_EUNSUPPORTED.  Accuracy as the forward of the
+ * form (relative L2 per map about 5e-7 for BF16X6).  The first call
+ * allocates the plan's transpose workspace (FP32 ring analysis and operand
+ * image of 32 maps: about 5 GB at lmax 2048 on a 4095-ring grid).
+ * prec SHT_FP32_TC: SHT_EUNSUPPORTED (its operand would need TF32 operands
+ * read MN-major; not built). */
 int sht_map2alm_adjoint(sht_plan_t plan, const void *map_dev, void *alm_dev, int prec, void *stream);
 
 /* Quadrature-weighted analysis, map2alm (Eq. map2almDef with the integral's
@@ -121,10 +131,14 @@ int sht_map2alm_adjoint(sht_plan_t plan, const void *map_dev, void *alm_dev, int
  * none on a RINGS grid until sht_set_ring_weights.  niter >= 0 Jacobi
  * refinements a += map2alm(y - alm2map(a)) follow (the usual HEALPix
  * iteration); they allocate two temporary buffers (nbatch maps, nbatch
- * coefficient sets) and synchronise `stream` at the end.  FP64 only (prec =
- * SHT_FP64, else SHT_EUNSUPPORTED).  map_dev: nbatch x npix float64;
+ * coefficient sets) and synchronise `stream` at the end; they are built for
+ * SHT_FP64 only.  prec SHT_BF16X6_TC / SHT_BF16X3_TC (niter = 0): the
+ * tensor-core transpose of sht_map2alm_adjoint with the ring weights and
+ * c_m = 1 (float32 maps; needs the plan-time Lambda operand of that form).
+ * map_dev: nbatch x npix float64 (float32 for the tensor-core forms);
  * alm_dev: nbatch x nalm complex128, fully overwritten.  Errors: SHT_EINVAL,
- * SHT_EUNSUPPORTED (no weights, or a precision form), SHT_ENOMEM, SHT_ECUDA. */
+ * SHT_EUNSUPPORTED (no weights, SHT_FP32_TC, niter > 0 in a tensor-core form,
+ * no Lambda operand), SHT_ENOMEM, SHT_ECUDA. */
 int sht_map2alm(sht_plan_t plan, const void *map_dev, void *alm_dev, int prec, int niter, void *stream);
 int sht_map2alm_batch(sht_plan_t plan, int nbatch, const void *map_dev, void *alm_dev, int prec, int niter,
                       void *stream);

@@ -1422,6 +1422,348 @@ cudaError_t run_main(const DevPlan &P, const TcWork &W, const void *acache, floa
                              nmaps, st);
 }
 
+// ------------------------------------------------ tensor-core transpose --
+// Legendre step of the transpose (map2alm_adjoint, Eq. DeltaDef transposed),
+// BF16 forms, from the plan-time Lambda operand:
+//     g_lm = c_m C_l sum_pairs p_l(x) (q_N + (-1)^{l-m} q_S)(m),  c_0 = 1, c_m = cfac,
+// i.e. per order m two GEMMs whose K axis is the ring pairs:
+//     E[l, c] = sum_pairs p_l(x) Q+[pair, c]  (l - m even),  O likewise with Q-,
+//     Q+- = q_N +- q_S  (columns c = 2 map + {re, im}).
+// The cached tile of (m, ring block, stage) holds p_l for 128 pairs (rows of
+// 32 bytes) x 16 degrees of one parity (K-major for the forward product).  A
+// 1 KB slice of it (32 pairs) is exactly the MN-major 32-byte-swizzle layout
+// of the transposed operand (M = degrees, K = pairs): 8 K rows of 32 bytes per
+// 256-byte atom, atoms along K 256 bytes apart (stride byte offset), the next
+// 16 degrees in the next stage's slice (leading byte offset 1 KB).  So the
+// tensor core reads the forward's operand transposed, with no data movement
+// other than the bulk copies of the slices.
+constexpr int kAdjStages = 8;                 // stages per block of 128 degrees of one parity
+constexpr int kAdjPairs = 32;                 // ring pairs per K chunk (two MMA K steps)
+constexpr int kAdjSlice = kAdjPairs * kRowBytes;  // 1 KB
+constexpr int kAdjWarps = 10;                 // 0-7 drain, 8 loads + tensor memory, 9 MMA
+
+template <int NPA, int NPB>
+struct AdjCfg {
+    static constexpr int NS = 3;                                       // chunks in flight
+    static constexpr int A_BYTES = 2 * NPA * kAdjStages * kAdjSlice;  // [par][piece][stage] slices
+    static constexpr int B_MAX = 2 * NPB * 2 * 64 * kRowBytes;         // [par][piece][ksub] x N <= 64 rows
+    static constexpr int STAGE_BYTES = A_BYTES + B_MAX;
+    static constexpr int NPROD = (NPA == 2 && NPB == 2) ? 3 : 6;
+    static constexpr int SMEM = NS * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
+};
+
+// MN-major operand with the 32-byte swizzle: leading byte offset = stride of
+// the 32-byte column blocks along M, stride byte offset = stride of the
+// 8-row groups along K (descriptor version 1).
+__device__ __forceinline__ uint64_t sdesc_sw32_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+
+// Operand image of the transpose: for every (m, chunk c of 32 pairs) a block
+// of 2 x NPB x 2 tiles ([parity][piece][ksub], N rows of 32 bytes each, row n
+// = 2 map + {re, im} holding 16 pairs, 16-byte halves swizzled by bit 2 of
+// the row) of the pieces of Q+ (parity 0) and Q- (parity 1).  q is the FP32
+// ring analysis [map][ring][m].  One thread per (m, map b < N / 2, c), m
+// fastest so that the reads of q are coalesced; maps b >= nmaps and pairs past
+// the last are zero.
+template <int NPB>
+__global__ void __launch_bounds__(256)
+adj_prep_kernel(const DevPlan P, const float2 *__restrict__ q, unsigned char *__restrict__ bout, int nmaps, int ncol)
+{
+    const int M1 = P.mmax + 1;
+    const int nch = (P.npairs + kAdjPairs - 1) / kAdjPairs;
+    const int nb2 = ncol >> 1;
+    const int c = blockIdx.y;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M1 * nb2) return;
+    const int m = idx % M1, b = idx / M1;
+    const size_t blk = (size_t)2 * NPB * 2 * ncol * kRowBytes;
+    unsigned char *out = bout + ((size_t)m * nch + c) * blk;
+    const float2 *qb = q + (size_t)b * P.nrings * M1 + m;
+#pragma unroll 1
+    for (int ks = 0; ks < 2; ++ks) {
+        float2 e[16], o[16];
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const int pair = c * kAdjPairs + 16 * ks + kk;
+            float2 vn = make_float2(0.f, 0.f), vs = make_float2(0.f, 0.f);
+            if (pair < P.npairs && b < nmaps) {
+                const int2 rr = P.pair_ring[pair];
+                vn = qb[(size_t)rr.x * M1];
+                if (rr.y >= 0) vs = qb[(size_t)rr.y * M1];
+            }
+            e[kk] = make_float2(vn.x + vs.x, vn.y + vs.y);
+            o[kk] = make_float2(vn.x - vs.x, vn.y - vs.y);
+        }
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+#pragma unroll
+            for (int col = 0; col < 2; ++col) {
+                const int n = 2 * b + col;
+                uint32_t w[NPB][8];
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) {
+                    const float2 v = par ? o[kk] : e[kk];
+                    uint32_t pc[NPB];
+                    split_pieces<true, NPB>(col ? v.y : v.x, pc);
+#pragma unroll
+                    for (int pq = 0; pq < NPB; ++pq) {
+                        if (kk & 1)
+                            w[pq][kk >> 1] |= pc[pq] & 0xFFFF0000u;
+                        else
+                            w[pq][kk >> 1] = pc[pq] >> 16;
+                    }
+                }
+                const int sw = (n >> 2) & 1;
+#pragma unroll
+                for (int pq = 0; pq < NPB; ++pq) {
+                    unsigned char *row = out + ((size_t)((par * NPB + pq) * 2 + ks) * ncol + n) * kRowBytes;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        *reinterpret_cast<uint4 *>(row + ((h ^ sw) << 4)) =
+                            make_uint4(w[pq][4 * h], w[pq][4 * h + 1], w[pq][4 * h + 2], w[pq][4 * h + 3]);
+                }
+            }
+        }
+    }
+}
+
+// One CTA per item (m, block j of 128 degrees of each parity), items by
+// increasing m; the K loop runs over the chunks of 32 ring pairs:
+//   warps 0-7  drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 32
+//              (rows = degrees) of E (w < 4) or O; after every chunk it adds
+//              the finished accumulator into its register totals (FP32, round
+//              to nearest: the tensor core's truncating accumulation stays
+//              within 12 MMAs, as in the forward kernels), and at the end
+//              writes g_lm = c C_l (E or O) for its degrees and maps;
+//   warp 8     tensor memory, and the chunk's copies: the block's stage
+//              slices of the cached operand (1 KB each) and the chunk's
+//              block of the transpose operand image, on one mbarrier;
+//   warp 9     the MMAs: per parity, 2 K steps x the piece products, A
+//              MN-major from the slices, B K-major; D alternates between two
+//              accumulator sets per chunk.
+// Chunks without a value in FP32 range are left out: past the order limit of
+// their ring block, or all of the block's degrees before the block's first
+// nonzero stage (evanescent skip).  Slices of stages past the order's last
+// stage are not loaded: the rows they feed are degrees above lmax, which are
+// never written.  Every wait is bounded as in the forward kernels.
+template <int NPA, int NPB>
+__global__ void __launch_bounds__(kAdjWarps * 32, 1)
+legendre_adj_tc_kernel(const DevPlan P, const unsigned char *__restrict__ acache, const int *__restrict__ seg_off,
+                       const unsigned char *__restrict__ bimg, const int2 *__restrict__ items,
+                       double2 *__restrict__ g, int nmaps, int ncol, double cfac, int *__restrict__ status)
+{
+    using A = AdjCfg<NPA, NPB>;
+    constexpr int NS = A::NS;
+    constexpr int STEPS = 32;               // degrees per cached stage (BF16)
+    constexpr int GROUP = 64 / STEPS;       // stages per skip group
+    constexpr size_t SA = (size_t)2 * NPA * kTileBytes;  // one cached stage block
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    const uint32_t pad = (1024u - (base_u32 & 1023u)) & 1023u;
+    unsigned char *stage0 = smem_raw + pad;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + NS * A::STAGE_BYTES);
+    // bars: full[NS], empty[NS], set_full[2], set_empty[2], mma_drain
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int L = P.lmax;
+    const int nrb = (P.npairs + kRows - 1) / kRows;
+    const int nch = (P.npairs + kAdjPairs - 1) / kAdjPairs;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int2 it = items[blockIdx.x];
+    const int m = it.x, j = it.y;
+    const int nst = (L - m + 1 + STEPS - 1) / STEPS;
+    const int i_lo = kAdjStages * j, i_hi = min(nst, i_lo + kAdjStages);  // the block's cached stages
+    const uint32_t sbb = (uint32_t)2 * NPB * 2 * ncol * kRowBytes;       // operand image block per chunk
+    SHT_CHECK(P.dbg, (ncol == 32 || ncol == 64) && i_lo < i_hi && 2 * nmaps <= ncol, 501);
+
+    auto bar_full = [&](int s) { return smem_u32(&bars[s]); };
+    auto bar_empty = [&](int s) { return smem_u32(&bars[NS + s]); };
+    auto bar_set_full = [&](int k) { return smem_u32(&bars[2 * NS + k]); };
+    auto bar_set_empty = [&](int k) { return smem_u32(&bars[2 * NS + 2 + k]); };
+    const uint32_t bar_mma_drain = smem_u32(&bars[2 * NS + 4]);
+    auto a_slice = [&](int s, int par, int piece, int st) {
+        return stage0 + (size_t)s * A::STAGE_BYTES + (size_t)((par * NPA + piece) * kAdjStages + st) * kAdjSlice;
+    };
+    auto b_tile = [&](int s, int par, int piece, int ks) {
+        return stage0 + (size_t)s * A::STAGE_BYTES + A::A_BYTES + (size_t)((par * NPB + piece) * 2 + ks) * ncol * kRowBytes;
+    };
+    // chunk k (pairs 32 k ..) of ring block k / 4 runs iff it has pairs, the
+    // block has a value in FP32 range at this order, and the item's degrees
+    // reach the block's first nonzero stage
+    auto live = [&](int k) {
+        const int rb = k >> 2;
+        if (P.block_mlim && m >= P.block_mlim[rb]) return false;
+        const int s0 = P.skip_g ? P.skip_g[m * nrb + rb] * GROUP : 0;
+        return i_hi > s0;
+    };
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(bar_full(s), 1);
+            mbar_init(bar_empty(s), 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(bar_set_full(k), 1);
+            mbar_init(bar_set_empty(k), 8);
+        }
+        mbar_init(bar_mma_drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(256u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp < 8) {
+        // ----------------------------------------------------------- drain --
+        const int quad = warp & 3;
+        const int half = warp >> 2;  // 0: E (l - m even), 1: O
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        float tot[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) tot[c] = 0.f;
+        uint32_t gg = 0;
+        bool ok = true;
+        for (int k = 0; k < nch && ok; ++k) {
+            if (!live(k)) continue;
+            const int set = (int)(gg & 1u);
+            ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
+            if (!ok) break;
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (32 * h < ncol) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(128 * set + half * ncol + 32 * h), v);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) tot[32 * h + c] += __uint_as_float(v[c]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_set_empty(set));
+            ++gg;
+        }
+        if (ok) {
+            // row r = 16 (stage in the block) + position in the stage's parity
+            const int r = quad * 32 + lane;
+            const int l = m + 2 * (kAdjStages * 16 * j + r) + half;
+            if (l <= L) {
+                const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
+                const double cl = (m == 0 ? 1.0 : cfac) * __ldg(&P.coefC[mofs + (l - m)]);
+                double2 *dst = g + mofs + (l - m);
+#pragma unroll
+                for (int b = 0; b < 32; ++b)
+                    if (b < nmaps)
+                        dst[(size_t)b * P.nalm] =
+                            make_double2(cl * (double)tot[2 * b], m == 0 ? 0.0 : cl * (double)tot[2 * b + 1]);
+            }
+        }
+    } else if (warp == 8) {
+        // ---------------------------------------------------------- loads --
+        if (lane == 0) {
+            const size_t st0 = (size_t)(seg_off[2 * m] / STEPS);  // stages of the orders below m
+            uint32_t gs = 0;
+            bool ok = true;
+            for (int k = 0; k < nch && ok; ++k) {
+                if (!live(k)) continue;
+                const int s = (int)(gs % NS);
+                const uint32_t ph = (gs / NS) & 1u;
+                if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                const int rb = k >> 2, w = k & 3;
+                mbar_expect_tx(bar_full(s), (uint32_t)((i_hi - i_lo) * 2 * NPA * kAdjSlice) + sbb);
+                const unsigned char *ablk = acache + (st0 * nrb + (size_t)rb * nst) * SA;
+                for (int i = i_lo; i < i_hi; ++i)
+#pragma unroll
+                    for (int par = 0; par < 2; ++par)
+#pragma unroll
+                        for (int pc = 0; pc < NPA; ++pc)
+                            bulk_load(smem_u32(a_slice(s, par, pc, i - i_lo)),
+                                      ablk + (size_t)i * SA + (size_t)(par * NPA + pc) * kTileBytes + (size_t)w * kAdjSlice,
+                                      kAdjSlice, bar_full(s));
+                bulk_load(smem_u32(b_tile(s, 0, 0, 0)), bimg + ((size_t)m * nch + k) * sbb, sbb, bar_full(s));
+                ++gs;
+            }
+            if (s_abort) {
+                const uint32_t first = gs > (uint32_t)NS ? gs - NS : 0u;
+                for (uint32_t q = first; q < gs; ++q) mbar_drain(bar_full((int)(q % NS)), (q / NS) & 1u);
+            }
+        }
+    } else {
+        // ----------------------------------------------------------- MMA --
+        if (lane == 0) {
+            const uint32_t id = idesc<true>(ncol) | (1u << 15);  // A MN-major
+            uint32_t gs = 0;
+            bool ok = true, issued = false;
+            for (int k = 0; k < nch && ok; ++k) {
+                if (!live(k)) continue;
+                const int s = (int)(gs % NS);
+                const uint32_t ph = (gs / NS) & 1u;
+                const int set = (int)(gs & 1u);
+                if (!mbar_wait(bar_set_empty(set), ((gs >> 1) & 1u) ^ 1u, &s_abort) ||
+                    !mbar_wait(bar_full(s), ph, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                SHT_CHECK(P.dbg, 128 * set + 2 * ncol <= 256 && s < NS, 502);
+#pragma unroll
+                for (int par = 0; par < 2; ++par) {
+                    const uint32_t d = tmem + (uint32_t)(128 * set + par * ncol);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+                        for (int pr = 0; pr < A::NPROD; ++pr) {
+                            int ia, ib;
+                            product_pieces<NPA, NPB>(pr, ia, ib);
+                            // K step ks: pairs 16 ks .. 16 ks + 15 = two 8-row groups further
+                            const uint64_t ad =
+                                sdesc_sw32_mn(smem_u32(a_slice(s, par, ia, 0)) + 512u * ks, kAdjSlice, 256u);
+                            const uint64_t bd = sdesc_sw32(smem_u32(b_tile(s, par, ib, ks)));
+                            tc_mma<true>(d, ad, bd, id, (ks > 0 || pr > 0) ? 1u : 0u);
+                        }
+                    }
+                }
+                issued = true;
+                tc_commit(bar_empty(s));
+                tc_commit(bar_set_full(set));
+                ++gs;
+            }
+            if (!ok && issued) {
+                tc_commit(bar_mma_drain);
+                mbar_drain(bar_mma_drain, 0u);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u));
+    }
+    if (threadIdx.x == 0 && s_abort) atomicExch(status, SHT_ETIMEOUT);
+}
+
 }  // namespace
 
 cudaError_t launch_tc_main_multi(const DevPlan &P, const DevPlan *plans_dev, const int4 *items, int nitems,
@@ -1449,6 +1791,48 @@ size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec)
     if (prec == SHT_BF16X3_TC) return (size_t)(W.kall_bf16 / 32) * nrb * 2 * 2 * kTileBytes;
     if (prec == SHT_BF16X6_TC) return (size_t)(W.kall_bf16 / 32) * nrb * 2 * 3 * kTileBytes;
     return 0;
+}
+
+size_t adj_tc_bimg_bytes(const DevPlan &P, int prec, int nmaps)
+{
+    const int npb = prec == SHT_BF16X6_TC ? 3 : 2;
+    const int ncol = nmaps <= 16 ? 32 : 64;
+    const size_t nch = (size_t)((P.npairs + kAdjPairs - 1) / kAdjPairs);
+    return nch * (size_t)(P.mmax + 1) * 2 * npb * 2 * ncol * kRowBytes;
+}
+
+cudaError_t launch_adj_tc(const DevPlan &P, const TcWork &W, int prec, const void *acache, const float2 *q,
+                          void *bimg, const int2 *items, int nitems, double2 *g, int nmaps, double cfac,
+                          cudaStream_t st)
+{
+    if (nmaps <= 0 || nitems <= 0) return cudaSuccess;
+    if (nmaps > 32 || (prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)) return cudaErrorInvalidValue;
+    const int ncol = nmaps <= 16 ? 32 : 64;
+    const int nch = (P.npairs + kAdjPairs - 1) / kAdjPairs;
+    dim3 pg(((P.mmax + 1) * (ncol >> 1) + 255) / 256, nch);
+    unsigned char *bo = static_cast<unsigned char *>(bimg);
+    const unsigned char *ac = static_cast<const unsigned char *>(acache);
+    cudaError_t e;
+    if (prec == SHT_BF16X6_TC) {
+        adj_prep_kernel<3><<<pg, 256, 0, st>>>(P, q, bo, nmaps, ncol);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        auto kern = legendre_adj_tc_kernel<3, 3>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjCfg<3, 3>::SMEM)) !=
+            cudaSuccess)
+            return e;
+        kern<<<nitems, kAdjWarps * 32, AdjCfg<3, 3>::SMEM, st>>>(P, ac, W.seg_bf16, bo, items, g, nmaps, ncol, cfac,
+                                                                   W.status);
+    } else {
+        adj_prep_kernel<2><<<pg, 256, 0, st>>>(P, q, bo, nmaps, ncol);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        auto kern = legendre_adj_tc_kernel<2, 2>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjCfg<2, 2>::SMEM)) !=
+            cudaSuccess)
+            return e;
+        kern<<<nitems, kAdjWarps * 32, AdjCfg<2, 2>::SMEM, st>>>(P, ac, W.seg_bf16, bo, items, g, nmaps, ncol, cfac,
+                                                                   W.status);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,

@@ -1080,5 +1080,12 @@ cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, doubl
                       map, q, wring);
 }
 
+cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
+                                      const double *wring, cudaStream_t st)
+{
+    return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, 0, st,
+                      map, q, wring);
+}
+
 
 }  // namespace sht

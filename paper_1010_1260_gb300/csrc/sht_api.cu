@@ -75,6 +75,12 @@ struct sht_plan_s {
     // sht_ring_synth_part), grown on demand
     void *part_buf = nullptr;
     size_t part_bytes = 0;
+    // tensor-core transpose (BF16 forms): FP32 ring analysis + operand image
+    // workspace, and the (m, degree block) items, built on first use
+    void *adj_ws = nullptr;
+    size_t adj_bytes = 0;
+    int2 *adj_items = nullptr;
+    int adj_nitems = 0;
     size_t lcache_bytes[4] = {};
     std::mutex mu;
 };
@@ -256,6 +262,8 @@ void free_plan(sht_plan_s *p)
         if (p->warm) cudaFree(p->warm);
         if (p->hp_buf) cudaFree(p->hp_buf);
         if (p->part_buf) cudaFree(p->part_buf);
+        if (p->adj_ws) cudaFree(p->adj_ws);
+        if (p->adj_items) cudaFree(p->adj_items);
         if (p->hp_up) cudaStreamDestroy(p->hp_up);
         if (p->hp_down) cudaStreamDestroy(p->hp_down);
         for (auto e : p->hp_ev)
@@ -911,6 +919,7 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
         d.warm_p0 = d.warm_p1 = nullptr;
         d.warm_k = nullptr;
         d.ring_mlim = nullptr;
+        d.block_mlim = nullptr;
         return ensure_sched(p, st);
     }
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -921,7 +930,8 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
     const size_t o_k = b_g + 2 * b_p;
     const size_t o_lim = o_k + up(nst * sizeof(int));
     const size_t o_rl = o_lim + up((size_t)p->npairs * sizeof(int));
-    const size_t total = o_rl + (size_t)p->nrings * sizeof(int);
+    const size_t o_bl = o_rl + up((size_t)p->nrings * sizeof(int));
+    const size_t total = o_bl + nrb * sizeof(int);
     if (!p->warm) {
         cudaError_t e = cudaMalloc(&p->warm, total);
         if (e != cudaSuccess) {
@@ -936,6 +946,7 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
         int *plim = reinterpret_cast<int *>(b + o_lim);
         d.skip_g = nullptr;  // the build itself starts every item at degree m
         d.ring_mlim = nullptr;
+        d.block_mlim = nullptr;
         e = cudaMemsetAsync(plim, 0, (size_t)p->npairs * sizeof(int), st);
         if (e == cudaSuccess) e = sht::launch_warm_start(d, g, w0, w1, wk, plim, st);
         if (e == cudaSuccess) {
@@ -957,6 +968,8 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
                 bl = std::max(bl, lim);
             }
             e = cudaMemcpy(b + o_rl, rl.data(), rl.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b + o_bl, p->blim_h.data(), p->blim_h.size() * sizeof(int), cudaMemcpyHostToDevice);
             p->ring_mlim_h = rl;
         }
         if (e != cudaSuccess) {
@@ -972,6 +985,7 @@ int ensure_warm(sht_plan_s *p, cudaStream_t st)
     d.warm_p1 = reinterpret_cast<const double *>(b + b_g + b_p);
     d.warm_k = reinterpret_cast<const int *>(b + o_k);
     d.ring_mlim = reinterpret_cast<const int *>(b + o_rl);
+    d.block_mlim = reinterpret_cast<const int *>(b + o_bl);
     return ensure_sched(p, st);
 }
 
@@ -1081,6 +1095,72 @@ int analysis_fp64(sht_plan_s *p, int nbatch, const double *map, double2 *alm, co
         e = sht::launch_legendre_adj_fp64(p->dp, q, alm + (size_t)b0 * p->nalm, nb, cfac, st);
         s2.done(e);
         if (e != cudaSuccess) return cuda_fail(e, "legendre_adj_fp64 launch");
+    }
+    return SHT_OK;
+}
+
+// The transpose in a BF16 tensor-core form (caller holds the plan lock and
+// the device): FP32 ring analysis of groups of up to 32 float maps, then the
+// contraction from the plan-time Lambda operand of that form, which must have
+// been built (sht_lambda_cache).  Weights and cfac as analysis_fp64.
+int analysis_tc(sht_plan_s *p, int nbatch, const float *map, double2 *alm, const double *wring, double cfac,
+                int prec, cudaStream_t st)
+{
+    int rc;
+    if (prec != SHT_BF16X3_TC && prec != SHT_BF16X6_TC)
+        return fail(SHT_EUNSUPPORTED, "the transpose has no tensor-core form for precision %d (BF16 forms only)", prec);
+    if (!p->lcache[prec])
+        return fail(SHT_EUNSUPPORTED,
+                    "the tensor-core transpose reads the plan-time Lambda operand: build it first (sht_lambda_cache)");
+    if ((rc = ensure_tc(p, prec)) || (rc = ensure_warm(p, st))) return rc;
+    constexpr int G = 32;  // maps per contraction launch
+    const size_t qb = (size_t)G * p->nrings * (p->mmax + 1) * sizeof(float2);
+    const size_t need = qb + sht::adj_tc_bimg_bytes(p->dp, prec, G);
+    if (p->adj_bytes < need) {
+        if (p->adj_ws) {
+            cudaStreamSynchronize(st);
+            cudaFree(p->adj_ws);
+        }
+        p->adj_ws = nullptr;
+        p->adj_bytes = 0;
+        cudaError_t e = cudaMalloc(&p->adj_ws, need);
+        if (e != cudaSuccess) {
+            p->adj_ws = nullptr;
+            cudaGetLastError();
+            return fail(SHT_ENOMEM, "transpose workspace: %s", cudaGetErrorString(e));
+        }
+        p->adj_bytes = need;
+    }
+    if (!p->adj_items) {
+        std::vector<int2> it;
+        for (int m = 0; m <= p->mmax; ++m) {
+            const int nst = (p->lmax - m + 1 + 31) / 32;
+            for (int j = 0; j < (nst + 7) / 8; ++j) it.push_back(make_int2(m, j));
+        }
+        cudaError_t e = cudaMalloc(&p->adj_items, it.size() * sizeof(int2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->adj_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (p->adj_items) cudaFree(p->adj_items);
+            p->adj_items = nullptr;
+            cudaGetLastError();
+            return fail(SHT_ENOMEM, "transpose items: %s", cudaGetErrorString(e));
+        }
+        p->adj_nitems = (int)it.size();
+    }
+    float2 *q = static_cast<float2 *>(p->adj_ws);
+    void *bimg = static_cast<char *>(p->adj_ws) + qb;
+    for (int b0 = 0; b0 < nbatch; b0 += G) {
+        const int nb = std::min(G, nbatch - b0);
+        StageScope s1(p, SHT_STAGE_ADJ_RING, st);
+        cudaError_t e = sht::launch_ring_analysis_fp32(p->dp, map + (size_t)b0 * p->npix, q, nb, wring, st);
+        s1.done(e, sht::ring_launches(p->dp));
+        if (e != cudaSuccess) return cuda_fail(e, "ring_analysis_fp32 launch");
+        StageScope s2(p, SHT_STAGE_ADJ_LEGENDRE, st);
+        e = sht::launch_adj_tc(p->dp, p->tc, prec, p->lcache[prec], q, bimg, p->adj_items, p->adj_nitems,
+                               alm + (size_t)b0 * p->nalm, nb, cfac, st);
+        s2.done(e, 2);
+        if (e != cudaSuccess) return cuda_fail(e, "legendre_adj_tc launch");
     }
     return SHT_OK;
 }
@@ -1595,7 +1675,6 @@ int sht_alm2map_host(sht_plan_t p, int nsteps, int nbatch, const void *const *al
         if (p->hp_bytes < need) {
             if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
             if (p->hp_buf) cudaFree(p->hp_buf);
-        if (p->part_buf) cudaFree(p->part_buf);
             p->hp_buf = nullptr;
             p->hp_bytes = 0;
             if ((e = cudaMalloc(&p->hp_buf, need)) != cudaSuccess) {
@@ -1651,7 +1730,12 @@ int sht_map2alm_adjoint_batch(sht_plan_t p, int nbatch, const void *map_dev, voi
         return fail(SHT_EINVAL, "unknown precision %d", prec);
     if (nbatch == 0) return SHT_OK;
     if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
-    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "precision %d not built for the adjoint", prec);
+    if (prec != SHT_FP64) {
+        std::lock_guard<std::mutex> lk(p->mu);
+        DeviceGuard dg(p->device);
+        return analysis_tc(p, nbatch, static_cast<const float *>(map_dev), static_cast<double2 *>(alm_dev), nullptr,
+                           2.0, prec, static_cast<cudaStream_t>(stream));
+    }
     if (sht::legendre_adj_smem_bytes(p->dp, 4) == 0)
         return fail(SHT_EUNSUPPORTED, "adjoint: %d ring pairs exceed the shared-memory state", p->npairs);
     std::lock_guard<std::mutex> lk(p->mu);
@@ -1671,8 +1755,9 @@ int sht_map2alm_batch(sht_plan_t p, int nbatch, const void *map_dev, void *alm_d
         return fail(SHT_EINVAL, "unknown precision %d", prec);
     if (nbatch == 0) return SHT_OK;
     if (!alm_dev || !map_dev) return fail(SHT_EINVAL, "null device pointer");
-    if (prec != SHT_FP64) return fail(SHT_EUNSUPPORTED, "precision %d not built for map2alm", prec);
-    if (sht::legendre_adj_smem_bytes(p->dp, 4) == 0)
+    if (prec != SHT_FP64 && niter > 0)
+        return fail(SHT_EUNSUPPORTED, "map2alm refinement steps (niter > 0) are built for SHT_FP64 only");
+    if (prec == SHT_FP64 && sht::legendre_adj_smem_bytes(p->dp, 4) == 0)
         return fail(SHT_EUNSUPPORTED, "map2alm: %d ring pairs exceed the shared-memory state", p->npairs);
     std::lock_guard<std::mutex> lk(p->mu);
     bool any = false;
@@ -1680,6 +1765,9 @@ int sht_map2alm_batch(sht_plan_t p, int nbatch, const void *map_dev, void *alm_d
     if (!any) return fail(SHT_EUNSUPPORTED, "the grid has no quadrature weights (sht_set_ring_weights)");
     DeviceGuard dg(p->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prec != SHT_FP64)
+        return analysis_tc(p, nbatch, static_cast<const float *>(map_dev), static_cast<double2 *>(alm_dev),
+                           p->wring_d, 1.0, prec, st);
     const double *map = static_cast<const double *>(map_dev);
     double2 *alm = static_cast<double2 *>(alm_dev);
     if ((rc = analysis_fp64(p, nbatch, map, alm, p->wring_d, 1.0, st))) return rc;

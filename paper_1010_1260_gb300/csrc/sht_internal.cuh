@@ -79,6 +79,7 @@ struct DevPlan {
     // items whose order is past every ring of their block, so those Delta
     // entries are never written, and the FP32 ring kernels read m < ring_mlim[r].
     const int *ring_mlim;
+    const int *block_mlim;  // [nrb] the largest ring_mlim of each block of 128 ring pairs
     // Work lists of the persistent tensor-core launches (sched_ctas == 0:
     // round robin): CTA b of sched_ctas runs items sched_items[sched_off[b] ..
     // sched_off[b + 1]), item = m nrb + rb.  The lists replay a work queue
@@ -192,6 +193,9 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
 // Ring step of the transpose: q[b][ring][m] = sum_j y_j e^{-i m phi_j}.
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
                                       const double *wring, cudaStream_t st);
+// The same ring step of the transpose in FP32 (the tensor-core forms' maps).
+cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
+                                      const double *wring, cudaStream_t st);
 // Legendre step of the transpose, FP64:
 //   g[b][idx(l, m)] = c_m sum_r lambda_lm(x_r) q[b][r][m],  c_0 = 1, c_m = cfac for m > 0
 //   (cfac = 2: the real-linear transpose of alm2map; cfac = 1: the analysis sum).
@@ -259,6 +263,17 @@ size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
 cudaError_t launch_warm_start(const DevPlan &P, int *skip_g, double *warm_p0, double *warm_p1, int *warm_k,
                               int *pair_lim, cudaStream_t st);
 cudaError_t launch_lambda_build(const DevPlan &P, const TcWork &W, int prec, void *out, cudaStream_t st);
+// Legendre step of the transpose (map2alm_adjoint), BF16 forms, from the
+// plan-time Lambda operand acache of the same form: g[map][alm] = c_m C_l
+// sum_pairs p_l(x) (q_N + (-1)^{l-m} q_S)(m), c_0 = 1, c_m = cfac, Im g_l0 = 0.  q: FP32 ring
+// analysis [map][ring][m] of nmaps <= 32 maps; bimg: workspace of
+// adj_tc_bimg_bytes(P, prec, nmaps) bytes; items: (m, block j of 128 degrees
+// of each parity) for every m and j < ceil(ceil((lmax - m + 1) / 32) / 8).
+// Two launches (operand image, contraction).
+size_t adj_tc_bimg_bytes(const DevPlan &P, int prec, int nmaps);
+cudaError_t launch_adj_tc(const DevPlan &P, const TcWork &W, int prec, const void *acache, const float2 *q,
+                          void *bimg, const int2 *items, int nitems, double2 *g, int nmaps, double cfac,
+                          cudaStream_t st);
 
 // FP32 ring step of the tensor-core forms with the FFT in registers, over the
 // plan's rf_rings (Delta [ring][m][map] for nmaps maps); status gets

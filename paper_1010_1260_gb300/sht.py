@@ -267,6 +267,7 @@ class Plan:
         self.nalm = int(L.sht_nalm(h))
         self.npix = int(L.sht_npix(h))
         self.nrings = int(L.sht_nrings(h))
+        self.lambda_cached = set()  # tensor-core forms whose plan-time Lambda operand is built
 
     @property
     def handle(self) -> int:
@@ -322,7 +323,9 @@ class Plan:
 
     def map2alm_adjoint(self, maps: torch.Tensor, prec: str = "fp64", out: torch.Tensor | None = None,
                         stream=None) -> torch.Tensor:
-        """Real-linear transpose of alm2map (cuda complex128 result)."""
+        """Real-linear transpose of alm2map (cuda complex128 result).  The BF16
+        tensor-core forms take float32 maps and need the plan-time Lambda
+        operand of that form (lambda_cache)."""
         if not (maps.is_cuda and maps.dtype == MAP_DTYPE[prec]):
             raise TypeError("maps must be a CUDA tensor of dtype %s" % MAP_DTYPE[prec])
         single = maps.dim() == 1
@@ -379,6 +382,10 @@ class Plan:
         later alm2map calls of that form stream it instead of running the
         recurrence, with identical results."""
         check(lib().sht_lambda_cache(self._h, PREC[prec], 1 if enable else 0, _stream_ptr(stream)))
+        if enable:
+            self.lambda_cached.add(prec)
+        else:
+            self.lambda_cached.discard(prec)
 
     # ------------------------------------------------------- tile shapes --
     TILE_NAMES = ("ring_maps_smooth", "ring_maps_bluestein", "ring_threads", "fp64_legendre_maps",
@@ -445,17 +452,19 @@ class Plan:
 
     # ---------------------------------------------------------- analysis --
     def map2alm(self, maps: torch.Tensor, niter: int = 0, out: torch.Tensor | None = None,
-                stream=None) -> torch.Tensor:
-        """Quadrature-weighted analysis of float64 CUDA maps ([B, npix] or
-        [npix]) with ``niter`` Jacobi refinements (complex128 result)."""
-        if not (maps.is_cuda and maps.dtype == torch.float64):
-            raise TypeError("maps must be a CUDA float64 tensor")
+                stream=None, prec: str = "fp64") -> torch.Tensor:
+        """Quadrature-weighted analysis of CUDA maps ([B, npix] or [npix];
+        float64, float32 for the BF16 tensor-core forms, which need the
+        plan-time Lambda operand and niter = 0) with ``niter`` Jacobi
+        refinements (complex128 result)."""
+        if not (maps.is_cuda and maps.dtype == MAP_DTYPE[prec]):
+            raise TypeError("maps must be a CUDA tensor of dtype %s" % MAP_DTYPE[prec])
         single = maps.dim() == 1
         y = maps.reshape(-1, self.npix).contiguous()
         B = y.shape[0]
         if out is None:
             out = torch.empty((B, self.nalm), dtype=torch.complex128, device=maps.device)
-        check(lib().sht_map2alm_batch(self._h, B, y.data_ptr(), out.data_ptr(), PREC["fp64"], int(niter),
+        check(lib().sht_map2alm_batch(self._h, B, y.data_ptr(), out.data_ptr(), PREC[prec], int(niter),
                                       _stream_ptr(stream)))
         return out.reshape(self.nalm) if single else out.reshape(B, self.nalm)
 

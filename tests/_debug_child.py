@@ -52,6 +52,13 @@ def main():
         g_adj = plan.map2alm_adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
         w_adj = oracle.map2alm_adjoint(og, L, L, y)
         res["errors"][name + "/adjoint"] = rl2(g_adj.view(np.float64), w_adj.view(np.float64))
+        # the tensor-core transpose (BF16x6) from the plan-time Lambda operand
+        y32 = y.astype(np.float32)
+        plan.lambda_cache("bf16x6_tc")
+        g_tc = plan.map2alm_adjoint(torch.from_numpy(y32).cuda(), "bf16x6_tc").cpu().numpy()
+        w_tc = oracle.map2alm_adjoint(og, L, L, y32.astype(np.float64))
+        res["errors"][name + "/adjoint_tc/bf16x6_tc"] = rl2(g_tc.view(np.float64), w_tc.view(np.float64))
+        plan.lambda_cache("bf16x6_tc", False)
         # partitioned transform over 3 parts, exchange by device copies
         mo, ro = sht.partition(L, L, plan.ring_lengths(), 3)
         sizes = sht.exchange_sizes(mo, ro, 3, B)
