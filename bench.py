@@ -78,6 +78,8 @@ def parse():
                     help="skip the batching form (256 requests) and the differentiation form (forward + backward) "
                          "timed beside the headline")
     ap.add_argument("--side-steps", type=int, default=3, help="timed steps of each side form")
+    ap.add_argument("--side-only", choices=["differentiation", "polarisation", "batching"], default=None,
+                    help="run only this side form beside the headline")
     return ap.parse_args()
 
 
@@ -532,6 +534,8 @@ def run_ours(args):
         for name, fn in (("differentiation_form", lambda: measure_differentiation(args, plan, args.side_steps)),
                          ("polarisation_form", lambda: measure_spin2(args, plan, args.side_steps)),
                          ("batching_form", lambda: measure_requests(args, rank, world, args.side_steps, 1))):
+            if args.side_only and not name.startswith(args.side_only):
+                continue
             try:
                 side[name] = fn()
             except Exception as exc:  # reported, not fatal: the headline stands on its own
@@ -614,6 +618,8 @@ def measure_requests(args, rank, world, steps, warmup):
     for prec in ("fp64", "fp32_tc"):
         multi = sht.Multi(plans, prec)
         outs = multi.outputs()
+        t1 = time.perf_counter()
+        tiles = dict(multi.autotune(alms, outs), seconds=time.perf_counter() - t1)
         for _ in range(warmup):
             multi.alm2map(alms, outs)
         torch.cuda.synchronize()
@@ -627,7 +633,7 @@ def measure_requests(args, rank, world, steps, warmup):
         ms = statistics.median([ev[k].elapsed_time(ev[k + 1]) for k in range(steps)])
         ms = max_over_ranks(ms, torch.device("cuda", torch.cuda.current_device()))
         res[prec] = {"ms_per_step": ms, "requests_per_s": world * args.requests / (ms * 1e-3),
-                     "gpu_launches_per_step": (sht.kernel_launches() - n0) / steps,
+                     "gpu_launches_per_step": (sht.kernel_launches() - n0) / steps, "tiles": tiles,
                      "timing": "median of %d steps (CUDA events per step)" % steps}
         multi.close()
         del outs

@@ -419,6 +419,22 @@ int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht_multi_t *o
 int sht_multi_alm2map(sht_multi_t multi, const void *const *alm_dev, void *const *map_dev, void *stream);
 int sht_multi_destroy(sht_multi_t multi);
 
+/* Tile shapes of a multi-request context (no counterpart in the paper;
+ * results do not depend on them): vals[0] = persistent CTAs per SM of the
+ * FP64 Legendre launch (1..32, default 8), vals[1] = threads per CTA of the
+ * tensor-core forms' shared-memory ring kernel (256 or 512, default 256).
+ * n >= 2.  SHT_EINVAL for a NULL context or array, n < 2 or a value out of
+ * range. */
+int sht_multi_tiles(sht_multi_t multi, int *out, int n);
+int sht_multi_set_tiles(sht_multi_t multi, const int *vals, int n);
+
+/* Autotuner of a multi-request context: times each candidate (FP64: 2, 4, 8,
+ * 16 CTAs per SM; tensor-core forms: 256 or 512 ring threads) on the caller's
+ * requests (one untimed call, one call timed with events on `stream`) and
+ * keeps the fastest.  The maps hold the last call's result.  Synchronises
+ * `stream`.  Errors as sht_multi_alm2map. */
+int sht_multi_autotune(sht_multi_t multi, const void *const *alm_dev, void *const *map_dev, void *stream);
+
 /* Test hook: sht_debug_poison_delta for the Delta workspace of a
  * multi-request context.  SHT_EINVAL for a NULL context. */
 int sht_multi_debug_poison_delta(sht_multi_t multi);

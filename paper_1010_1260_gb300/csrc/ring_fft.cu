@@ -987,20 +987,23 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
 
 cudaError_t launch_ring_synth_mf_multi(const DevPlan *plans_dev, const int2 *smooth_items, int n_smooth,
                                        int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
-                                       const MultiTcPtrs &mp, cudaStream_t st)
+                                       const MultiTcPtrs &mp, int nt, cudaStream_t st)
 {
+    const bool big = nt >= 512;
     for (int pass = 0; pass < 2; ++pass) {
         const bool blue = pass == 1;
         const int n = blue ? n_blue : n_smooth;
         if (n <= 0) continue;
         const int cap = blue ? blue_cap : smooth_cap;
         const size_t smem = ring_mf_smem_bytes(cap, 1);
-        auto k = blue ? ring_synth_mf_kernel<true, 1, 256, true> : ring_synth_mf_kernel<false, 1, 256, true>;
+        auto k = blue ? (big ? ring_synth_mf_kernel<true, 1, 512, true> : ring_synth_mf_kernel<true, 1, 256, true>)
+                      : (big ? ring_synth_mf_kernel<false, 1, 512, true> : ring_synth_mf_kernel<false, 1, 256, true>);
         if (smem > 40 * 1024) {  // dynamic + static above the 48 KB default needs the opt-in
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k<<<n, 256, smem, st>>>(DevPlan{}, nullptr, nullptr, 1, plans_dev, blue ? blue_items : smooth_items, mp, cap);
+        k<<<n, big ? 512 : 256, smem, st>>>(DevPlan{}, nullptr, nullptr, 1, plans_dev, blue ? blue_items : smooth_items,
+                                            mp, cap);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -2146,6 +2146,8 @@ extern "C" int sht_ring_synth_part(sht_plan_t p, int nbatch, int nparts, const i
 
 struct sht_multi_s {
     int nreq = 0, prec = 0, device = 0, nctas = 0;
+    int nsm = 1;         // SMs of the device
+    int ring_nt = 256;   // tensor-core forms: threads per CTA of the shared-memory ring kernel
     std::vector<sht_plan_t> plans;
     std::vector<size_t> delta_ofs;  // bytes, per request
     std::vector<void *> allocs;
@@ -2292,6 +2294,7 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, q->device);
         q->nctas = std::max(1, nsm) * 8;  // persistent CTAs: several per SM hide the FP64 latency
+        q->nsm = std::max(1, nsm);
     } else {
         // tensor-core forms: each plan's B operand buffer and skip tables, then
         // one work list (request, m, ring block) by decreasing cost for one
@@ -2377,6 +2380,10 @@ extern "C" int sht_multi_create(int nreq, const sht_plan_t *plans, int prec, sht
             return fail(SHT_ENOMEM, "multi workspace: %s", cudaGetErrorString(e));
         }
         q->allocs.push_back(q->d_delta);
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, q->device);
+        q->nsm = std::max(1, nsm);
+        q->nctas = 8 * q->nsm;  // the FP64 launch's setting, kept for sht_multi_tiles
     }
     *out = q;
     return SHT_OK;
@@ -2441,7 +2448,7 @@ extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void
         if (e != cudaSuccess) return cuda_fail(e, "ring_reg multi launch");
         g_launches.fetch_add(q->n_rf > 0, std::memory_order_relaxed);
         e = sht::launch_ring_synth_mf_multi(q->d_plans, q->d_smooth, q->n_smooth, q->smooth_cap, q->d_blue, q->n_blue,
-                                            q->blue_cap, mp, st);
+                                            q->blue_cap, mp, q->ring_nt, st);
         if (e != cudaSuccess) return cuda_fail(e, "ring_synth_mf multi launch");
         g_launches.fetch_add((q->n_smooth > 0) + (q->n_blue > 0), std::memory_order_relaxed);
         return SHT_OK;
@@ -2464,6 +2471,78 @@ extern "C" int sht_multi_alm2map(sht_multi_t q, const void *const *alm_dev, void
     if (e != cudaSuccess) return cuda_fail(e, "ring_synth_multi launch");
     g_launches.fetch_add((q->n_smooth > 0) + (q->n_blue > 0), std::memory_order_relaxed);
     return SHT_OK;
+}
+
+// Tile shapes of a multi-request context: vals[0] = persistent CTAs per SM of
+// the FP64 Legendre launch, vals[1] = threads per CTA of the tensor-core
+// forms' shared-memory ring kernel.  Results do not depend on them.
+extern "C" int sht_multi_tiles(sht_multi_t q, int *out, int n)
+{
+    g_err.clear();
+    if (!q || !out || n < 2) return fail(SHT_EINVAL, "null multi handle or array, or n < 2");
+    out[0] = q->nctas / q->nsm;
+    out[1] = q->ring_nt;
+    return SHT_OK;
+}
+
+extern "C" int sht_multi_set_tiles(sht_multi_t q, const int *vals, int n)
+{
+    g_err.clear();
+    if (!q || !vals || n < 2) return fail(SHT_EINVAL, "null multi handle or array, or n < 2");
+    if (vals[0] < 1 || vals[0] > 32) return fail(SHT_EINVAL, "CTAs per SM %d not in 1..32", vals[0]);
+    if (vals[1] != 256 && vals[1] != 512) return fail(SHT_EINVAL, "ring threads %d not 256 or 512", vals[1]);
+    q->nctas = vals[0] * q->nsm;
+    q->ring_nt = vals[1];
+    return SHT_OK;
+}
+
+// Times every candidate tile shape of the context on the caller's requests
+// (one untimed call, then one call timed with events on `stream`) and keeps
+// the fastest; the maps are overwritten by the last call.
+extern "C" int sht_multi_autotune(sht_multi_t q, const void *const *alm_dev, void *const *map_dev, void *stream)
+{
+    g_err.clear();
+    if (!q) return fail(SHT_EINVAL, "null multi handle");
+    DeviceGuard dg(q->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<std::pair<int, int>> cand;
+    if (q->prec == SHT_FP64) {
+        for (int c : {2, 4, 8, 16}) cand.push_back({c, q->ring_nt});
+    } else {
+        for (int t : {256, 512}) cand.push_back({q->nctas / q->nsm, t});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    int rc = SHT_OK;
+    float best = 1e30f;
+    std::pair<int, int> pick = cand[0];
+    for (const auto &c : cand) {
+        const int v[2] = {c.first, c.second};
+        if ((rc = sht_multi_set_tiles(q, v, 2)) || (rc = sht_multi_alm2map(q, alm_dev, map_dev, stream))) break;
+        cudaEventRecord(e0, st);
+        if ((rc = sht_multi_alm2map(q, alm_dev, map_dev, stream))) break;
+        cudaEventRecord(e1, st);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int v[2] = {pick.first, pick.second};
+    sht_multi_set_tiles(q, v, 2);
+    return rc;
 }
 
 extern "C" int sht_alm2map_multi(int nreq, const sht_plan_t *plans, const void *const *alm_dev,

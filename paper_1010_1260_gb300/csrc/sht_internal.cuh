@@ -255,7 +255,7 @@ cudaError_t launch_tc_main_multi(const DevPlan &P, const DevPlan *plans_dev, con
 // buffers over the requests.
 cudaError_t launch_ring_synth_mf_multi(const DevPlan *plans_dev, const int2 *smooth_items, int n_smooth,
                                        int smooth_cap, const int2 *blue_items, int n_blue, int blue_cap,
-                                       const MultiTcPtrs &mp, cudaStream_t st);
+                                       const MultiTcPtrs &mp, int nt, cudaStream_t st);
 size_t tc_lambda_bytes(const DevPlan &P, const TcWork &W, int prec);
 // Fill the evanescent-skip tables (skip_g: [mmax+1][nrb]; warm_*: [mmax+1][npairs])
 // and raise pair_lim[pair] (zeroed by the caller) to 1 + the largest order with

@@ -95,6 +95,9 @@ def lib():
             L.sht_debug_poison_delta.argtypes = [P]
             L.sht_order_limits.argtypes = [P, ctypes.POINTER(I)]
             L.sht_multi_debug_poison_delta.argtypes = [P]
+            L.sht_multi_tiles.argtypes = [P, ctypes.POINTER(I), I]
+            L.sht_multi_set_tiles.argtypes = [P, ctypes.POINTER(I), I]
+            L.sht_multi_autotune.argtypes = [P, PP, PP, V]
             L.sht_alm2map_host.argtypes = [P, I, I, PP, PP, I, V]
             IP = ctypes.POINTER(I)
             L.sht_partition.argtypes = [I, I, I, IP, I, IP, IP]
@@ -120,7 +123,8 @@ def lib():
                       "sht_work_lists", "sht_debug_work_lists", "sht_debug_ring_kernel",
                       "sht_alm2map_host", "sht_partition", "sht_ring_lengths", "sht_alm2map_mpart",
                       "sht_ring_synth_part", "sht_debug_report", "sht_alm2map_spin2", "sht_debug_poison_delta",
-                      "sht_multi_debug_poison_delta", "sht_order_limits"):
+                      "sht_multi_debug_poison_delta", "sht_order_limits", "sht_multi_tiles", "sht_multi_set_tiles",
+                      "sht_multi_autotune"):
                 getattr(L, f).restype = I
             _lib = L
     return _lib
@@ -560,6 +564,26 @@ class Multi:
     def debug_poison_delta(self):
         """Test hook: fill the context's Delta workspace with NaN bytes (synchronises)."""
         check(lib().sht_multi_debug_poison_delta(self._h))
+
+    def tiles(self) -> dict:
+        """Tile shapes: FP64 persistent CTAs per SM, tensor-core ring-kernel threads."""
+        out = (ctypes.c_int * 2)()
+        check(lib().sht_multi_tiles(self._h, out, 2))
+        return {"fp64_ctas_per_sm": out[0], "ring_threads": out[1]}
+
+    def set_tiles(self, fp64_ctas_per_sm: int, ring_threads: int):
+        vals = (ctypes.c_int * 2)(int(fp64_ctas_per_sm), int(ring_threads))
+        check(lib().sht_multi_set_tiles(self._h, vals, 2))
+
+    def autotune(self, alms, outs=None, stream=None) -> dict:
+        """Time the candidate tile shapes on these requests, keep the fastest; returns tiles()."""
+        n = len(self.plans)
+        if outs is None:
+            outs = self.outputs(alms[0].device)
+        a_arr = (ctypes.c_void_p * n)(*[a.data_ptr() for a in alms])
+        m_arr = (ctypes.c_void_p * n)(*[m.data_ptr() for m in outs])
+        check(lib().sht_multi_autotune(self._h, a_arr, m_arr, _stream_ptr(stream)))
+        return self.tiles()
 
     def outputs(self, device=None):
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())

@@ -66,6 +66,9 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.sht_debug_ring_kernel(None, 0) == sht.SHT_EINVAL
     assert lib.sht_debug_poison_delta(None) == sht.SHT_EINVAL
     assert lib.sht_multi_debug_poison_delta(None) == sht.SHT_EINVAL
+    assert lib.sht_multi_tiles(None, None, 2) == sht.SHT_EINVAL
+    assert lib.sht_multi_set_tiles(None, None, 2) == sht.SHT_EINVAL
+    assert lib.sht_multi_autotune(None, None, None, None) == sht.SHT_EINVAL
     assert lib.sht_alm2map_host(None, 1, 1, None, None, 0, None) == sht.SHT_EINVAL
     assert lib.sht_alm2map_mpart(None, 1, 1, None, None, 0, None, None, 0, None) == sht.SHT_EINVAL
     assert lib.sht_ring_synth_part(None, 1, 1, None, None, 0, None, None, 0, None) == sht.SHT_EINVAL

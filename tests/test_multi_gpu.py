@@ -203,3 +203,32 @@ def test_multi_rejects_bad_arguments(sht):
     arr = (ctypes.c_void_p * 1)(plan.handle)
     assert L.sht_multi_create(1, arr, 9, ctypes.byref(h)) == sht.SHT_EINVAL
     assert L.sht_multi_alm2map(None, None, None, None) == sht.SHT_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_tc", "bf16x6_tc"])
+def test_multi_tiles_bit_identical_and_autotune(sht, prec):
+    """Every tile shape of a multi-request context gives the same maps bit for
+    bit; the autotuner keeps one of the candidates."""
+    plans, alms = _requests(sht, [64, 130, 33, 200, 97])
+    mc = sht.Multi(plans, prec)
+    ref = [o.clone() for o in mc.alm2map(alms)]
+    torch.cuda.synchronize()
+    assert mc.tiles() == {"fp64_ctas_per_sm": 8, "ring_threads": 256}
+    cands = [(c, 256) for c in (2, 4, 8, 16)] if prec == "fp64" else [(8, 256), (8, 512)]
+    for c, t in cands:
+        mc.set_tiles(c, t)
+        outs = mc.alm2map(alms)
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r), (c, t)
+    tiles = mc.autotune(alms)
+    assert (tiles["fp64_ctas_per_sm"], tiles["ring_threads"]) in cands
+    outs = mc.alm2map(alms)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    with pytest.raises(Exception):
+        mc.set_tiles(0, 256)
+    with pytest.raises(Exception):
+        mc.set_tiles(8, 384)
+    mc.close()
