@@ -1211,14 +1211,6 @@ __device__ __forceinline__ void prep_b_order(const DevPlan &P, const double2 *__
     }
 }
 
-template <bool BF16, int NPB>
-__global__ void prep_b_kernel(const DevPlan P, const double2 *__restrict__ alm, const int *__restrict__ seg_off,
-                              unsigned char *__restrict__ bout, int nmaps, int ncols)
-{
-    prep_b_order<BF16, NPB>(P, alm, seg_off, bout, nmaps, ncols, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x,
-                            gridDim.x * blockDim.x);
-}
-
 // Operand prep of many one-map requests in one launch: block i converts order
 // items[i].y of request items[i].x into that request's B operand image.
 template <bool BF16, int NPB>
@@ -1231,13 +1223,79 @@ __global__ void prep_b_multi_kernel(const DevPlan *__restrict__ plans, const int
                             threadIdx.x, blockDim.x);
 }
 
+// The same operand image, one CTA per (stage i, order m): the stage's 2 KC
+// degrees of every map are read once with coalesced loads (512 contiguous
+// bytes per map for BF16), multiplied by C_l and rounded to FP32 into shared
+// memory (row c = 2 map + {re, im}, padded to avoid bank conflicts), then each
+// thread turns one half row (parity, c, 16-byte half) into the half rows of
+// every piece, written as 16-byte stores.  Same values as prep_b_order.
+template <bool BF16, int NPB>
+__global__ void __launch_bounds__(256)
+prep_b_stage_kernel(const DevPlan P, const double2 *__restrict__ alm, const int *__restrict__ seg_off,
+                    unsigned char *__restrict__ bout, int nmaps, int ncols)
+{
+    constexpr int KC = BF16 ? 16 : 8;
+    constexpr int STEPS = 2 * KC;
+    constexpr int VEC = BF16 ? 8 : 4;  // values per 16-byte half row
+    constexpr size_t SB = (size_t)2 * NPB * kTileBytes;
+    __shared__ float sv[128][STEPS + 1];
+    const int L = P.lmax;
+    const int m = blockIdx.y, i = blockIdx.x;
+    const int nst = (L - m + 1 + STEPS - 1) / STEPS;
+    if (i >= nst) return;
+    const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
+    const int l0 = m + STEPS * i;
+    SHT_CHECK(P.dbg, ncols <= 128, 408);
+    for (int e = threadIdx.x; e < (ncols >> 1) * STEPS; e += blockDim.x) {
+        const int b = e / STEPS, o = e - b * STEPS, l = l0 + o;
+        float re = 0.f, im = 0.f;
+        if (l <= L && b < nmaps) {
+            const double c = __ldg(&P.coefC[mofs + (l - m)]);
+            const double2 a = __ldg(&alm[(size_t)b * P.nalm + mofs + (l - m)]);
+            re = rn_f32(c * a.x);
+            if (m != 0) im = rn_f32(c * a.y);
+        }
+        sv[2 * b][o] = re;
+        sv[2 * b + 1][o] = im;
+    }
+    __syncthreads();
+    unsigned char *blk = bout + (size_t)(seg_off[2 * m] / STEPS + i) * SB;
+    for (int w = threadIdx.x; w < 4 * ncols; w += blockDim.x) {
+        const int h = w & 1, c = (w >> 1) % ncols, par = (w >> 1) / ncols;
+        uint32_t words[NPB][4];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            uint32_t pc[NPB];
+            split_pieces<BF16, NPB>(sv[c][par + 2 * (VEC * h + v)], pc);
+#pragma unroll
+            for (int q = 0; q < NPB; ++q) {
+                if (BF16) {
+                    if (v & 1)
+                        words[q][v >> 1] |= pc[q] & 0xFFFF0000u;
+                    else
+                        words[q][v >> 1] = pc[q] >> 16;
+                } else {
+                    words[q][v] = pc[q];
+                }
+            }
+        }
+        const int off = c * kRowBytes + ((h ^ ((c >> 2) & 1)) << 4);
+#pragma unroll
+        for (int q = 0; q < NPB; ++q)
+            *reinterpret_cast<uint4 *>(blk + (size_t)(par * NPB + q) * kTileBytes + off) =
+                make_uint4(words[q][0], words[q][1], words[q][2], words[q][3]);
+    }
+}
+
 template <bool BF16, int NPA, int NPB>
 cudaError_t run_prep(const DevPlan &P, const TcWork &W, const double2 *alm, int nmaps, cudaStream_t st)
 {
+    constexpr int STEPS = BF16 ? 32 : 16;
     const int ncols = tc_ncols(nmaps);
     const int *seg = BF16 ? W.seg_bf16 : W.seg_tf32;
-    dim3 grid(64, P.mmax + 1);
-    prep_b_kernel<BF16, NPB><<<grid, 256, 0, st>>>(P, alm, seg, static_cast<unsigned char *>(W.bbuf), nmaps, ncols);
+    dim3 grid((P.lmax + 1 + STEPS - 1) / STEPS, P.mmax + 1);  // stages of order 0, the most
+    prep_b_stage_kernel<BF16, NPB>
+        <<<grid, 256, 0, st>>>(P, alm, seg, static_cast<unsigned char *>(W.bbuf), nmaps, ncols);
     return cudaGetLastError();
 }
 
