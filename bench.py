@@ -63,7 +63,8 @@ def parse():
                     help="stratified ring sample on which every map of the batch is checked against the oracle")
     ap.add_argument("--acc-full-maps", type=int, default=2,
                     help="maps checked against the oracle on every ring (first and last of the batch)")
-    ap.add_argument("--e2e-steps", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=32,
+                    help="steps of the end-to-end (host buffers) measurement, one pipelined call")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--lambda-cache", action="store_true",
@@ -477,7 +478,10 @@ def run_ours(args):
         a_pins = [torch.from_numpy(alm_h).pin_memory() for _ in range(2)]
         m_pins = [torch.empty((B, plan.npix), dtype=sht.MAP_DTYPE[args.prec], pin_memory=True)
                   for _ in range(2)]
-        plan.alm2map_host_stream(a_pins[:1], args.prec, outs=m_pins[:1])  # warm-up
+        # warm-up through both buffer pairs (device buffers allocated, every
+        # pinned page touched once)
+        plan.alm2map_host_stream([a_pins[k % 2] for k in range(max(2, args.warmup))], args.prec,
+                                 outs=[m_pins[k % 2] for k in range(max(2, args.warmup))])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plan.alm2map_host_stream([a_pins[k % 2] for k in range(args.e2e_steps)], args.prec,
