@@ -41,12 +41,16 @@
 #include "sht.h"
 #include "sht_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <cstdint>
 #include <mutex>
 
 namespace sht {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();  // ring_reg.cu
 namespace {
 
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s per wait
@@ -1593,8 +1597,9 @@ adj_prep_kernel(const DevPlan P, const float2 *__restrict__ q, unsigned char *__
     }
 }
 
-// One CTA per item (m, block j of 128 degrees of each parity), items by
-// increasing m; the K loop runs over the chunks of 32 ring pairs:
+// Persistent, one CTA per SM over the items (m, block j of 128 degrees of
+// each parity), taken round robin in increasing m; per item the K loop runs
+// over the chunks of 32 ring pairs:
 //   warps 0-7  drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 32
 //              (rows = degrees) of E (w < 4) or O; after every chunk it adds
 //              the finished accumulator into its register totals (FP32, round
@@ -1615,8 +1620,9 @@ adj_prep_kernel(const DevPlan P, const float2 *__restrict__ q, unsigned char *__
 template <int NPA, int NPB>
 __global__ void __launch_bounds__(kAdjWarps * 32, 1)
 legendre_adj_tc_kernel(const DevPlan P, const unsigned char *__restrict__ acache, const int *__restrict__ seg_off,
-                       const unsigned char *__restrict__ bimg, const int2 *__restrict__ items,
-                       double2 *__restrict__ g, int nmaps, int ncol, double cfac, int *__restrict__ status)
+                       const unsigned char *__restrict__ bimg, const int2 *__restrict__ items, int nitems,
+                       double2 *__restrict__ g, int nmaps, int ncol, double cfac, int *__restrict__ status,
+                       const __grid_constant__ CUtensorMap amap, int use_tma)
 {
     using A = AdjCfg<NPA, NPB>;
     constexpr int NS = A::NS;
@@ -1637,20 +1643,35 @@ legendre_adj_tc_kernel(const DevPlan P, const unsigned char *__restrict__ acache
     const int nch = (P.npairs + kAdjPairs - 1) / kAdjPairs;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int2 it = items[blockIdx.x];
-    const int m = it.x, j = it.y;
-    const int nst = (L - m + 1 + STEPS - 1) / STEPS;
-    const int i_lo = kAdjStages * j, i_hi = min(nst, i_lo + kAdjStages);  // the block's cached stages
-    const uint32_t sbb = (uint32_t)2 * NPB * 2 * ncol * kRowBytes;       // operand image block per chunk
-    SHT_CHECK(P.dbg, (ncol == 32 || ncol == 64) && i_lo < i_hi && 2 * nmaps <= ncol, 501);
+    const uint32_t sbb = (uint32_t)2 * NPB * 2 * ncol * kRowBytes;  // operand image block per chunk
+    SHT_CHECK(P.dbg, (ncol == 32 || ncol == 64) && 2 * nmaps <= ncol, 501);
+    // persistent: the CTA runs items blockIdx.x, + gridDim.x, ...; every role
+    // walks the same sequence, and the barrier phases run on across items
+    struct Item {
+        int m, j, nst, i_lo, i_hi;  // order, degree block, stages of m, the block's cached stages
+    };
+    auto item_of = [&](int t) {
+        const int2 it = items[t];
+        Item I;
+        I.m = it.x;
+        I.j = it.y;
+        I.nst = (L - I.m + 1 + STEPS - 1) / STEPS;
+        I.i_lo = kAdjStages * I.j;
+        I.i_hi = min(I.nst, I.i_lo + kAdjStages);
+        return I;
+    };
 
     auto bar_full = [&](int s) { return smem_u32(&bars[s]); };
     auto bar_empty = [&](int s) { return smem_u32(&bars[NS + s]); };
     auto bar_set_full = [&](int k) { return smem_u32(&bars[2 * NS + k]); };
     auto bar_set_empty = [&](int k) { return smem_u32(&bars[2 * NS + 2 + k]); };
     const uint32_t bar_mma_drain = smem_u32(&bars[2 * NS + 4]);
+    // A slices of a chunk: [stage][parity][piece], 1 KB each (the order of a
+    // tensor-map box over the cached operand), so consecutive 16-degree blocks
+    // of one (parity, piece) are 2 NPA KB apart (the MN-major leading byte offset)
+    constexpr uint32_t kLbo = 2 * NPA * kAdjSlice;
     auto a_slice = [&](int s, int par, int piece, int st) {
-        return stage0 + (size_t)s * A::STAGE_BYTES + (size_t)((par * NPA + piece) * kAdjStages + st) * kAdjSlice;
+        return stage0 + (size_t)s * A::STAGE_BYTES + (size_t)(st * 2 * NPA + par * NPA + piece) * kAdjSlice;
     };
     auto b_tile = [&](int s, int par, int piece, int ks) {
         return stage0 + (size_t)s * A::STAGE_BYTES + A::A_BYTES + (size_t)((par * NPB + piece) * 2 + ks) * ncol * kRowBytes;
@@ -1658,11 +1679,11 @@ legendre_adj_tc_kernel(const DevPlan P, const unsigned char *__restrict__ acache
     // chunk k (pairs 32 k ..) of ring block k / 4 runs iff it has pairs, the
     // block has a value in FP32 range at this order, and the item's degrees
     // reach the block's first nonzero stage
-    auto live = [&](int k) {
+    auto live = [&](const Item &I, int k) {
         const int rb = k >> 2;
-        if (P.block_mlim && m >= P.block_mlim[rb]) return false;
-        const int s0 = P.skip_g ? P.skip_g[m * nrb + rb] * GROUP : 0;
-        return i_hi > s0;
+        if (P.block_mlim && I.m >= P.block_mlim[rb]) return false;
+        const int s0 = P.skip_g ? P.skip_g[I.m * nrb + rb] * GROUP : 0;
+        return I.i_hi > s0;
     };
 
     if (threadIdx.x == 0) {
@@ -1693,35 +1714,38 @@ legendre_adj_tc_kernel(const DevPlan P, const unsigned char *__restrict__ acache
         const int quad = warp & 3;
         const int half = warp >> 2;  // 0: E (l - m even), 1: O
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        float tot[64];
-#pragma unroll
-        for (int c = 0; c < 64; ++c) tot[c] = 0.f;
         uint32_t gg = 0;
         bool ok = true;
-        for (int k = 0; k < nch && ok; ++k) {
-            if (!live(k)) continue;
-            const int set = (int)(gg & 1u);
-            ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
-            if (!ok) break;
-            tc_fence_after();
+        for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+            const Item I = item_of(t);
+            float tot[64];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (32 * h < ncol) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(128 * set + half * ncol + 32 * h), v);
+            for (int c = 0; c < 64; ++c) tot[c] = 0.f;
+            for (int k = 0; k < nch && ok; ++k) {
+                if (!live(I, k)) continue;
+                const int set = (int)(gg & 1u);
+                ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
+                if (!ok) break;
+                tc_fence_after();
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) tot[32 * h + c] += __uint_as_float(v[c]);
+                for (int h = 0; h < 2; ++h) {
+                    if (32 * h < ncol) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + lane_base + (uint32_t)(128 * set + half * ncol + 32 * h), v);
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) tot[32 * h + c] += __uint_as_float(v[c]);
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_set_empty(set));
+                ++gg;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_set_empty(set));
-            ++gg;
-        }
-        if (ok) {
+            if (!ok) break;
             // row r = 16 (stage in the block) + position in the stage's parity
+            const int m = I.m;
             const int r = quad * 32 + lane;
-            const int l = m + 2 * (kAdjStages * 16 * j + r) + half;
+            const int l = m + 2 * (kAdjStages * 16 * I.j + r) + half;
             if (l <= L) {
                 const long long mofs = (long long)m * (2 * L + 3 - m) / 2;
                 const double cl = (m == 0 ? 1.0 : cfac) * __ldg(&P.coefC[mofs + (l - m)]);
@@ -1736,30 +1760,49 @@ legendre_adj_tc_kernel(const DevPlan P, const unsigned char *__restrict__ acache
     } else if (warp == 8) {
         // ---------------------------------------------------------- loads --
         if (lane == 0) {
-            const size_t st0 = (size_t)(seg_off[2 * m] / STEPS);  // stages of the orders below m
             uint32_t gs = 0;
             bool ok = true;
-            for (int k = 0; k < nch && ok; ++k) {
-                if (!live(k)) continue;
-                const int s = (int)(gs % NS);
-                const uint32_t ph = (gs / NS) & 1u;
-                if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
-                    ok = false;
-                    break;
+            for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+                const Item I = item_of(t);
+                const size_t st0 = (size_t)(seg_off[2 * I.m] / STEPS);  // stages of the orders below m
+                SHT_CHECK(P.dbg, I.i_lo < I.i_hi, 503);
+                for (int k = 0; k < nch && ok; ++k) {
+                    if (!live(I, k)) continue;
+                    const int s = (int)(gs % NS);
+                    const uint32_t ph = (gs / NS) & 1u;
+                    if (!mbar_wait(bar_empty(s), ph ^ 1u, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const int rb = k >> 2, w = k & 3;
+                    const size_t sg = st0 * nrb + (size_t)rb * I.nst + I.i_lo;  // first stage, whole-operand index
+                    if (use_tma) {
+                        // one box: 8 stages x 2 NPA tiles x the chunk's 1 KB slice (stages
+                        // past the operand's end read as zeros, the rest feed rows above lmax)
+                        mbar_expect_tx(bar_full(s), (uint32_t)(kAdjStages * 2 * NPA * kAdjSlice) + sbb);
+                        SHT_CHECK(P.dbg, sg < 0x7fffffffull, 504);
+                        asm volatile(
+                            "cp.async.bulk.tensor.4d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+                                smem_u32(a_slice(s, 0, 0, 0))),
+                            "l"(reinterpret_cast<uint64_t>(&amap)), "r"(0), "r"(w), "r"(0), "r"((int)sg),
+                            "r"(bar_full(s))
+                            : "memory");
+                    } else {
+                        mbar_expect_tx(bar_full(s), (uint32_t)((I.i_hi - I.i_lo) * 2 * NPA * kAdjSlice) + sbb);
+                        const unsigned char *ablk = acache + sg * SA;
+                        for (int i = 0; i < I.i_hi - I.i_lo; ++i)
+#pragma unroll
+                            for (int par = 0; par < 2; ++par)
+#pragma unroll
+                                for (int pc = 0; pc < NPA; ++pc)
+                                    bulk_load(smem_u32(a_slice(s, par, pc, i)),
+                                              ablk + (size_t)i * SA + (size_t)(par * NPA + pc) * kTileBytes +
+                                                  (size_t)w * kAdjSlice,
+                                              kAdjSlice, bar_full(s));
+                    }
+                    bulk_load(smem_u32(b_tile(s, 0, 0, 0)), bimg + ((size_t)I.m * nch + k) * sbb, sbb, bar_full(s));
+                    ++gs;
                 }
-                const int rb = k >> 2, w = k & 3;
-                mbar_expect_tx(bar_full(s), (uint32_t)((i_hi - i_lo) * 2 * NPA * kAdjSlice) + sbb);
-                const unsigned char *ablk = acache + (st0 * nrb + (size_t)rb * nst) * SA;
-                for (int i = i_lo; i < i_hi; ++i)
-#pragma unroll
-                    for (int par = 0; par < 2; ++par)
-#pragma unroll
-                        for (int pc = 0; pc < NPA; ++pc)
-                            bulk_load(smem_u32(a_slice(s, par, pc, i - i_lo)),
-                                      ablk + (size_t)i * SA + (size_t)(par * NPA + pc) * kTileBytes + (size_t)w * kAdjSlice,
-                                      kAdjSlice, bar_full(s));
-                bulk_load(smem_u32(b_tile(s, 0, 0, 0)), bimg + ((size_t)m * nch + k) * sbb, sbb, bar_full(s));
-                ++gs;
             }
             if (s_abort) {
                 const uint32_t first = gs > (uint32_t)NS ? gs - NS : 0u;
@@ -1772,39 +1815,42 @@ legendre_adj_tc_kernel(const DevPlan P, const unsigned char *__restrict__ acache
             const uint32_t id = idesc<true>(ncol) | (1u << 15);  // A MN-major
             uint32_t gs = 0;
             bool ok = true, issued = false;
-            for (int k = 0; k < nch && ok; ++k) {
-                if (!live(k)) continue;
-                const int s = (int)(gs % NS);
-                const uint32_t ph = (gs / NS) & 1u;
-                const int set = (int)(gs & 1u);
-                if (!mbar_wait(bar_set_empty(set), ((gs >> 1) & 1u) ^ 1u, &s_abort) ||
-                    !mbar_wait(bar_full(s), ph, &s_abort)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                SHT_CHECK(P.dbg, 128 * set + 2 * ncol <= 256 && s < NS, 502);
+            for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+                const Item I = item_of(t);
+                for (int k = 0; k < nch && ok; ++k) {
+                    if (!live(I, k)) continue;
+                    const int s = (int)(gs % NS);
+                    const uint32_t ph = (gs / NS) & 1u;
+                    const int set = (int)(gs & 1u);
+                    if (!mbar_wait(bar_set_empty(set), ((gs >> 1) & 1u) ^ 1u, &s_abort) ||
+                        !mbar_wait(bar_full(s), ph, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    SHT_CHECK(P.dbg, 128 * set + 2 * ncol <= 256 && s < NS, 502);
 #pragma unroll
-                for (int par = 0; par < 2; ++par) {
-                    const uint32_t d = tmem + (uint32_t)(128 * set + par * ncol);
+                    for (int par = 0; par < 2; ++par) {
+                        const uint32_t d = tmem + (uint32_t)(128 * set + par * ncol);
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
+                        for (int ks = 0; ks < 2; ++ks) {
 #pragma unroll
-                        for (int pr = 0; pr < A::NPROD; ++pr) {
-                            int ia, ib;
-                            product_pieces<NPA, NPB>(pr, ia, ib);
-                            // K step ks: pairs 16 ks .. 16 ks + 15 = two 8-row groups further
-                            const uint64_t ad =
-                                sdesc_sw32_mn(smem_u32(a_slice(s, par, ia, 0)) + 512u * ks, kAdjSlice, 256u);
-                            const uint64_t bd = sdesc_sw32(smem_u32(b_tile(s, par, ib, ks)));
-                            tc_mma<true>(d, ad, bd, id, (ks > 0 || pr > 0) ? 1u : 0u);
+                            for (int pr = 0; pr < A::NPROD; ++pr) {
+                                int ia, ib;
+                                product_pieces<NPA, NPB>(pr, ia, ib);
+                                // K step ks: pairs 16 ks .. 16 ks + 15 = two 8-row groups further
+                                const uint64_t ad =
+                                    sdesc_sw32_mn(smem_u32(a_slice(s, par, ia, 0)) + 512u * ks, kLbo, 256u);
+                                const uint64_t bd = sdesc_sw32(smem_u32(b_tile(s, par, ib, ks)));
+                                tc_mma<true>(d, ad, bd, id, (ks > 0 || pr > 0) ? 1u : 0u);
+                            }
                         }
                     }
+                    issued = true;
+                    tc_commit(bar_empty(s));
+                    tc_commit(bar_set_full(set));
+                    ++gs;
                 }
-                issued = true;
-                tc_commit(bar_empty(s));
-                tc_commit(bar_set_full(set));
-                ++gs;
             }
             if (!ok && issued) {
                 tc_commit(bar_mma_drain);
@@ -1870,7 +1916,33 @@ cudaError_t launch_adj_tc(const DevPlan &P, const TcWork &W, int prec, const voi
     dim3 pg(((P.mmax + 1) * (ncol >> 1) + 255) / 256, nch);
     unsigned char *bo = static_cast<unsigned char *>(bimg);
     const unsigned char *ac = static_cast<const unsigned char *>(acache);
-    cudaError_t e;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nitems, std::max(1, nsm));  // persistent: one CTA per SM
+    // the cached operand as a 4-D array of 32-bit words: (256 words = one 1 KB
+    // slice of 32 pairs) x (4 slices of a tile) x (2 NPA tiles of a stage) x
+    // stages; a box of 8 stages x 2 NPA tiles x 1 slice is one chunk's A
+    CUtensorMap amap;
+    std::memset(&amap, 0, sizeof amap);
+    int use_tma = 0;
+    {
+        const int npa = prec == SHT_BF16X6_TC ? 3 : 2;
+        const size_t sa = (size_t)2 * npa * kTileBytes;
+        const size_t nstg = tc_lambda_bytes(P, W, prec) / sa;
+        auto enc = tensor_map_encoder();
+        if (enc && (reinterpret_cast<uintptr_t>(acache) & 15) == 0 && nstg > 0 && nstg < 0x7fffffffull) {
+            const cuuint64_t dims[4] = {256, 4, (cuuint64_t)(2 * npa), (cuuint64_t)nstg};
+            const cuuint64_t strides[3] = {(cuuint64_t)kAdjSlice, (cuuint64_t)kTileBytes, (cuuint64_t)sa};
+            const cuuint32_t box[4] = {256, 1, (cuuint32_t)(2 * npa), (cuuint32_t)kAdjStages};
+            const cuuint32_t es[4] = {1, 1, 1, 1};
+            const CUresult cr = enc(&amap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<void *>(acache), dims, strides,
+                                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            use_tma = cr == CUDA_SUCCESS ? 1 : 0;
+        }
+    }
     if (prec == SHT_BF16X6_TC) {
         adj_prep_kernel<3><<<pg, 256, 0, st>>>(P, q, bo, nmaps, ncol);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1878,8 +1950,8 @@ cudaError_t launch_adj_tc(const DevPlan &P, const TcWork &W, int prec, const voi
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjCfg<3, 3>::SMEM)) !=
             cudaSuccess)
             return e;
-        kern<<<nitems, kAdjWarps * 32, AdjCfg<3, 3>::SMEM, st>>>(P, ac, W.seg_bf16, bo, items, g, nmaps, ncol, cfac,
-                                                                   W.status);
+        kern<<<grid, kAdjWarps * 32, AdjCfg<3, 3>::SMEM, st>>>(P, ac, W.seg_bf16, bo, items, nitems, g, nmaps, ncol,
+                                                                 cfac, W.status, amap, use_tma);
     } else {
         adj_prep_kernel<2><<<pg, 256, 0, st>>>(P, q, bo, nmaps, ncol);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1887,8 +1959,8 @@ cudaError_t launch_adj_tc(const DevPlan &P, const TcWork &W, int prec, const voi
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjCfg<2, 2>::SMEM)) !=
             cudaSuccess)
             return e;
-        kern<<<nitems, kAdjWarps * 32, AdjCfg<2, 2>::SMEM, st>>>(P, ac, W.seg_bf16, bo, items, g, nmaps, ncol, cfac,
-                                                                   W.status);
+        kern<<<grid, kAdjWarps * 32, AdjCfg<2, 2>::SMEM, st>>>(P, ac, W.seg_bf16, bo, items, nitems, g, nmaps, ncol,
+                                                                 cfac, W.status, amap, use_tma);
     }
     return cudaGetLastError();
 }

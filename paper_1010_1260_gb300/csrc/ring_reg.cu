@@ -576,6 +576,10 @@ cudaError_t launch_reg(const DevPlan &P, const RegArgs &A0, const CUtensorMap &t
 
 }  // namespace
 
+// The driver's tensor-map encoder (nullptr when the driver has none), shared
+// with the other kernel files.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 size_t ring_reg_smem_bytes(int mmax) { return reg_smem_bytes(slot_rows_for(mmax)); }
 
 cudaError_t launch_ring_reg(const DevPlan &P, const float2 *delta_rm, float *map, int nmaps, int *status,

@@ -1118,7 +1118,8 @@ int analysis_tc(sht_plan_s *p, int nbatch, const float *map, double2 *alm, const
     const size_t need = qb + sht::adj_tc_bimg_bytes(p->dp, prec, G);
     if (p->adj_bytes < need) {
         if (p->adj_ws) {
-            cudaStreamSynchronize(st);
+            cudaError_t e = cudaDeviceSynchronize();  // an earlier call may still use it
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
             cudaFree(p->adj_ws);
         }
         p->adj_ws = nullptr;
