@@ -281,15 +281,16 @@ int sht_skip_evanescent(sht_plan_t plan, int enable);
  * SHT_EINVAL (no plan, unknown prec, nbatch < 1), SHT_ENOMEM, SHT_ECUDA. */
 int sht_autotune(sht_plan_t plan, int prec, int nbatch, void *stream);
 
-/* Current tile shapes of the plan: out[0..min(n, 5)) = {FP32 ring maps per
+/* Current tile shapes of the plan: out[0..min(n, 6)) = {FP32 ring maps per
  * CTA (smooth list), (Bluestein list), FP32 ring threads per CTA, FP64
- * Legendre maps per CTA, FP64 ring maps per CTA}.  Errors: SHT_EINVAL. */
+ * Legendre maps per CTA, FP64 ring maps per CTA, FP32 ring-analysis maps per
+ * CTA of the tensor-core transpose}.  Errors: SHT_EINVAL. */
 int sht_tiles(sht_plan_t plan, int *out, int n);
 
-/* Set the first n (0..5) tile shapes, in the order of sht_tiles (e.g. ones an
+/* Set the first n (0..6) tile shapes, in the order of sht_tiles (e.g. ones an
  * earlier sht_autotune picked and the caller saved).  Each value must be one
- * of the autotuner's candidates ({1, 2, 4}, {1, 2}, {256, 512}, {1, 2, 4, 8},
- * {1, 2, 4, 8, 16}), else SHT_EINVAL and nothing changes. */
+ * of the candidates ({1, 2, 4}, {1, 2}, {256, 512}, {1, 2, 4, 8},
+ * {1, 2, 4, 8, 16}, {1, 2, 4, 8}), else SHT_EINVAL and nothing changes. */
 int sht_set_tiles(sht_plan_t plan, const int *vals, int n);
 
 /* FP64 alm2map that allocates nothing (the paper has no counterpart: this is

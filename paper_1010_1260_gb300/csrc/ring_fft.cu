@@ -1084,10 +1084,10 @@ cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, doubl
 }
 
 cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
-                                      const double *wring, cudaStream_t st)
+                                      const double *wring, int group, cudaStream_t st)
 {
-    return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, 0, st,
-                      map, q, wring);
+    return launch_two(ring_analysis_kernel<float, false>, ring_analysis_kernel<float, true>, P, false, nmaps, group,
+                      st, map, q, wring);
 }
 
 

@@ -54,6 +54,7 @@ struct sht_plan_s {
     int ring_nt = 256;       // threads per CTA of the FP32 ring step
     int fp64_bc = 8;         // maps per CTA of the FP64 Legendre step
     int fp64_ring_g = 8;     // maps per CTA of the FP64 ring step
+    int adj_ring_g = 8;      // maps per CTA of the FP32 ring analysis (tensor-core transpose)
     void *lcache[4] = {};  // plan-time Lambda operand per tensor-core form (sht_lambda_cache)
     bool skip_evanescent = true;  // tensor-core forms: start items after their all-zero degrees
     void *warm = nullptr;         // the skip tables (one allocation), built on first use
@@ -1154,7 +1155,8 @@ int analysis_tc(sht_plan_s *p, int nbatch, const float *map, double2 *alm, const
     for (int b0 = 0; b0 < nbatch; b0 += G) {
         const int nb = std::min(G, nbatch - b0);
         StageScope s1(p, SHT_STAGE_ADJ_RING, st);
-        cudaError_t e = sht::launch_ring_analysis_fp32(p->dp, map + (size_t)b0 * p->npix, q, nb, wring, st);
+        cudaError_t e =
+            sht::launch_ring_analysis_fp32(p->dp, map + (size_t)b0 * p->npix, q, nb, wring, p->adj_ring_g, st);
         s1.done(e, sht::ring_launches(p->dp));
         if (e != cudaSuccess) return cuda_fail(e, "ring_analysis_fp32 launch");
         StageScope s2(p, SHT_STAGE_ADJ_LEGENDRE, st);
@@ -1450,8 +1452,8 @@ int sht_tiles(sht_plan_t p, int *out, int n)
     int rc = check_plan(p);
     if (rc) return rc;
     if (!out || n < 0) return fail(SHT_EINVAL, "null output or n < 0");
-    const int v[5] = {p->ring_g[0], p->ring_g[1], p->ring_nt, p->fp64_bc, p->fp64_ring_g};
-    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
+    const int v[6] = {p->ring_g[0], p->ring_g[1], p->ring_nt, p->fp64_bc, p->fp64_ring_g, p->adj_ring_g};
+    for (int i = 0; i < n && i < 6; ++i) out[i] = v[i];
     return SHT_OK;
 }
 
@@ -1556,7 +1558,7 @@ int sht_set_tiles(sht_plan_t p, const int *vals, int n)
     g_err.clear();
     int rc = check_plan(p);
     if (rc) return rc;
-    if (!vals || n < 0 || n > 5) return fail(SHT_EINVAL, "need 0 <= n <= 5 values");
+    if (!vals || n < 0 || n > 6) return fail(SHT_EINVAL, "need 0 <= n <= 6 values");
     auto in = [](int v, std::initializer_list<int> ok) {
         for (int o : ok)
             if (v == o) return true;
@@ -1564,10 +1566,10 @@ int sht_set_tiles(sht_plan_t p, const int *vals, int n)
     };
     const bool valid = (n < 1 || in(vals[0], {1, 2, 4})) && (n < 2 || in(vals[1], {1, 2})) &&
                        (n < 3 || in(vals[2], {256, 512})) && (n < 4 || in(vals[3], {1, 2, 4, 8})) &&
-                       (n < 5 || in(vals[4], {1, 2, 4, 8, 16}));
+                       (n < 5 || in(vals[4], {1, 2, 4, 8, 16})) && (n < 6 || in(vals[5], {1, 2, 4, 8}));
     if (!valid) return fail(SHT_EINVAL, "tile shape outside the candidate set");
     std::lock_guard<std::mutex> lk(p->mu);
-    int *dst[5] = {&p->ring_g[0], &p->ring_g[1], &p->ring_nt, &p->fp64_bc, &p->fp64_ring_g};
+    int *dst[6] = {&p->ring_g[0], &p->ring_g[1], &p->ring_nt, &p->fp64_bc, &p->fp64_ring_g, &p->adj_ring_g};
     for (int i = 0; i < n; ++i) *dst[i] = vals[i];
     return SHT_OK;
 }

@@ -193,9 +193,10 @@ cudaError_t launch_ring_synth_fp64(const DevPlan &P, const double2 *delta, doubl
 // Ring step of the transpose: q[b][ring][m] = sum_j y_j e^{-i m phi_j}.
 cudaError_t launch_ring_analysis_fp64(const DevPlan &P, const double *map, double2 *q, int nmaps,
                                       const double *wring, cudaStream_t st);
-// The same ring step of the transpose in FP32 (the tensor-core forms' maps).
+// The same ring step of the transpose in FP32 (the tensor-core forms' maps);
+// group = maps per CTA (a tile shape: results do not depend on it).
 cudaError_t launch_ring_analysis_fp32(const DevPlan &P, const float *map, float2 *q, int nmaps,
-                                      const double *wring, cudaStream_t st);
+                                      const double *wring, int group, cudaStream_t st);
 // Legendre step of the transpose, FP64:
 //   g[b][idx(l, m)] = c_m sum_r lambda_lm(x_r) q[b][r][m],  c_0 = 1, c_m = cfac for m > 0
 //   (cfac = 2: the real-linear transpose of alm2map; cfac = 1: the analysis sum).

@@ -393,7 +393,7 @@ class Plan:
 
     # ------------------------------------------------------- tile shapes --
     TILE_NAMES = ("ring_maps_smooth", "ring_maps_bluestein", "ring_threads", "fp64_legendre_maps",
-                  "fp64_ring_maps")
+                  "fp64_ring_maps", "fp32_analysis_maps")
 
     def autotune(self, prec: str, nbatch: int, stream=None) -> dict:
         """Time the tile-shape candidates for form ``prec`` and batches of
@@ -403,8 +403,9 @@ class Plan:
 
     def tiles(self) -> dict:
         """The plan's current tile shapes."""
-        out = (ctypes.c_int * 5)()
-        check(lib().sht_tiles(self._h, out, 5))
+        n = len(self.TILE_NAMES)
+        out = (ctypes.c_int * n)()
+        check(lib().sht_tiles(self._h, out, n))
         return dict(zip(self.TILE_NAMES, list(out)))
 
     def set_tiles(self, **kw):
@@ -414,8 +415,9 @@ class Plan:
             if k not in cur:
                 raise KeyError(k)
             cur[k] = int(v)
-        vals = (ctypes.c_int * 5)(*[cur[k] for k in self.TILE_NAMES])
-        check(lib().sht_set_tiles(self._h, vals, 5))
+        n = len(self.TILE_NAMES)
+        vals = (ctypes.c_int * n)(*[cur[k] for k in self.TILE_NAMES])
+        check(lib().sht_set_tiles(self._h, vals, n))
 
     def skip_evanescent(self, enable: bool = True):
         """Tensor-core forms: start work items after their all-zero degrees."""

@@ -150,3 +150,19 @@ def test_map2alm_tc_matches_oracle(oracle_mod, sht):
         assert _rl2(got[b], want[b]) < 1e-6
     with pytest.raises(Exception, match="niter"):
         plan.map2alm(torch.from_numpy(y).cuda(), niter=1, prec=prec)
+
+
+def test_adjoint_tc_analysis_tiles_bit_identical(sht):
+    """The FP32 ring analysis gives the same bits for every maps-per-CTA tile."""
+    plan = sht.Plan(sht.healpix(32), 64)
+    plan.lambda_cache("bf16x6_tc")
+    y = torch.from_numpy(inputs.gaussian_map(plan.npix, 14, 11).astype(np.float32)).cuda()
+    assert plan.tiles()["fp32_analysis_maps"] == 8
+    ref = plan.map2alm_adjoint(y, "bf16x6_tc")
+    for g in (1, 2, 4):
+        plan.set_tiles(fp32_analysis_maps=g)
+        got = plan.map2alm_adjoint(y, "bf16x6_tc")
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), g
+    with pytest.raises(sht.ShtError):
+        plan.set_tiles(fp32_analysis_maps=3)
