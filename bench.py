@@ -299,6 +299,38 @@ def traffic_for(kernel: str, algorithmic_bytes: float):
     return ent["ratio"] * algorithmic_bytes
 
 
+def copy_times(a_host, m_host, reps: int = 3):
+    """Context for the end-to-end figure: the host link alone, without the
+    transform -- one step's upload, one step's download, and both at once on
+    two streams (ms, median of `reps`)."""
+    import torch
+    da = torch.empty_like(a_host, device="cuda")
+    dm = torch.empty_like(m_host, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        out = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            out.append((time.perf_counter() - t0) * 1e3)
+        return statistics.median(out[1:])
+
+    def up():
+        with torch.cuda.stream(s1):
+            da.copy_(a_host, non_blocking=True)
+
+    def down():
+        with torch.cuda.stream(s2):
+            m_host.copy_(dm, non_blocking=True)
+
+    res = {"h2d": timed(up), "d2h": timed(down), "both": timed(lambda: (up(), down()))}
+    del da, dm
+    return res
+
+
 def tc_bop_bytes(L: int, M: int, prec: str) -> int:
     """Bytes of the tensor-core B operand image (pieces of C_l a_lm per (m,
     parity) segment, padded to whole stages of KC degrees, 128 columns)."""
@@ -491,7 +523,8 @@ def run_ours(args):
         e2e = {"value": world * B / dt, "unit": UNIT, "h2d_bytes_per_step": int(a_pins[0].numel() * 16),
                "d2h_bytes_per_step": int(m_pins[0].numel() * m_pins[0].element_size()), "ms_per_step": dt * 1000,
                "steps": args.e2e_steps, "pipelined": True,
-               "api": "sht_alm2map_host (C ABI: pinned host buffers, copies pipelined inside the library)"}
+               "api": "sht_alm2map_host (C ABI: pinned host buffers, copies pipelined inside the library)",
+               "copies_alone_ms": copy_times(a_pins[0], m_pins[0])}
         del a_pins, m_pins
 
     # the same form with the plan-time Lambda operand (the recurrence moved to

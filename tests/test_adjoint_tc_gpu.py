@@ -59,6 +59,28 @@ def test_adjoint_tc_matches_oracle(oracle_mod, sht, case, prec):
     assert np.all(got[:, ms == 0].imag == 0)
 
 
+def test_adjoint_tc_generic_rings(oracle_mod, sht):
+    """Rings at arbitrary colatitudes with arbitrary phi0 (phases by sincos),
+    odd and even lengths, a ring on each pole, and ring weights for map2alm."""
+    theta = np.array([0.0, 0.05, 0.3, 0.8, 1.3, np.pi / 2, 1.9, 2.2, 2.9, np.pi])
+    nphi = np.array([1, 7, 24, 33, 50, 61, 48, 40, 11, 2])
+    phi0 = np.array([0.0, 0.3, -0.2, 0.0, 1.7, 0.05, 2.0, 0.4, 0.9, 0.1])
+    og = oracle_mod.rings_grid(theta, nphi, phi0)
+    plan = sht.Plan(sht.rings(theta, nphi, phi0), 24, 20)
+    plan.lambda_cache("bf16x6_tc")
+    y = inputs.gaussian_map(og["npix"], 15, 3).astype(np.float32)
+    got = plan.map2alm_adjoint(torch.from_numpy(y).cuda(), "bf16x6_tc").cpu().numpy()
+    want = oracle_mod.map2alm_adjoint(og, 24, 20, y.astype(np.float64))
+    for b in range(3):
+        assert _rl2(got[b], want[b]) < 1e-6
+    w = np.linspace(0.5, 1.5, len(theta))
+    plan.set_ring_weights(w)
+    got = plan.map2alm(torch.from_numpy(y).cuda(), prec="bf16x6_tc").cpu().numpy()
+    want = oracle_mod.map2alm(og, 24, 20, y.astype(np.float64), weights=w)
+    for b in range(3):
+        assert _rl2(got[b], want[b]) < 1e-6
+
+
 def test_adjoint_tc_skip_off_same(sht):
     """The chunks the skip leaves out hold only zeros: same result without it."""
     plan = sht.Plan(sht.healpix(64), 160)
