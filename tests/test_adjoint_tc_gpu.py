@@ -188,3 +188,44 @@ def test_adjoint_tc_analysis_tiles_bit_identical(sht):
         assert torch.equal(got, ref), g
     with pytest.raises(sht.ShtError):
         plan.set_tiles(fp32_analysis_maps=3)
+
+
+def test_finite_differences_tc_backward(sht):
+    """The weighted least-squares loss through autograd with the BF16x6 forward
+    (from the Lambda operand) and the tensor-core transpose as backward,
+    against central differences of the same loss on 16 random coefficients.
+    The loss is quadratic in a, so central differences carry no truncation
+    error and a unit step only meets the FP32 rounding of the maps."""
+    from paper_1010_1260_gb300 import autograd
+    nside, lmax, nmaps = 64, 128, 2
+    plan = sht.Plan(sht.healpix(nside), lmax)
+    plan.lambda_cache("bf16x6_tc")
+    a0 = torch.from_numpy(inputs.batch_alm(lmax, lmax, 5, nmaps)).cuda()
+    w_np, d_np = inputs.loss_weights(plan.npix, 5, nmaps)
+    w = torch.from_numpy(w_np).cuda()
+    d = torch.from_numpy(d_np).cuda()
+
+    def loss(a):
+        s = autograd.alm2map(a, plan, "bf16x6_tc")
+        return (w * (s.double() - d) ** 2).sum()
+
+    a = a0.clone().requires_grad_(True)
+    L = loss(a)
+    L.backward()
+    grad = a.grad.detach()
+    rng = np.random.default_rng(16)
+    h = 1.0
+    worst = 0.0
+    for _ in range(16):
+        b = int(rng.integers(nmaps))
+        i = int(rng.integers(plan.nalm))
+        comp = int(rng.integers(2))
+        if i <= lmax and comp == 1:
+            comp = 0
+        e = torch.zeros_like(a0)
+        e[b, i] = h if comp == 0 else 1j * h
+        with torch.no_grad():
+            fd = (float(loss(a0 + e)) - float(loss(a0 - e))) / (2 * h)
+        an = float(grad[b, i].real if comp == 0 else grad[b, i].imag)
+        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * float(L.detach()) / plan.npix))
+    assert worst < 1e-4, worst
