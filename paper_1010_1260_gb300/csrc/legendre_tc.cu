@@ -23,11 +23,15 @@
 //              contiguous), prefetching the next stages into L2;
 //   warp 9     one thread issues tcgen05.mma (M = 128, N = 2 x maps, K = one
 //              chunk) and releases stages with tcgen05.commit;
-//   warps 4-7  drain: the MMAs of every 64 degrees accumulate into one of two
-//              tensor-memory accumulator sets; the drain warps read a finished
-//              set (tcgen05.ld), add it in FP32 (round to nearest) into
-//              per-row totals in shared memory, release the set, and at the
-//              end of an item write Delta.  The tensor core's FP32
+//   warps 4-7  drain: the MMAs of every 64 degrees accumulate into tensor-
+//              memory columns 0-255; the drain warps read the finished group
+//              (tcgen05.ld), add it in FP32 (round to nearest) into the item's
+//              totals in columns 256-511 (tcgen05.st), release the
+//              accumulator, and at the end of an item write Delta through a
+//              small shared-memory staging buffer.  Keeping the totals out of
+//              shared memory leaves it to the stage ring (4 or 6 stages) and
+//              takes the drain's traffic off the producers' shared-memory
+//              path.  The tensor core's FP32
 //              accumulation rounds toward zero, which over ~400 accumulating
 //              MMAs biases the result by ~1e-5; summing short groups on the
 //              CUDA cores removes the bias.
@@ -169,6 +173,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// The same load without the wait (tmem_wait_ld before the registers are read).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 consecutive columns of the warp's 32 lanes from registers; tmem_wait_st
+// before the registers are reused or the columns are read back.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // K-major operand tile with the 32-byte swizzle: rows of 32 bytes, 8-row
 // groups 256 bytes apart (stride byte offset), descriptor version 1.
@@ -313,11 +344,12 @@ struct Cfg {
     static constexpr int A_TILES = 2 * NPA;    // [parity][piece]
     static constexpr int B_TILES = 2 * NPB;
     static constexpr int STAGE_BYTES = (A_TILES + B_TILES) * kTileBytes;
-    static constexpr int NS = (STAGE_BYTES * 3 <= 96 * 1024) ? 3 : 2;
     static constexpr int NPROD = (NPA == 2 && NPB == 2) ? 3 : 6;
     static constexpr int GROUP = 64 / STEPS;   // stages per accumulation group (64 degrees)
-    static constexpr int TOT_BYTES = kRows * 256 * 4;  // FP32 totals, [column][row]
-    static constexpr int SMEM = NS * STAGE_BYTES + TOT_BYTES + 1024 /* align */ + 256 /* barriers */;
+    static constexpr int STG_BYTES = 4 * 32 * 16 * 8;  // Delta staging, per drain warp 32 rows x 16 float2
+    // stage ring: as deep as shared memory allows (4 of 48 KB, 6 of 32 KB)
+    static constexpr int NS = (227 * 1024 - 1024 - 256 - STG_BYTES) / STAGE_BYTES;
+    static constexpr int SMEM = NS * STAGE_BYTES + STG_BYTES + 1024 /* align */ + 256 /* barriers */;
 };
 
 template <int NPA, int NPB>
@@ -530,9 +562,9 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
     const uint32_t base_u32 = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (base_u32 & 1023u)) & 1023u;
     unsigned char *stage0 = smem_raw + pad;
-    float *tot = reinterpret_cast<float *>(stage0 + C::NS * C::STAGE_BYTES);  // [256][128]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + C::NS * C::STAGE_BYTES + C::TOT_BYTES);
-    // bars: full_a[NS], full_b[NS], empty[NS], set_full[2], set_empty[2], mma_drain
+    float2 *stage_d = reinterpret_cast<float2 *>(stage0 + C::NS * C::STAGE_BYTES);  // Delta staging, 4 x 4 KB
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage0 + C::NS * C::STAGE_BYTES + C::STG_BYTES);
+    // bars: full_a[NS], full_b[NS], empty[NS], acc_full, acc_empty, mma_drain
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
 
@@ -544,9 +576,9 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
     auto bar_full_a = [&](int s) { return smem_u32(&bars[s]); };
     auto bar_full_b = [&](int s) { return smem_u32(&bars[C::NS + s]); };
     auto bar_empty = [&](int s) { return smem_u32(&bars[2 * C::NS + s]); };
-    auto bar_set_full = [&](int j) { return smem_u32(&bars[3 * C::NS + j]); };
-    auto bar_set_empty = [&](int j) { return smem_u32(&bars[3 * C::NS + 2 + j]); };
-    const uint32_t bar_mma_drain = smem_u32(&bars[3 * C::NS + 4]);
+    const uint32_t bar_acc_full = smem_u32(&bars[3 * C::NS]);
+    const uint32_t bar_acc_empty = smem_u32(&bars[3 * C::NS + 1]);
+    const uint32_t bar_mma_drain = smem_u32(&bars[3 * C::NS + 2]);
     auto a_tile = [&](int s, int par, int piece) {
         return stage0 + s * C::STAGE_BYTES + (par * NPA + piece) * kTileBytes;
     };
@@ -594,16 +626,15 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
             mbar_init(bar_full_b(s), 1);
             mbar_init(bar_empty(s), 1);
         }
-        for (int j = 0; j < 2; ++j) {
-            mbar_init(bar_set_full(j), 1);
-            mbar_init(bar_set_empty(j), 4);
-        }
+        mbar_init(bar_acc_full, 1);
+        mbar_init(bar_acc_empty, 4);
         mbar_init(bar_mma_drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 8) {
-        // two accumulator sets of 256 columns: set j holds E in [256 j, 256 j + ncols)
-        // and O in [256 j + ncols, 256 j + 2 ncols)
+        // columns [0, 256): the accumulator of the current 64-degree group, E
+        // in [0, ncols) and O in [ncols, 2 ncols); columns [256, 512): the
+        // item's FP32 totals in the same arrangement
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(512u));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -676,8 +707,9 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
         }
     } else if (warp < 8) {
         // ----------------------------------------------------------- drain --
-        const int row = (warp - 4) * 32 + lane;  // tensor-memory lane = ring pair in the block
-        const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+        const int quad = warp - 4;
+        const int row = quad * 32 + lane;  // tensor-memory lane = ring pair in the block
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t gg = 0;
         bool ok = true;
         for (int jt = i0; jt < i1 && ok; jt += istep) {
@@ -685,92 +717,84 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
             const Work w = work_of(item);
             const DevPlan &Q = *w.Q;
             const int m = w.m;
-            const int L = Q.lmax;
             const int pair = w.rb * kRows + row;
             const int ngroups = (nstages_of(Q, m) + C::GROUP - 1) / C::GROUP - first_stage(Q, m, w.rb) / C::GROUP;
             for (int g = 0; g < ngroups; ++g) {
-                const int set = (int)(gg & 1u);
-                ok = __all_sync(0xffffffffu, mbar_wait(bar_set_full(set), (gg >> 1) & 1u, &s_abort));
+                ok = __all_sync(0xffffffffu, mbar_wait(bar_acc_full, gg & 1u, &s_abort));
                 if (!ok) break;
                 tc_fence_after();
+                // totals (columns 256 + c) = accumulator (g = 0), else totals + accumulator,
+                // added in FP32 with rounding to nearest, 32 columns at a time
                 for (int c0 = 0; c0 < 2 * ncols; c0 += 32) {
-                    uint32_t v[32];
-                    SHT_CHECK(Q.dbg, 256 * set + c0 + 32 <= 512 && c0 + 32 <= 256, 402);
-                    tmem_ld32(tmem + lane_base + (uint32_t)(256 * set + c0), v);
-                    float *tp = tot + (size_t)c0 * kRows + row;
-                    if (g == 0) {
+                    uint32_t v[32], t[32];
+                    SHT_CHECK(Q.dbg, c0 + 32 <= 256, 402);
+                    tmem_ld32_async(tmem + lane_base + (uint32_t)c0, v);
+                    if (g > 0) tmem_ld32_async(tmem + lane_base + (uint32_t)(256 + c0), t);
+                    tmem_wait_ld();
+                    if (g > 0) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) tp[j * kRows] = __uint_as_float(v[j]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) tp[j * kRows] += __uint_as_float(v[j]);
+                        for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(t[j]) + __uint_as_float(v[j]));
                     }
+                    tmem_st32(tmem + lane_base + (uint32_t)(256 + c0), v);
+                    tmem_wait_st();
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(bar_set_empty(set));
+                if (lane == 0) mbar_arrive(bar_acc_empty);
                 ++gg;
             }
             if (!ok) break;
             // Delta_m(north) = E + O, Delta_m(south) = E - O for the warp's 32
             // rows; Delta is [ring][m][map].  Per block of 16 maps (columns
-            // 32 k .. 32 k + 31 of E and of O) the warp reads its rows' totals,
-            // writes N and S back transposed into the same, now consumed,
-            // totals (row r's 32 floats as 16-byte granules, granule x at
-            // x ^ (r & 7): no bank conflicts) and sends each row's 128 bytes
-            // out as 16-byte stores, four rows per instruction.
+            // 32 k .. 32 k + 31 of E and of O) the warp reads its rows'
+            // totals, and each row's 128 bytes of N (then S) go through the
+            // warp's staging buffer (row = lane, element c at c ^ (lane & 15):
+            // no bank conflicts) and out as 16-byte stores, four rows per
+            // instruction.
             {
-                const int quad = warp - 4;
                 int2 rr = make_int2(-1, -1);
                 if (pair < Q.npairs) rr = Q.pair_ring[pair];
                 const int M1 = Q.mmax + 1;
                 const bool vec = (nmaps & 1) == 0;
-                // float x of row r of the transposed block at column col0
-                auto slot = [&](int col0, int r, int x) {
-                    return tot + (size_t)(col0 + r) * kRows + 32 * quad + ((((x >> 2) ^ (r & 7)) << 2) | (x & 3));
-                };
+                float2 *stg = stage_d + quad * (32 * 16);
                 for (int k = 0; 32 * k < ncols; ++k) {
-                    float e[32], o[32];
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        e[c] = tot[(32 * k + c) * kRows + row];
-                        o[c] = tot[(ncols + 32 * k + c) * kRows + row];
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int x = 0; x < 32; x += 4) {
-                        const float4 nv = make_float4(e[x] + o[x], (m == 0) ? 0.f : e[x + 1] + o[x + 1],
-                                                      e[x + 2] + o[x + 2], (m == 0) ? 0.f : e[x + 3] + o[x + 3]);
-                        const float4 sv = make_float4(e[x] - o[x], (m == 0) ? 0.f : e[x + 1] - o[x + 1],
-                                                      e[x + 2] - o[x + 2], (m == 0) ? 0.f : e[x + 3] - o[x + 3]);
-                        *reinterpret_cast<float4 *>(slot(32 * k, lane, x)) = nv;
-                        *reinterpret_cast<float4 *>(slot(ncols + 32 * k, lane, x)) = sv;
-                    }
-                    __syncwarp();
-                    const int sg = lane & 7;  // granule sg: maps 16 k + 2 sg and + 1
-                    const int b = 16 * k + 2 * sg;
+                    uint32_t e[32], o[32];
+                    tmem_ld32_async(tmem + lane_base + (uint32_t)(256 + 32 * k), e);
+                    tmem_ld32_async(tmem + lane_base + (uint32_t)(256 + ncols + 32 * k), o);
+                    tmem_wait_ld();
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float er = __uint_as_float(e[2 * c]), ei = __uint_as_float(e[2 * c + 1]);
+                            const float orr = __uint_as_float(o[2 * c]), oi = __uint_as_float(o[2 * c + 1]);
+                            stg[lane * 16 + (c ^ (lane & 15))] =
+                                side == 0 ? make_float2(er + orr, (m == 0) ? 0.f : ei + oi)
+                                          : make_float2(er - orr, (m == 0) ? 0.f : ei - oi);
+                        }
+                        __syncwarp();
+                        const int sg = lane & 7;  // maps 16 k + 2 sg and + 1
+                        const int b = 16 * k + 2 * sg;
 #pragma unroll
                         for (int it = 0; it < 8; ++it) {
                             const int rw = it * 4 + (lane >> 3);
                             const int ring = __shfl_sync(0xffffffffu, side == 0 ? rr.x : rr.y, rw);
-                            const float4 v =
-                                *reinterpret_cast<const float4 *>(slot(side == 0 ? 32 * k : ncols + 32 * k, rw, 4 * sg));
+                            const float2 v0 = stg[rw * 16 + ((2 * sg) ^ (rw & 15))];
+                            const float2 v1 = stg[rw * 16 + ((2 * sg + 1) ^ (rw & 15))];
                             if (ring >= 0) {
                                 // maps b, b + 1 are stored only where they exist (b < nmaps)
                                 SHT_CHECK(Q.dbg, ring < Q.nrings && m < M1, 403);
                                 float2 *d = w.dl + ((size_t)ring * M1 + m) * nmaps + b;
                                 if (vec && b + 1 < nmaps) {
-                                    *reinterpret_cast<float4 *>(d) = v;
+                                    *reinterpret_cast<float4 *>(d) = make_float4(v0.x, v0.y, v1.x, v1.y);
                                 } else {
-                                    if (b < nmaps) d[0] = make_float2(v.x, v.y);
-                                    if (b + 1 < nmaps) d[1] = make_float2(v.z, v.w);
+                                    if (b < nmaps) d[0] = v0;
+                                    if (b + 1 < nmaps) d[1] = v1;
                                 }
                             }
                         }
+                        __syncwarp();
                     }
-                    __syncwarp();
                 }
             }
         }
@@ -834,8 +858,8 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
             const int L = Q.lmax;
                 const int nst = nstages_of(Q, m);
                 for (int i0 = first_stage(Q, m, w.rb); i0 < nst && ok; i0 += C::GROUP) {
-                    const int set = (int)(gg & 1u);
-                    if (!mbar_wait(bar_set_empty(set), ((gg >> 1) & 1u) ^ 1u, &s_abort)) {
+                    // the drain has read the previous group's accumulator
+                    if (!mbar_wait(bar_acc_empty, (gg & 1u) ^ 1u, &s_abort)) {
                         ok = false;
                         break;
                     }
@@ -849,10 +873,10 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                             break;
                         }
                         tc_fence_after();
-                        SHT_CHECK(Q.dbg, 256 * set + 2 * ncols <= 512 && s < C::NS, 406);
+                        SHT_CHECK(Q.dbg, 2 * ncols <= 256 && s < C::NS, 406);
 #pragma unroll
                         for (int par = 0; par < 2; ++par) {
-                            const uint32_t d = tmem + (uint32_t)(256 * set + par * ncols);
+                            const uint32_t d = tmem + (uint32_t)(par * ncols);
 #pragma unroll
                             for (int pr = 0; pr < C::NPROD; ++pr) {
                                 int ia, ib;
@@ -867,7 +891,7 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                         ++gs;
                     }
                     if (!ok) break;
-                    tc_commit(bar_set_full(set));
+                    tc_commit(bar_acc_full);
                     ++gg;
                 }
             }
