@@ -732,8 +732,16 @@ legendre_tc_kernel(const __grid_constant__ DevPlan P, const unsigned char *__res
                     if (g > 0) tmem_ld32_async(tmem + lane_base + (uint32_t)(256 + c0), t);
                     tmem_wait_ld();
                     if (g > 0) {
+                        // two FP32 adds (round to nearest) per instruction
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(t[j]) + __uint_as_float(v[j]));
+                        for (int j = 0; j < 32; j += 2) {
+                            const unsigned long long a = ((unsigned long long)t[j + 1] << 32) | t[j];
+                            const unsigned long long b = ((unsigned long long)v[j + 1] << 32) | v[j];
+                            unsigned long long d;
+                            asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+                            v[j] = (uint32_t)d;
+                            v[j + 1] = (uint32_t)(d >> 32);
+                        }
                     }
                     tmem_st32(tmem + lane_base + (uint32_t)(256 + c0), v);
                     tmem_wait_st();
