@@ -293,11 +293,12 @@ __device__ __forceinline__ double mul_coef(double a, const XInt &X)
 // degrees (by position in the stage) whose coefficient product runs on the
 // integer pipes; the rest are DMULs (as an FMA with +0): both give the same bits
 // (bit q of the pattern, q = position of the degree in the stage).  Two of
-// every three (q mod 3 != 0): measured at nside 1024, lmax 2048, 64 maps,
-// 13.29 ms against 13.59 for one in two, 13.89 for three in four and 14.42 for
-// three in eight.
+// every three (q mod 3 != 1): measured at nside 1024, lmax 2048, 64 maps,
+// 13.15 ms, against 13.30 and 13.52 for the other two phases of two in three,
+// 13.19 for five in seven, 13.34 for seven in ten, 13.59 for one in two, 13.68
+// for three in five, 13.89 for three in four and 14.42 for three in eight.
 #ifndef SHT_INT_PRODUCT_BITS
-#define SHT_INT_PRODUCT_BITS 0xB6DB6DB6u
+#define SHT_INT_PRODUCT_BITS 0x6DB6DB6Du
 #endif
 __host__ __device__ constexpr bool int_product(int q) { return ((SHT_INT_PRODUCT_BITS >> (q & 31)) & 1u) != 0u; }
 template <int Q>
